@@ -94,14 +94,35 @@ static void SFX(column_solve)(int nlon, int nlat, int nz,
         x[k] = x[k + 1] + (y[k] - (q[k] / p[k]) * x[k + 1]);
 }
 
-/* One block-Jacobi (vertical line relaxation) sweep, Eq. (1):
+/*
+ * One block-Jacobi (vertical line relaxation) sweep, Eq. (1):
  *   u <- u + omega H_z^{-1} (b - H u).
- * r is caller-provided work space of the field's size. */
+ * With H = H_z + dH this equals (1 - omega) u + omega H_z^{-1} (b - dH u),
+ * and that is how it is evaluated: b - dH u = b + sum over the four
+ * horizontal faces of T_f u_nb(f) has no vertical fluxes, so the
+ * cancellation of the large vertical terms inside b - H u (couplings ~1e6
+ * times the row sums) never happens.  rhs is caller-provided work space of
+ * the field's size; every column reads the old u.
+ */
 void SFX(orc_smooth)(int nlon, int nlat, int nz,
                      const REAL *tx, const REAL *ty, const REAL *tz, const REAL *h,
-                     const REAL *b, REAL *u, REAL omega, REAL *r)
+                     const REAL *b, REAL *u, REAL omega, REAL *rhs)
 {
-    SFX(orc_residual)(nlon, nlat, nz, tx, ty, tz, h, b, u, r);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < nlat; ++j)
+            for (int i = 0; i < nlon; ++i) {
+                size_t c = IX(k, j, i);
+                int ie = (i + 1) % nlon;
+                int iw = (i + nlon - 1) % nlon;
+                REAL v = b[c];
+                v += tx[c] * u[IX(k, j, ie)];
+                v += tx[IX(k, j, iw)] * u[IX(k, j, iw)];
+                if (j + 1 < nlat) v += ty[c] * u[IX(k, j + 1, i)];
+                if (j > 0) v += ty[IX(k, j - 1, i)] * u[IX(k, j - 1, i)];
+                rhs[c] = v;
+            }
+    const REAL one = (REAL)1;
 #pragma omp parallel
     {
         REAL *q = (REAL *)malloc(4 * (size_t)nz * sizeof(REAL));
@@ -109,8 +130,11 @@ void SFX(orc_smooth)(int nlon, int nlat, int nz,
 #pragma omp for schedule(static)
         for (int j = 0; j < nlat; ++j)
             for (int i = 0; i < nlon; ++i) {
-                SFX(column_solve)(nlon, nlat, nz, tx, ty, tz, h, r, j, i, q, p, y, x);
-                for (int k = 0; k < nz; ++k) u[IX(k, j, i)] += omega * x[k];
+                SFX(column_solve)(nlon, nlat, nz, tx, ty, tz, h, rhs, j, i, q, p, y, x);
+                for (int k = 0; k < nz; ++k) {
+                    size_t c = IX(k, j, i);
+                    u[c] = (one - omega) * u[c] + omega * x[k];
+                }
             }
         free(q);
     }

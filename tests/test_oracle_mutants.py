@@ -31,7 +31,9 @@ MUTANTS = [
      "x[k] = x[k + 1] + (y[k] - (q[k] / p[k]) * x[k + 1]);",
      "x[k] = x[k + 1] + (y[k] - (tz[IX(k, j, i)] / p[k]) * x[k + 1]);"),
     ("smoother sign as printed in Eq. (1)", "tpmg_oracle_real.h",
-     "u[IX(k, j, i)] += omega * x[k];", "u[IX(k, j, i)] -= omega * x[k];"),
+     "u[c] = (one - omega) * u[c] + omega * x[k];", "u[c] = (one + omega) * u[c] - omega * x[k];"),
+    ("smoother right-hand side misses the north neighbour", "tpmg_oracle_real.h",
+     "if (j + 1 < nlat) v += ty[c] * u[IX(k, j + 1, i)];", ""),
     ("restriction lon weights swapped", "tpmg_oracle_real.h",
      "bc[base + I] += w * three4 * rv;", "bc[base + I] += w * one4 * rv;"),
     ("prolongation lon neighbour on the wrong side", "tpmg_oracle_real.h",

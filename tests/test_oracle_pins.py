@@ -195,20 +195,64 @@ def test_column_solve_matches_exact_rational_solve_of_Hz():
         assert np.max(np.abs(x[:, j, i] - xe)) <= 1e-13 * np.max(np.abs(xe))
 
 
+def _exact_residual_form_sweep(P, b, u, omega):
+    """Eq. (1) as printed (with the convergent sign), in exact rational
+    arithmetic: u + omega H_z^{-1} (b - H u), with H from the definition."""
+    tx, ty, tz, h = (P[k] for k in ("tx", "ty", "tz", "h"))
+    nz, nlat, nlon = h.shape
+    F = lambda v: Fraction(float(v))
+    U = {(k, j, i): F(u[k, j, i]) for k in range(nz) for j in range(nlat) for i in range(nlon)}
+    out = np.empty_like(u)
+    for j in range(nlat):
+        for i in range(nlon):
+            r, diag, off = [], [], []
+            for k in range(nz):
+                c = U[k, j, i]
+                faces = [(F(tx[k, j, i]), U[k, j, (i + 1) % nlon]),
+                         (F(tx[k, j, i - 1]), U[k, j, (i - 1) % nlon])]
+                if j + 1 < nlat:
+                    faces.append((F(ty[k, j, i]), U[k, j + 1, i]))
+                if j > 0:
+                    faces.append((F(ty[k, j - 1, i]), U[k, j - 1, i]))
+                if k + 1 < nz:
+                    faces.append((F(tz[k, j, i]), U[k + 1, j, i]))
+                if k > 0:
+                    faces.append((F(tz[k - 1, j, i]), U[k - 1, j, i]))
+                hu = F(h[k, j, i]) * c + sum(t * (c - un) for t, un in faces)
+                r.append(F(b[k, j, i]) - hu)
+                diag.append(F(h[k, j, i]) + sum(t for t, _ in faces))
+                if k + 1 < nz:
+                    off.append(-F(tz[k, j, i]))
+            # exact tridiagonal solve
+            d, rr = list(diag), list(r)
+            for k in range(1, nz):
+                m = off[k - 1] / d[k - 1]
+                d[k] -= m * off[k - 1]
+                rr[k] -= m * rr[k - 1]
+            x = [Fraction(0)] * nz
+            x[-1] = rr[-1] / d[-1]
+            for k in range(nz - 2, -1, -1):
+                x[k] = (rr[k] - off[k] * x[k + 1]) / d[k]
+            for k in range(nz):
+                out[k, j, i] = float(U[k, j, i] + F(omega) * x[k])
+    return out
+
+
 def test_smoother_is_eq1_with_convergent_sign():
-    """One sweep: u_new = u + omega H_z^{-1} (b - H u) (Eq. 1, '+' sign), and
-    repeated sweeps reduce the error (the printed '-' sign diverges)."""
-    P = small(nlon=16, nlat=8, nz=8)
+    """One sweep equals Eq. (1) with the '+' sign, u + omega H_z^{-1}(b - H u),
+    evaluated exactly in rational arithmetic (the oracle evaluates the same
+    iteration as (1 - omega) u + omega H_z^{-1}(b - dH u)); repeated sweeps
+    reduce the error (the printed '-' sign diverges)."""
+    P = small(nlon=8, nlat=4, nz=6, sigma=0.2)
     lev = O.build_hierarchy(P["tx"], P["ty"], P["tz"], P["h"], O.MGParams(levels=1))[0]
     rng = np.random.default_rng(2)
     u = rng.standard_normal(lev.shape)
     b = P["b"]
     u1 = u.copy()
     O.smooth(lev, b, u1, 0.8)
-    want = u + 0.8 * O.column_solve(lev, O.residual(lev, b, u))
-    assert np.allclose(u1, want, rtol=1e-14, atol=1e-14 * np.abs(want).max())
-    A = O.dense_operator(lev)
-    xs = np.linalg.solve(A, b.ravel()).reshape(lev.shape)
+    want = _exact_residual_form_sweep(P, b, u, 0.8)
+    assert np.max(np.abs(u1 - want)) <= 1e-14 * np.max(np.abs(want))
+    xs, _ = _dense_solve(P, b)
     e0 = np.linalg.norm(u - xs)
     for _ in range(30):
         O.smooth(lev, b, u, 0.8)
