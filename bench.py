@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark: milliseconds to a 1e-10 relative residual on the operational-size
+lat-lon grid (1536 x 1152 x 70, ~124M unknowns), FP32 multigrid inside FP64
+refinement (the headline `value`) next to the plain FP64 multigrid solve.
+
+One step = one solve of H x = b from x = 0 (all kernels of the path).  Inputs
+are synthetic (seeded generator of `synthetic`), resident in HBM when the
+timed region starts; every array exceeds the 129 MB L2, so no flush is
+needed.  N > 1 GPUs run independent replicas (one system per rank, seeds
+differ), so scaling is weak and there is no collective on the data path.
+
+`--impl reference` times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from synthetic import WORKLOADS, make_problem, workload_seed  # noqa: E402
+
+METRIC = "ms to 1e-10 rel residual, 1536x1152x70: FP32-MG+FP64 refine vs FP64 MG; HBM %"
+UNIT = "ms"
+TOL = 1e-10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="latlon_1536x1152x70")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- CPU oracle
+def oracle_iteration_ms(P, its: int):
+    """Time one V-cycle-preconditioned CG iteration of the FP64 oracle (V-cycle,
+    operator apply, two inner products, vector updates) on the host cores."""
+    from oracle import tpmg as O
+    p = O.MGParams()
+    lev = O.build_hierarchy(P["tx"], P["ty"], P["tz"], P["h"], p)
+    b = P["b"]
+    r = b.copy()
+    t0 = time.perf_counter()
+    z = O.vcycle(lev, r, p)
+    Ad = O.apply(lev[0], z)
+    a = O.dot(r, z) / O.dot(z, Ad)
+    r -= a * Ad
+    z *= a
+    t1 = time.perf_counter()
+    per_it = (t1 - t0) * 1e3
+    return per_it, O.num_threads(), lev, p
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import tpmg as O
+    w = WORKLOADS[args.workload]
+    P = make_problem(w["nlon"], w["nlat"], w["nz"], w["sigma"], workload_seed(args.workload))
+    # iteration count of the oracle's own FP64 solve to 1e-10 (untimed, once)
+    p = O.MGParams()
+    lev = O.build_hierarchy(P["tx"], P["ty"], P["tz"], P["h"], p)
+    _, hist, st = O.solve(lev, P["b"], TOL, params=p)
+    its = len(hist) - 1
+    times = []
+    for step in range(args.warmup + args.steps):
+        per_it, cores, _, _ = oracle_iteration_ms(P, its)
+        if step >= args.warmup:
+            times.append(per_it * its)
+    v = statistics.mean(times)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "tol": TOL, "iterations": its,
+                   "oracle_status": int(st)},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: one FP64 CG iteration of the oracle at "
+                                   f"{args.workload} x {its} iterations (its own solve)"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2307_04528_gb300 import _lib as L
+    from paper_2307_04528_gb300.solver import MGHandle
+
+    w = WORKLOADS[args.workload]
+    P = make_problem(w["nlon"], w["nlat"], w["nz"], w["sigma"],
+                     workload_seed(args.workload, rank))
+    N = P["h"].size
+    d = lambda a: torch.as_tensor(a, dtype=torch.float64).cuda()
+    tx, ty, tz, hh, b = d(P["tx"]), d(P["ty"]), d(P["tz"]), d(P["h"]), d(P["b"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H = MGHandle(tx, ty, tz, hh, mixed=1)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    del tx, ty, tz, hh
+    x = torch.zeros_like(b)
+    lib = L.load()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(fn, steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        infos = [fn() for _ in range(steps)]
+        ev1.record(stream)
+        barrier()
+        return ev0.elapsed_time(ev1), infos
+
+    def mixed_step():
+        x.zero_()
+        _, info = H.solve_mixed(b, x, tol=TOL)
+        return info
+
+    def fp64_step():
+        x.zero_()
+        _, info = H.solve(b, x, tol=TOL)
+        return info
+
+    for _ in range(args.warmup):
+        mixed_step()
+    fp64_step()
+
+    # headline: mixed precision, clocks sampled during the timed region
+    clocks = ClockSampler(local)
+    n0 = lib.mg_launch_count()
+    ms_mixed, infos = timed(mixed_step, args.steps)
+    launches = lib.mg_launch_count() - n0
+    clk = clocks.stop()
+    ms_mixed = max_over_ranks(ms_mixed / args.steps)
+    info_m = infos[-1]
+    # the same timed steps again with CUDA events around every fine-level launch
+    H.profile(True)
+    ms_prof, _ = timed(mixed_step, args.steps)
+    sm_calls, sm_ms = H.profile_read(L.K_SMOOTH, 0, L.MG_PREC_FP32)
+    res_calls, res_ms = H.profile_read(L.K_RESID, 0, L.MG_PREC_FP64)
+    H.profile(False)
+    ms_prof = max_over_ranks(ms_prof / args.steps)
+
+    ms_fp64, infos64 = timed(fp64_step, args.steps)
+    ms_fp64 = max_over_ranks(ms_fp64 / args.steps)
+    info_d = infos64[-1]
+
+    # end to end through the public API with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        hb = torch.from_numpy(P["b"]).pin_memory()
+        hx = torch.empty_like(hb).pin_memory()
+
+        def e2e_step():
+            bd = hb.to("cuda", non_blocking=True)
+            xd = torch.zeros_like(bd)
+            _, info = H.solve_mixed(bd, xd, tol=TOL)
+            hx.copy_(xd, non_blocking=True)
+            return info
+
+        e2e_step()
+        ms_e2e, _ = timed(e2e_step, args.steps)
+        ms_e2e = max_over_ranks(ms_e2e / args.steps)
+        e2e = {"value": ms_e2e, "unit": UNIT, "h2d_bytes_per_step": int(hb.numel() * 8),
+               "d2h_bytes_per_step": int(hx.numel() * 8)}
+
+    peak, peak_kind = load_peaks()
+    # FP32 smoother sweep, algorithmic bytes: reads u, b, tx, ty, tz, h; writes u (7 x 4 B)
+    sm_bytes = 28 * N
+    sm_avg_ms = sm_ms / max(sm_calls, 1)
+    achieved = sm_bytes / (sm_avg_ms * 1e-3) / 1e9 if sm_calls else None
+    roofline = {"kernel": "k_smooth<float> fine level (non-zero guess)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "launches_timed": sm_calls, "avg_ms": sm_avg_ms,
+                "bytes_per_launch": sm_bytes, "peak_source": peak_kind,
+                "timed_region": "repeat of the K timed mixed solves with events around "
+                                "fine-level launches", "ms_per_step_profiled": ms_prof}
+    res_avg = res_ms / max(res_calls, 1)
+
+    out = {
+        "metric": METRIC, "value": ms_mixed, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "unknowns": int(N), "tol": TOL,
+                   "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (no flush)",
+                   "mixed_refinement_steps": info_m["iterations"],
+                   "mixed_fp32_iterations": info_m["inner_iterations"],
+                   "mixed_rel_res": info_m["rel_res"],
+                   "fp64_ms": ms_fp64, "fp64_iterations": info_d["iterations"],
+                   "fp64_rel_res": info_d["rel_res"],
+                   "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed,
+                   "levels": H.num_levels, "setup_ms": setup_ms,
+                   "fp64_residual_kernel_avg_ms": res_avg},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": roofline,
+    }
+    if e2e:
+        out["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per_it, cores, _, _ = oracle_iteration_ms(P, info_d["iterations"])
+        out["cpu_baseline"] = {
+            "value": per_it * info_d["iterations"], "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": f"one FP64 CG iteration of the oracle at {args.workload}, scaled by the "
+                      f"FP64 iteration count to 1e-10 ({info_d['iterations']})"}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

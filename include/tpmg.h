@@ -1,0 +1,206 @@
+/*
+ * tpmg.h -- C ABI of the GB300 tensor-product multigrid library (libtpmg.so).
+ *
+ * Solves H u = b for the pressure-correction system of the paper (Section 2:
+ * "H is a sparse, discrete Laplacian-like matrix") on a cell-centred
+ * latitude-longitude grid of nz layers, nlat latitude rows and nlon
+ * longitudes, with the tensor-product multigrid of Sections 2.1-2.3: a
+ * vertical line (block-Jacobi) smoother, Eq. (1); horizontal-only coarsening
+ * with conditional semi-coarsening in latitude (Section 2.2); a V-cycle
+ * (Section 2, Fig. 1) with a simple iterative coarsest-level solve
+ * (Section 2.3).
+ *
+ * Conventions
+ *   Layout. Every field is a dense array [nz][nlat][nlon] (C order, index
+ *     (k*nlat + j)*nlon + i), longitude fastest.  Face coefficients:
+ *       tx[k,j,i] couples cells (i, i+1 mod nlon)  (periodic longitude)
+ *       ty[k,j,i] couples rows  (j, j+1); ty[:, nlat-1, :] must be 0 (pole)
+ *       tz[k,j,i] couples layers (k, k+1); tz[nz-1] must be 0 (model top)
+ *       h [k,j,i] Helmholtz (diagonal) term, > 0
+ *     (H u)_c = h_c u_c + sum over the six faces of T_f (u_c - u_nb(f)).
+ *   Memory. Unless stated otherwise, pointers are DEVICE pointers on the
+ *     current CUDA device.  The library allocates no device memory: the
+ *     caller passes one device workspace (size from mg_workspace_bytes) to
+ *     mg_setup and keeps it alive until mg_destroy.  The handle itself is
+ *     host memory owned by the library.
+ *   Streams. `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Every call is stream-ordered; only the calls that
+ *     return host scalars (solves, norms, mg_setup's validation) synchronise
+ *     the stream.
+ *   Errors. Every int-returning call returns an mg_status; no call aborts,
+ *     traps or throws.  mg_last_error() returns a thread-local message for
+ *     the last failing call on this thread.
+ */
+#ifndef TPMG_H
+#define TPMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MG_OK = 0,
+    MG_ERR_ARG = 1,            /* bad shape, null pointer, level out of range */
+    MG_ERR_COEFF = 2,          /* h <= 0, T < 0, non-finite, or a non-zero pole/top face */
+    MG_ERR_NONFINITE = 3,      /* NaN/Inf met in a right-hand side or residual */
+    MG_ERR_NOT_CONVERGED = 4,  /* maxit reached before the tolerance */
+    MG_ERR_DIVERGED = 5,       /* residual grew beyond 1e3 x its start */
+    MG_ERR_TIMEOUT = 6,        /* reserved: a bounded device wait gave up */
+    MG_ERR_CUDA = 7,           /* a CUDA runtime call failed */
+    MG_ERR_WORKSPACE = 8       /* workspace too small or misaligned */
+} mg_status;
+
+enum { MG_METHOD_CG = 0, MG_METHOD_STATIONARY = 1 };
+enum { MG_PREC_FP64 = 0, MG_PREC_FP32 = 1 };
+
+typedef struct mg_handle mg_handle;
+
+typedef struct {
+    int nlon;   /* longitudes; divisible by 2^(levels-1); >= 4 */
+    int nlat;   /* latitude rows; even (mirror-symmetric hemispheres); >= 2 */
+    int nz;     /* layers; 1 <= nz <= MG_MAX_NZ */
+} mg_grid;
+
+#define MG_MAX_NZ 192
+
+typedef struct {
+    const double *tx, *ty, *tz, *h;   /* device, [nz][nlat][nlon], FP64 */
+} mg_coeffs;
+
+typedef struct {
+    int levels;        /* 0: coarsen down to the coarsest level (nlon >= 4 there);
+                          4 is the shallow hierarchy of Section 2.3 */
+    int nu1, nu2;      /* pre/post smoothing sweeps (V(1,1) default) */
+    int coarse_iters;  /* block-Jacobi sweeps on the coarsest level (8) */
+    int method;        /* MG_METHOD_CG (V-cycle-preconditioned CG, default) or
+                          MG_METHOD_STATIONARY (x <- x + V(b - H x), Section 2) */
+    int mixed;         /* 1: also build the FP32 hierarchy for mg_solve_mixed */
+    int maxit;         /* outer iterations (200) */
+    int inner_maxit;   /* mixed: FP32 iterations per FP64 refinement step (8) */
+    double omega;      /* Eq. (1) relaxation factor (0.8) */
+    double alpha_c;    /* Section 2.2 anisotropy threshold for merging rows (0.5) */
+    double inner_tol;  /* mixed: FP32 relative tolerance per refinement step (1e-3) */
+} mg_params;
+
+typedef struct {
+    int iterations;         /* outer iterations (V-cycles or refinement steps) */
+    int inner_iterations;   /* mixed: total FP32 iterations */
+    double rel_res;         /* final ||b - H x||_2 / ||b||_2 (FP64) */
+    double *history;        /* HOST array (may be NULL): rel. residual per outer step */
+    int history_cap;        /* capacity of history */
+    int history_len;        /* entries written */
+} mg_stats;
+
+/* Fill *p with the defaults listed above.  Never fails. */
+void mg_default_params(mg_params *p);
+
+/* Bytes of device workspace mg_setup needs for this grid and these
+ * parameters (256-byte aligned start required).  MG_ERR_ARG on a bad grid. */
+int mg_workspace_bytes(const mg_grid *grid, const mg_params *params, size_t *bytes);
+
+/* Build the hierarchy (Sections 2.1-2.3): copy the fine coefficients into
+ * the workspace (the caller may free them afterwards), validate them
+ * (MG_ERR_COEFF), build the conditional semi-coarsening row maps
+ * (Section 2.2), assemble the coarse operators, factor every column
+ * tridiagonal of every level (FP64, and FP32 when params->mixed).
+ * Synchronises `stream` once.  On failure *out is NULL. */
+int mg_setup(const mg_grid *grid, const mg_coeffs *coeffs, const mg_params *params,
+             void *workspace, size_t ws_bytes, void *stream, mg_handle **out);
+
+/* Release the handle (host memory only; the workspace stays the caller's). */
+void mg_destroy(mg_handle *h);
+
+/* y = H x on the fine level (Section 2).  x, y: device FP64 fields. */
+int mg_apply(mg_handle *h, const double *x, double *y, void *stream);
+
+/* e = V r: one V(nu1, nu2)-cycle from a zero initial guess (Section 2,
+ * Fig. 1).  r, e: device FP64 fine-level fields; r is not modified. */
+int mg_vcycle(mg_handle *h, const double *r, double *e, void *stream);
+
+/* Solve H x = b to ||b - H x||_2 <= tol ||b||_2 in FP64 (Section 2).
+ * x: in = initial guess, out = solution.  stats may be NULL.  Returns
+ * MG_OK, MG_ERR_NOT_CONVERGED (x holds the last iterate), MG_ERR_NONFINITE
+ * or MG_ERR_DIVERGED.  Synchronises once per iteration (one scalar). */
+int mg_solve(mg_handle *h, const double *b, double *x, double tol, mg_stats *stats,
+             void *stream);
+
+/* Same system, FP32 multigrid inside FP64 iterative refinement (Section 1:
+ * single-precision solves): FP64 residual, norms and update; FP32 storage
+ * and arithmetic in the smoother, residual and transfers of the inner
+ * solve.  Needs params->mixed = 1 at setup (else MG_ERR_ARG).  x: in =
+ * initial guess, out = solution. */
+int mg_solve_mixed(mg_handle *h, const double *b, double *x, double tol, mg_stats *stats,
+                   void *stream);
+
+/* Coefficient gradient of a loss L(x) through H x = b (differentiable
+ * solve), given the adjoint lambda = H^{-T} dL/dx (H is symmetric, so
+ * lambda comes from mg_solve on dL/dx) and the solution x:
+ *   gh  = -lambda * x
+ *   gtx = -(lambda_c - lambda_e)(x_c - x_e)  (east faces; same for gty/gtz)
+ * All device FP64 fields; any of the outputs may be NULL. */
+int mg_coeff_grad(mg_handle *h, const double *lambda, const double *x,
+                  double *gh, double *gtx, double *gty, double *gtz, void *stream);
+
+/* ---- per-level kernels (the V-cycle's steps), for checking and profiling.
+ * `prec` selects the FP64 or FP32 hierarchy; pointers are device arrays of
+ * that precision with the level's shape (mg_level_shape). */
+
+/* Shape of level l (0 = finest) and the number of levels. */
+int mg_num_levels(const mg_handle *h);
+int mg_level_shape(const mg_handle *h, int level, int *nlon, int *nlat, int *nz);
+
+/* Copy level l's coefficients (FP64) into caller device arrays (any NULL). */
+int mg_level_coeffs(mg_handle *h, int level, double *tx, double *ty, double *tz,
+                    double *hh, void *stream);
+
+/* y = H_l x (prec: MG_PREC_FP64 or MG_PREC_FP32; FP32 acts on the scaled
+ * copies, see mg_fp32_scale). */
+int mg_level_apply(mg_handle *h, int level, int prec, const void *x, void *y, void *stream);
+
+/* r = b - H_l u. */
+int mg_level_residual(mg_handle *h, int level, int prec, const void *b, const void *u,
+                      void *r, void *stream);
+
+/* One smoother sweep of Eq. (1) on level l:
+ *   u_out = u_in + omega H_z^{-1} (b - H u_in), evaluated as
+ *   (1 - omega) u_in + omega H_z^{-1} (b - dH u_in).
+ * u_in == NULL means the zero initial guess.  u_out must not alias u_in. */
+int mg_level_smooth(mg_handle *h, int level, int prec, const void *b, const void *u_in,
+                    void *u_out, void *stream);
+
+/* bc = R r: restriction from level l to l+1 (R = P^T). */
+int mg_level_restrict(mg_handle *h, int level, int prec, const void *r, void *bc,
+                      void *stream);
+
+/* u += P ec: bilinear horizontal prolongation from level l+1 to level l. */
+int mg_level_prolong_add(mg_handle *h, int level, int prec, const void *ec, void *u,
+                         void *stream);
+
+/* The power-of-two factor c by which the FP32 coefficient copies are
+ * scaled (FP32 level l holds c * coefficients); 0 when not built. */
+double mg_fp32_scale(const mg_handle *h);
+
+/* ---- measurement hooks (off by default; no effect on results).
+ * When profiling is on (on = 1: fine-level launches only; on = 2: every
+ * level), each kernel launch of this handle is bracketed by CUDA events on
+ * its stream (events created by mg_profile_enable, freed by
+ * mg_profile_enable(h, 0) or mg_destroy).  mg_profile_read returns, for the
+ * launches of kernel class `kind` on `level` in precision `prec`, the launch
+ * count and the summed event time in ms (synchronises on the events).
+ * kind: 0 smoother (non-zero guess), 1 smoother (zero guess), 2 residual,
+ * 3 apply, 4 restriction, 5 prolongation, 6 vector/reduction kernels. */
+int mg_profile_enable(mg_handle *h, int on);
+int mg_profile_read(mg_handle *h, int kind, int level, int prec, int *launches, double *ms);
+
+/* Kernel launches issued by this library in this process so far. */
+unsigned long long mg_launch_count(void);
+
+/* Thread-local message of the last error on this thread ("" if none). */
+const char *mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPMG_H */

@@ -1,0 +1,987 @@
+// Host driver and C ABI of the tensor-product multigrid (see include/tpmg.h).
+//
+// The host side builds the hierarchy's integer structure (conditional
+// semi-coarsening, Section 2.2), carves every device array out of the
+// caller's workspace, and sequences the kernels of tpmg_kernels.cu into
+// V-cycles (Section 2, Fig. 1) and solvers.  It allocates no device memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/tpmg.h"
+#include "tpmg_internal.h"
+
+using namespace tpmg;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(MG_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),      \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+#define CHK(expr)                  \
+    do {                           \
+        int st_ = (expr);          \
+        if (st_ != MG_OK) return st_; \
+    } while (0)
+
+// ------------------------------------------------------------------ hierarchy (host)
+namespace {
+
+struct LinkHost {
+    int nlat_c = 0;
+    std::vector<int> cfirst, ccnt, j0, j1, rptr, rrow;
+    std::vector<double> w0, w1, rw, sy;
+};
+
+struct LevelShape {
+    int nlon, nlat;
+    std::vector<double> south, north;  // row edges (latitude)
+    double centre(int j) const { return 0.5 * (south[j] + north[j]); }
+};
+
+// Conditional semi-coarsening (Section 2.2): longitude halves; in each
+// hemisphere rows are merged in pairs from the equator poleward while the
+// merged cell keeps alpha = cos(theta_c) dlambda_c / dtheta >= alpha_c, and
+// stay single from the first failure on.  The south mirrors the north.
+void coarsen_rows(const LevelShape &f, int nlon_c, double alpha_c, LevelShape &c, LinkHost &K)
+{
+    const int n = f.nlat, half = n / 2;
+    const double dlon_c = 2.0 * M_PI / nlon_c;
+    std::vector<std::pair<int, int>> north;  // (first row, count)
+    int q = half;
+    bool merging = true;
+    while (q < n) {
+        if (merging && q + 1 < n) {
+            const double ths = f.south[q], thn = f.north[q + 1];
+            const double alpha = std::cos(0.5 * (ths + thn)) * dlon_c / (thn - ths);
+            if (alpha >= alpha_c) {
+                north.push_back({q, 2});
+                q += 2;
+                continue;
+            }
+            merging = false;
+        }
+        north.push_back({q, 1});
+        q += 1;
+    }
+    std::vector<std::pair<int, int>> groups;
+    for (auto it = north.rbegin(); it != north.rend(); ++it)
+        groups.push_back({n - 1 - (it->first + it->second - 1), it->second});
+    groups.insert(groups.end(), north.begin(), north.end());
+
+    const int nc = (int)groups.size();
+    c.nlon = nlon_c;
+    c.nlat = nc;
+    c.south.resize(nc);
+    c.north.resize(nc);
+    K.nlat_c = nc;
+    K.cfirst.resize(nc);
+    K.ccnt.resize(nc);
+    std::vector<int> row_of(n);
+    for (int J = 0; J < nc; ++J) {
+        const int g = groups[J].first, cnt = groups[J].second;
+        for (int j = g; j < g + cnt; ++j) row_of[j] = J;
+        c.south[J] = f.south[g];
+        c.north[J] = f.north[g + cnt - 1];
+        K.cfirst[J] = g;
+        K.ccnt[J] = cnt;
+    }
+    // prolongation weights in latitude (linear between coarse row centres)
+    K.j0.assign(n, 0);
+    K.j1.assign(n, -1);
+    K.w0.assign(n, 1.0);
+    K.w1.assign(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        const int J = row_of[j];
+        K.j0[j] = J;
+        const double d = f.centre(j) - c.centre(J);
+        if (d == 0.0) continue;
+        const int Jn = d > 0 ? J + 1 : J - 1;
+        if (Jn < 0 || Jn >= nc) continue;
+        const double w = d / (c.centre(Jn) - c.centre(J));
+        K.j1[j] = Jn;
+        K.w1[j] = w;
+        K.w0[j] = 1.0 - w;
+    }
+    // restriction = transpose, as a per-coarse-row gather list
+    K.rptr.assign(nc + 1, 0);
+    std::vector<std::vector<std::pair<int, double>>> lists(nc);
+    for (int j = 0; j < n; ++j) {
+        lists[K.j0[j]].push_back({j, K.w0[j]});
+        if (K.j1[j] >= 0) lists[K.j1[j]].push_back({j, K.w1[j]});
+    }
+    K.rrow.clear();
+    K.rw.clear();
+    for (int J = 0; J < nc; ++J) {
+        std::sort(lists[J].begin(), lists[J].end());
+        for (auto &pr : lists[J]) {
+            K.rrow.push_back(pr.first);
+            K.rw.push_back(pr.second);
+        }
+        K.rptr[J + 1] = (int)K.rrow.size();
+    }
+    // coarse north-face distance ratio
+    K.sy.assign(nc, 0.0);
+    for (int J = 0; J + 1 < nc; ++J) {
+        const int top = K.cfirst[J] + K.ccnt[J] - 1;
+        K.sy[J] = (f.centre(top + 1) - f.centre(top)) / (c.centre(J + 1) - c.centre(J));
+    }
+}
+
+int auto_levels(int nlon)
+{
+    int L = 1, n = nlon;
+    while (n % 2 == 0 && n / 2 >= 4) {
+        n /= 2;
+        ++L;
+    }
+    return L;
+}
+
+// Bump allocator over the caller's workspace (dry run when base == nullptr).
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base((char *)b) {}
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+struct LevelHost {
+    int nlon = 0, nlat = 0, nz = 0;
+    size_t n = 0;
+    double *tx = nullptr, *ty = nullptr, *tz = nullptr, *h = nullptr, *m = nullptr, *dq = nullptr;
+    float *tx32 = nullptr, *ty32 = nullptr, *tz32 = nullptr, *h32 = nullptr, *m32 = nullptr,
+          *dq32 = nullptr;
+    // V-cycle vectors: rhs, result, ping-pong scratch, residual
+    double *b = nullptr, *u = nullptr, *w = nullptr, *r = nullptr;
+    float *b32 = nullptr, *u32 = nullptr, *w32 = nullptr, *r32 = nullptr;
+    LinkHost link;
+    LinkDev linkdev{};
+};
+
+template <typename T>
+struct CgVecs {
+    T *r = nullptr, *z = nullptr, *d0 = nullptr, *d1 = nullptr, *Ad = nullptr, *x = nullptr;
+};
+
+struct ProfRec {
+    int key;
+    cudaEvent_t a, b;
+};
+
+struct Profiler {
+    bool on = false;
+    bool all_levels = false;
+    std::vector<cudaEvent_t> pool;
+    size_t next = 0;
+    std::vector<ProfRec> recs;
+};
+
+struct mg_handle {
+    Profiler prof;
+    mg_grid grid{};
+    mg_params p{};
+    int L = 0;
+    std::vector<LevelHost> lev;
+    CgVecs<double> cg64;
+    CgVecs<float> cg32;
+    double *partial = nullptr;
+    CgScalars *sc = nullptr;
+    int *flag = nullptr;
+    double scale32 = 0.0;
+};
+
+template <typename T>
+static LevelDev<T> dev(const LevelHost &l);
+template <>
+LevelDev<double> dev<double>(const LevelHost &l)
+{
+    return {l.nlon, l.nlat, l.nz, l.tx, l.ty, l.tz, l.h, l.m, l.dq};
+}
+template <>
+LevelDev<float> dev<float>(const LevelHost &l)
+{
+    return {l.nlon, l.nlat, l.nz, l.tx32, l.ty32, l.tz32, l.h32, l.m32, l.dq32};
+}
+template <typename T>
+struct Vec;
+template <>
+struct Vec<double> {
+    static double *b(LevelHost &l) { return l.b; }
+    static double *u(LevelHost &l) { return l.u; }
+    static double *w(LevelHost &l) { return l.w; }
+    static double *r(LevelHost &l) { return l.r; }
+    static CgVecs<double> &cg(mg_handle *h) { return h->cg64; }
+};
+template <>
+struct Vec<float> {
+    static float *b(LevelHost &l) { return l.b32; }
+    static float *u(LevelHost &l) { return l.u32; }
+    static float *w(LevelHost &l) { return l.w32; }
+    static float *r(LevelHost &l) { return l.r32; }
+    static CgVecs<float> &cg(mg_handle *h) { return h->cg32; }
+};
+
+static std::atomic<unsigned long long> g_launches{0};
+
+enum { K_SMOOTH = 0, K_SMOOTH0 = 1, K_RESID = 2, K_APPLY = 3, K_RESTRICT = 4, K_PROLONG = 5,
+       K_VEC = 6 };
+
+static int prof_key(int kind, int level, int prec) { return (kind * 64 + level) * 2 + prec; }
+
+// Run one launcher (which may issue one kernel); count it and, when
+// profiling is on, bracket it with events on its stream.
+template <typename F>
+static int run_k(mg_handle *H, int kind, int level, int prec, cudaStream_t s, F &&f)
+{
+    Profiler &P = H->prof;
+    const bool rec = P.on && (P.all_levels || level == 0) && P.next + 2 <= P.pool.size();
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (rec) {
+        a = P.pool[P.next++];
+        b = P.pool[P.next++];
+        CU(cudaEventRecord(a, s));
+    }
+    const cudaError_t e = f();
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (e != cudaSuccess)
+        return fail(MG_ERR_CUDA, "kernel launch (kind %d, level %d): %s", kind, level,
+                    cudaGetErrorString(e));
+    if (rec) {
+        CU(cudaEventRecord(b, s));
+        P.recs.push_back({prof_key(kind, level, prec), a, b});
+    }
+    return MG_OK;
+}
+
+static inline cudaError_t to_err(cudaError_t e) { return e != cudaSuccess ? e : cudaGetLastError(); }
+static inline cudaError_t to_err(int) { return cudaGetLastError(); }
+
+#define KRUN(kind, level, prec, expr) \
+    CHK(run_k(H, kind, level, prec, s, [&]() -> cudaError_t { return to_err(expr); }))
+
+template <typename T>
+static constexpr int prec_of() { return sizeof(T) == 8 ? MG_PREC_FP64 : MG_PREC_FP32; }
+
+static int check_grid(const mg_grid *g, const mg_params *p, int *L_out)
+{
+    if (!g || !p) return fail(MG_ERR_ARG, "null grid or params");
+    if (g->nz < 1 || g->nz > MG_MAX_NZ)
+        return fail(MG_ERR_ARG, "nz=%d outside [1, %d]", g->nz, MG_MAX_NZ);
+    if (g->nlat < 2 || g->nlat % 2)
+        return fail(MG_ERR_ARG, "nlat=%d must be even and >= 2", g->nlat);
+    if (g->nlon < 4) return fail(MG_ERR_ARG, "nlon=%d must be >= 4", g->nlon);
+    const int L = p->levels > 0 ? p->levels : auto_levels(g->nlon);
+    if (L > 1 && (g->nlon % (1 << (L - 1)) || (g->nlon >> (L - 1)) < 2))
+        return fail(MG_ERR_ARG, "nlon=%d not divisible by 2^(levels-1) = %d", g->nlon,
+                    1 << (L - 1));
+    if (p->nu1 < 1 || p->nu2 < 0 || p->coarse_iters < 1 || p->maxit < 0 ||
+        !(p->omega > 0.0 && p->omega < 2.0) || (p->method != MG_METHOD_CG &&
+                                                 p->method != MG_METHOD_STATIONARY))
+        return fail(MG_ERR_ARG, "invalid multigrid parameters");
+    if ((size_t)g->nlon * g->nlat > (size_t)kReduceSlots * kBlock)
+        return fail(MG_ERR_ARG, "nlon*nlat=%zu exceeds %zu columns", (size_t)g->nlon * g->nlat,
+                    (size_t)kReduceSlots * kBlock);
+    *L_out = L;
+    return MG_OK;
+}
+
+static void build_shapes(const mg_grid *g, const mg_params *p, int L, std::vector<LevelHost> &lev)
+{
+    lev.assign(L, LevelHost{});
+    LevelShape cur;
+    cur.nlon = g->nlon;
+    cur.nlat = g->nlat;
+    cur.south.resize(g->nlat);
+    cur.north.resize(g->nlat);
+    const double dth = M_PI / g->nlat;
+    for (int j = 0; j < g->nlat; ++j) {
+        cur.south[j] = -0.5 * M_PI + j * dth;
+        cur.north[j] = -0.5 * M_PI + (j + 1) * dth;
+    }
+    cur.south[0] = -0.5 * M_PI;
+    cur.north[g->nlat - 1] = 0.5 * M_PI;
+    for (int l = 0; l < L; ++l) {
+        lev[l].nlon = cur.nlon;
+        lev[l].nlat = cur.nlat;
+        lev[l].nz = g->nz;
+        lev[l].n = (size_t)cur.nlon * cur.nlat * g->nz;
+        if (l + 1 < L) {
+            LevelShape next;
+            coarsen_rows(cur, cur.nlon / 2, p->alpha_c, next, lev[l].link);
+            cur = next;
+        }
+    }
+}
+
+// Lay out every device array; with base == nullptr only sizes are computed.
+static size_t carve(mg_handle *H, void *base)
+{
+    Carver cv(base);
+    const bool mixed = H->p.mixed != 0;
+    for (int l = 0; l < H->L; ++l) {
+        LevelHost &v = H->lev[l];
+        const size_t n = v.n;
+        v.tx = cv.take<double>(n);
+        v.ty = cv.take<double>(n);
+        v.tz = cv.take<double>(n);
+        v.h = cv.take<double>(n);
+        v.m = cv.take<double>(n);
+        v.dq = cv.take<double>(n);
+        v.u = cv.take<double>(n);
+        v.w = cv.take<double>(n);
+        v.r = cv.take<double>(n);
+        if (l > 0) v.b = cv.take<double>(n);
+        if (mixed) {
+            v.tx32 = cv.take<float>(n);
+            v.ty32 = cv.take<float>(n);
+            v.tz32 = cv.take<float>(n);
+            v.h32 = cv.take<float>(n);
+            v.m32 = cv.take<float>(n);
+            v.dq32 = cv.take<float>(n);
+            v.u32 = cv.take<float>(n);
+            v.w32 = cv.take<float>(n);
+            v.r32 = cv.take<float>(n);
+            v.b32 = cv.take<float>(n);  // level 0: right-hand side of the inner solve
+        }
+        if (l + 1 < H->L) {
+            LinkHost &K = v.link;
+            LinkDev &D = v.linkdev;
+            D.nlat_c = K.nlat_c;
+            D.j0 = cv.take<int>(K.j0.size());
+            D.w0 = cv.take<double>(K.w0.size());
+            D.j1 = cv.take<int>(K.j1.size());
+            D.w1 = cv.take<double>(K.w1.size());
+            D.rptr = cv.take<int>(K.rptr.size());
+            D.rrow = cv.take<int>(K.rrow.size());
+            D.rw = cv.take<double>(K.rw.size());
+            D.cfirst = cv.take<int>(K.cfirst.size());
+            D.ccnt = cv.take<int>(K.ccnt.size());
+            D.sy = cv.take<double>(K.sy.size());
+        }
+    }
+    const size_t n0 = H->lev[0].n;
+    H->cg64.r = cv.take<double>(n0);
+    H->cg64.z = cv.take<double>(n0);
+    H->cg64.d0 = cv.take<double>(n0);
+    H->cg64.d1 = cv.take<double>(n0);
+    H->cg64.Ad = cv.take<double>(n0);
+    if (mixed) {
+        H->cg32.r = cv.take<float>(n0);
+        H->cg32.z = cv.take<float>(n0);
+        H->cg32.d0 = cv.take<float>(n0);
+        H->cg32.d1 = cv.take<float>(n0);
+        H->cg32.Ad = cv.take<float>(n0);
+        H->cg32.x = cv.take<float>(n0);
+    }
+    H->partial = cv.take<double>(kReduceSlots);
+    H->sc = cv.take<CgScalars>(1);
+    H->flag = cv.take<int>(4);
+    return cv.off + 256;
+}
+
+// ------------------------------------------------------------------ C ABI: setup
+extern "C" void mg_default_params(mg_params *p)
+{
+    if (!p) return;
+    p->levels = 0;
+    p->nu1 = 1;
+    p->nu2 = 1;
+    p->coarse_iters = 8;
+    p->method = MG_METHOD_CG;
+    p->mixed = 0;
+    p->maxit = 200;
+    p->inner_maxit = 8;
+    p->omega = 0.8;
+    p->alpha_c = 0.5;
+    p->inner_tol = 1e-3;
+}
+
+extern "C" const char *mg_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int mg_workspace_bytes(const mg_grid *grid, const mg_params *params, size_t *bytes)
+{
+    int L = 0;
+    CHK(check_grid(grid, params, &L));
+    if (!bytes) return fail(MG_ERR_ARG, "null bytes");
+    mg_handle tmp;
+    tmp.grid = *grid;
+    tmp.p = *params;
+    tmp.L = L;
+    build_shapes(grid, params, L, tmp.lev);
+    *bytes = carve(&tmp, nullptr);
+    return MG_OK;
+}
+
+template <typename V>
+static int upload(const V &host, const void *dst, cudaStream_t s)
+{
+    if (host.empty()) return MG_OK;
+    CU(cudaMemcpyAsync(const_cast<void *>(dst), host.data(), host.size() * sizeof(host[0]),
+                       cudaMemcpyHostToDevice, s));
+    return MG_OK;
+}
+
+static int read_scalar(mg_handle *H, int which, double *out, cudaStream_t s)
+{
+    CU(cudaMemcpyAsync(out, reinterpret_cast<double *>(H->sc) + which, sizeof(double),
+                       cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return MG_OK;
+}
+
+enum { S_RZ = 0, S_RZNEW = 1, S_DAD = 2, S_RR = 3, S_ALPHA = 4, S_BETA = 5, S_MAX = 6 };
+
+static int device_max(mg_handle *H, const double *a, size_t n, double *out, cudaStream_t s)
+{
+    int nb = 0;
+    KRUN(K_VEC, 0, 0, nb = launch_maxabs<double>(a, n, H->partial, s));
+    KRUN(K_VEC, 0, 0, launch_finalize(H->partial, nb, H->sc, S_MAX, 3, s));
+    return read_scalar(H, S_MAX, out, s);
+}
+
+static int setup_impl(mg_handle *H, const mg_coeffs *co, void *ws, size_t ws_bytes, cudaStream_t s)
+{
+    size_t need = carve(H, nullptr);
+    if (!ws) return fail(MG_ERR_WORKSPACE, "null workspace");
+    if ((uintptr_t)ws % 256) return fail(MG_ERR_WORKSPACE, "workspace not 256-byte aligned");
+    if (ws_bytes < need)
+        return fail(MG_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    carve(H, ws);
+    LevelHost &f = H->lev[0];
+    const size_t bytes0 = f.n * sizeof(double);
+    CU(cudaMemcpyAsync(f.tx, co->tx, bytes0, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(f.ty, co->ty, bytes0, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(f.tz, co->tz, bytes0, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(f.h, co->h, bytes0, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemsetAsync(H->flag, 0, 4 * sizeof(int), s));
+    KRUN(K_VEC, 0, 0, launch_validate(dev<double>(f), H->flag, s));
+    int flag = 0;
+    CU(cudaMemcpyAsync(&flag, H->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (flag)
+        return fail(MG_ERR_COEFF, "invalid coefficients (bits %d: 1 h<=0/non-finite, 2 T<0/"
+                                  "non-finite, 4 non-zero pole or top face)", flag);
+    for (int l = 0; l < H->L; ++l) {
+        LevelHost &v = H->lev[l];
+        if (l + 1 < H->L) {
+            const LinkHost &K = v.link;
+            const LinkDev &D = v.linkdev;
+            CHK(upload(K.j0, D.j0, s));
+            CHK(upload(K.w0, D.w0, s));
+            CHK(upload(K.j1, D.j1, s));
+            CHK(upload(K.w1, D.w1, s));
+            CHK(upload(K.rptr, D.rptr, s));
+            CHK(upload(K.rrow, D.rrow, s));
+            CHK(upload(K.rw, D.rw, s));
+            CHK(upload(K.cfirst, D.cfirst, s));
+            CHK(upload(K.ccnt, D.ccnt, s));
+            CHK(upload(K.sy, D.sy, s));
+            LevelHost &c = H->lev[l + 1];
+            KRUN(K_VEC, l, 0, launch_coarsen(dev<double>(v), D, 0.5, c.tx, c.ty, c.tz, c.h, s));
+        }
+        KRUN(K_VEC, l, 0, launch_column_lu(dev<double>(v), v.m, v.dq, s));
+        // the uploads above read pageable host vectors: finish before they go away
+        CU(cudaStreamSynchronize(s));
+    }
+    if (H->p.mixed) {
+        double big = 0;
+        for (int l = 0; l < H->L; ++l) {
+            const LevelHost &v = H->lev[l];
+            for (const double *a : {v.tx, v.ty, v.tz, v.h}) {
+                double m = 0;
+                CHK(device_max(H, a, v.n, &m, s));
+                big = std::max(big, m);
+            }
+        }
+        if (!(big > 0) || !std::isfinite(big)) return fail(MG_ERR_COEFF, "bad coefficient range");
+        int ex = 0;
+        std::frexp(big, &ex);
+        H->scale32 = std::ldexp(1.0, -ex);
+        for (int l = 0; l < H->L; ++l) {
+            LevelHost &v = H->lev[l];
+            KRUN(K_VEC, l, 1, launch_to_float(v.tx, v.tx32, H->scale32, v.n, s));
+            KRUN(K_VEC, l, 1, launch_to_float(v.ty, v.ty32, H->scale32, v.n, s));
+            KRUN(K_VEC, l, 1, launch_to_float(v.tz, v.tz32, H->scale32, v.n, s));
+            KRUN(K_VEC, l, 1, launch_to_float(v.h, v.h32, H->scale32, v.n, s));
+            KRUN(K_VEC, l, 1, launch_to_float(v.m, v.m32, 1.0 / H->scale32, v.n, s));
+            KRUN(K_VEC, l, 1, launch_to_float(v.dq, v.dq32, 1.0, v.n, s));
+        }
+    }
+    CU(cudaStreamSynchronize(s));
+    return MG_OK;
+}
+
+extern "C" int mg_setup(const mg_grid *grid, const mg_coeffs *coeffs, const mg_params *params,
+                        void *workspace, size_t ws_bytes, void *stream, mg_handle **out)
+{
+    if (!out) return fail(MG_ERR_ARG, "null out");
+    *out = nullptr;
+    int L = 0;
+    CHK(check_grid(grid, params, &L));
+    if (!coeffs || !coeffs->tx || !coeffs->ty || !coeffs->tz || !coeffs->h)
+        return fail(MG_ERR_ARG, "null coefficient pointer");
+    mg_handle *H = new mg_handle;
+    H->grid = *grid;
+    H->p = *params;
+    H->L = L;
+    build_shapes(grid, params, L, H->lev);
+    const int st = setup_impl(H, coeffs, workspace, ws_bytes, (cudaStream_t)stream);
+    if (st != MG_OK) {
+        delete H;
+        return st;
+    }
+    *out = H;
+    return MG_OK;
+}
+
+static void prof_release(mg_handle *H)
+{
+    for (cudaEvent_t e : H->prof.pool) cudaEventDestroy(e);
+    H->prof.pool.clear();
+    H->prof.recs.clear();
+    H->prof.next = 0;
+    H->prof.on = false;
+}
+
+extern "C" void mg_destroy(mg_handle *h)
+{
+    if (!h) return;
+    prof_release(h);
+    delete h;
+}
+
+extern "C" int mg_profile_enable(mg_handle *H, int on)
+{
+    if (!H) return fail(MG_ERR_ARG, "null handle");
+    prof_release(H);
+    if (!on) return MG_OK;
+    const int n = 2 * 16384;
+    H->prof.pool.reserve(n);
+    for (int i = 0; i < n; ++i) {
+        cudaEvent_t e;
+        CU(cudaEventCreate(&e));
+        H->prof.pool.push_back(e);
+    }
+    H->prof.on = true;
+    H->prof.all_levels = on >= 2;
+    return MG_OK;
+}
+
+extern "C" int mg_profile_read(mg_handle *H, int kind, int level, int prec, int *launches, double *ms)
+{
+    if (!H) return fail(MG_ERR_ARG, "null handle");
+    const int key = prof_key(kind, level, prec);
+    int cnt = 0;
+    double tot = 0;
+    for (const ProfRec &r : H->prof.recs) {
+        if (r.key != key) continue;
+        CU(cudaEventSynchronize(r.b));
+        float t = 0;
+        CU(cudaEventElapsedTime(&t, r.a, r.b));
+        tot += t;
+        ++cnt;
+    }
+    if (launches) *launches = cnt;
+    if (ms) *ms = tot;
+    return MG_OK;
+}
+
+extern "C" unsigned long long mg_launch_count(void) { return g_launches.load(); }
+
+// ------------------------------------------------------------------ V-cycle
+// Smoother sweeps from a zero guess, alternating between two buffers so that
+// the last sweep writes `out`.
+template <typename T>
+static int smooth_from_zero(mg_handle *H, int l, const LevelDev<T> &D, const T *b, T *out,
+                            T *scratch, int sweeps, double omega, cudaStream_t s)
+{
+    T *cur = (sweeps % 2 == 1) ? out : scratch;
+    T *oth = (cur == out) ? scratch : out;
+    KRUN(K_SMOOTH0, l, prec_of<T>(), launch_smooth<T>(D, b, nullptr, cur, omega, s));
+    for (int it = 1; it < sweeps; ++it) {
+        KRUN(K_SMOOTH, l, prec_of<T>(), launch_smooth<T>(D, b, cur, oth, omega, s));
+        std::swap(cur, oth);
+    }
+    return MG_OK;
+}
+
+// out = V_l b (zero initial guess).  scratch, rbuf: level-l work vectors.
+template <typename T>
+static int vcycle_level(mg_handle *H, int l, const T *b, T *out, T *scratch, T *rbuf, cudaStream_t s)
+{
+    LevelHost &v = H->lev[l];
+    const LevelDev<T> D = dev<T>(v);
+    const double om = H->p.omega;
+    if (l == H->L - 1)
+        return smooth_from_zero<T>(H, l, D, b, out, scratch, H->p.coarse_iters, om, s);
+    const int writes = H->p.nu1 + H->p.nu2;
+    T *cur = (writes % 2 == 1) ? out : scratch;
+    T *oth = (cur == out) ? scratch : out;
+    constexpr int P = prec_of<T>();
+    KRUN(K_SMOOTH0, l, P, launch_smooth<T>(D, b, nullptr, cur, om, s));
+    for (int it = 1; it < H->p.nu1; ++it) {
+        KRUN(K_SMOOTH, l, P, launch_smooth<T>(D, b, cur, oth, om, s));
+        std::swap(cur, oth);
+    }
+    KRUN(K_RESID, l, P, launch_stencil<T>(D, 1, b, cur, rbuf, nullptr, s));
+    LevelHost &c = H->lev[l + 1];
+    KRUN(K_RESTRICT, l, P, launch_restrict<T>(D, v.linkdev, rbuf, Vec<T>::b(c), s));
+    CHK(vcycle_level<T>(H, l + 1, Vec<T>::b(c), Vec<T>::u(c), Vec<T>::w(c), Vec<T>::r(c), s));
+    KRUN(K_PROLONG, l, P, launch_prolong_add<T>(D, v.linkdev, Vec<T>::u(c), cur, s));
+    for (int it = 0; it < H->p.nu2; ++it) {
+        KRUN(K_SMOOTH, l, P, launch_smooth<T>(D, b, cur, oth, om, s));
+        std::swap(cur, oth);
+    }
+    return MG_OK;
+}
+
+template <typename T>
+static int vcycle_fine(mg_handle *H, const T *r, T *e, cudaStream_t s)
+{
+    LevelHost &f = H->lev[0];
+    return vcycle_level<T>(H, 0, r, e, Vec<T>::w(f), Vec<T>::r(f), s);
+}
+
+// ------------------------------------------------------------------ solvers
+static bool bad(double v) { return !(v == v) || std::isinf(v); }
+
+// Conjugate gradients preconditioned by one V-cycle, or the stationary
+// iteration x <- x + V(b - H x) (Section 2).  Scalars in FP64.
+template <typename T>
+static int solve_impl(mg_handle *H, const T *b, T *x, double tol, int maxit, int method,
+                      std::vector<double> *hist, int *its_out, double *rel_out, cudaStream_t s)
+{
+    LevelHost &f = H->lev[0];
+    const LevelDev<T> D = dev<T>(f);
+    const size_t n = f.n;
+    CgVecs<T> &cg = Vec<T>::cg(H);
+    double bb = 0;
+    {
+        int nb = 0;
+        KRUN(K_VEC, 0, prec_of<T>(), nb = launch_dot<T>(b, b, n, H->partial, s));
+        KRUN(K_VEC, 0, prec_of<T>(), launch_finalize(H->partial, nb, H->sc, S_RR, 0, s));
+        CHK(read_scalar(H, S_RR, &bb, s));
+    }
+    if (bad(bb)) return fail(MG_ERR_NONFINITE, "non-finite right-hand side");
+    const double bn = std::sqrt(bb);
+    constexpr int P = prec_of<T>();
+    int its = 0;
+    double rel = 0, rr0 = -1;
+    auto record = [&](double rr) {
+        rel = bn > 0 ? std::sqrt(rr) / bn : 0.0;
+        if (hist) hist->push_back(rel);
+    };
+    while (true) {
+        int nb = 0;
+        KRUN(K_RESID, 0, P, nb = launch_stencil<T>(D, 1, b, x, cg.r, H->partial, s));
+        KRUN(K_VEC, 0, P, launch_finalize(H->partial, nb, H->sc, S_RR, 0, s));
+        double rr;
+        CHK(read_scalar(H, S_RR, &rr, s));
+        if (bad(rr)) return fail(MG_ERR_NONFINITE, "non-finite residual");
+        if (rr0 < 0) rr0 = rr;
+        record(rr);
+        *its_out = its;
+        *rel_out = rel;
+        if (std::sqrt(rr) <= tol * bn) return MG_OK;
+        if (its >= maxit)
+            return fail(MG_ERR_NOT_CONVERGED, "not converged after %d iterations (rel %.3e)", its,
+                        rel);
+        if (rr > 1e6 * rr0) return fail(MG_ERR_DIVERGED, "residual grew to %.3e", rel);
+        if (method == MG_METHOD_STATIONARY) {
+            CHK(vcycle_fine<T>(H, cg.r, cg.z, s));
+            KRUN(K_VEC, 0, P, launch_add<T>(x, cg.z, n, s));
+            ++its;
+            continue;
+        }
+        CHK(vcycle_fine<T>(H, cg.r, cg.z, s));
+        int nbd = 0;
+        KRUN(K_VEC, 0, P, nbd = launch_dot<T>(cg.r, cg.z, n, H->partial, s));
+        KRUN(K_VEC, 0, P, launch_finalize(H->partial, nbd, H->sc, S_RZ, 0, s));
+        T *d = cg.d0, *dn = cg.d1;
+        KRUN(K_VEC, 0, P, launch_cg_direction<T>(cg.z, nullptr, d, n, H->sc, true, s));
+        while (its < maxit) {
+            ++its;
+            int na = 0, nu = 0;
+            KRUN(K_APPLY, 0, P, na = launch_stencil<T>(D, 0, nullptr, d, cg.Ad, H->partial, s));
+            KRUN(K_VEC, 0, P, launch_finalize(H->partial, na, H->sc, S_DAD, 1, s));
+            KRUN(K_VEC, 0, P, nu = launch_cg_update<T>(x, cg.r, d, cg.Ad, n, H->sc, H->partial, s));
+            KRUN(K_VEC, 0, P, launch_finalize(H->partial, nu, H->sc, S_RR, 0, s));
+            CHK(read_scalar(H, S_RR, &rr, s));
+            if (bad(rr)) return fail(MG_ERR_NONFINITE, "non-finite residual");
+            if (std::sqrt(rr) <= tol * bn || its >= maxit) break;  // confirm with the true residual
+            record(rr);
+            if (rr > 1e6 * rr0) return fail(MG_ERR_DIVERGED, "residual grew to %.3e", rel);
+            CHK(vcycle_fine<T>(H, cg.r, cg.z, s));
+            KRUN(K_VEC, 0, P, nbd = launch_dot<T>(cg.r, cg.z, n, H->partial, s));
+            KRUN(K_VEC, 0, P, launch_finalize(H->partial, nbd, H->sc, S_RZNEW, 2, s));
+            KRUN(K_VEC, 0, P, launch_cg_direction<T>(cg.z, d, dn, n, H->sc, false, s));
+            std::swap(d, dn);
+        }
+    }
+}
+
+static void fill_stats(mg_stats *st, const std::vector<double> &hist, int its, int inner,
+                       double rel)
+{
+    if (!st) return;
+    st->iterations = its;
+    st->inner_iterations = inner;
+    st->rel_res = rel;
+    st->history_len = 0;
+    if (st->history && st->history_cap > 0) {
+        const int m = std::min<int>(st->history_cap, (int)hist.size());
+        std::memcpy(st->history, hist.data(), m * sizeof(double));
+        st->history_len = m;
+    }
+}
+
+extern "C" int mg_solve(mg_handle *H, const double *b, double *x, double tol, mg_stats *st,
+                        void *stream)
+{
+    if (!H || !b || !x) return fail(MG_ERR_ARG, "null argument");
+    if (!(tol >= 0)) return fail(MG_ERR_ARG, "tol must be >= 0");
+    std::vector<double> hist;
+    int its = 0;
+    double rel = 0;
+    const int rc = solve_impl<double>(H, b, x, tol, H->p.maxit, H->p.method, &hist, &its, &rel,
+                                      (cudaStream_t)stream);
+    fill_stats(st, hist, its, 0, rel);
+    return rc;
+}
+
+extern "C" int mg_solve_mixed(mg_handle *H, const double *b, double *x, double tol, mg_stats *st,
+                              void *stream)
+{
+    if (!H || !b || !x) return fail(MG_ERR_ARG, "null argument");
+    if (!H->p.mixed) return fail(MG_ERR_ARG, "handle built without the FP32 hierarchy (mixed=0)");
+    if (!(tol >= 0)) return fail(MG_ERR_ARG, "tol must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelHost &f = H->lev[0];
+    const LevelDev<double> D = dev<double>(f);
+    const size_t n = f.n;
+    std::vector<double> hist;
+    double bb = 0;
+    {
+        int nb = 0;
+        KRUN(K_VEC, 0, 0, nb = launch_dot<double>(b, b, n, H->partial, s));
+        KRUN(K_VEC, 0, 0, launch_finalize(H->partial, nb, H->sc, S_RR, 0, s));
+        CHK(read_scalar(H, S_RR, &bb, s));
+    }
+    if (bad(bb)) return fail(MG_ERR_NONFINITE, "non-finite right-hand side");
+    const double bn = std::sqrt(bb);
+    int outer = 0, inner = 0;
+    double rel = 0, rr0 = -1;
+    int rc = MG_OK;
+    while (true) {
+        int nb = 0;
+        KRUN(K_RESID, 0, 0, nb = launch_stencil<double>(D, 1, b, x, H->cg64.r, H->partial, s));
+        KRUN(K_VEC, 0, 0, launch_finalize(H->partial, nb, H->sc, S_RR, 0, s));
+        double rr;
+        CHK(read_scalar(H, S_RR, &rr, s));
+        if (bad(rr)) {
+            rc = fail(MG_ERR_NONFINITE, "non-finite residual");
+            break;
+        }
+        if (rr0 < 0) rr0 = rr;
+        rel = bn > 0 ? std::sqrt(rr) / bn : 0.0;
+        hist.push_back(rel);
+        if (std::sqrt(rr) <= tol * bn) break;
+        if (outer >= H->p.maxit) {
+            rc = fail(MG_ERR_NOT_CONVERGED, "not converged after %d refinement steps", outer);
+            break;
+        }
+        if (rr > 1e6 * rr0) {
+            rc = fail(MG_ERR_DIVERGED, "residual grew to %.3e", rel);
+            break;
+        }
+        // scale by a power of two (exact) so that FP32 holds the residual at O(1)
+        double mx = 0;
+        CHK(device_max(H, H->cg64.r, n, &mx, s));
+        int ex = 0;
+        std::frexp(mx, &ex);
+        const double sc = std::ldexp(1.0, ex);
+        KRUN(K_VEC, 0, 1, launch_cast_scaled(H->cg64.r, f.b32, 1.0 / sc, n, s));
+        CU(cudaMemsetAsync(H->cg32.x, 0, n * sizeof(float), s));
+        int its_in = 0;
+        double rel_in = 0;
+        const int rin = solve_impl<float>(H, f.b32, H->cg32.x, H->p.inner_tol, H->p.inner_maxit,
+                                          H->p.method, nullptr, &its_in, &rel_in, s);
+        if (rin != MG_OK && rin != MG_ERR_NOT_CONVERGED && rin != MG_ERR_DIVERGED) {
+            rc = rin;
+            break;
+        }
+        inner += its_in;
+        // the FP32 hierarchy holds c H: (c H) e = r / sc  =>  x += c sc e
+        KRUN(K_VEC, 0, 0, launch_update_mixed(x, H->cg32.x, H->scale32 * sc, n, s));
+        ++outer;
+    }
+    fill_stats(st, hist, outer, inner, rel);
+    return rc;
+}
+
+// ------------------------------------------------------------------ C ABI: operators
+extern "C" int mg_apply(mg_handle *H, const double *x, double *y, void *stream)
+{
+    if (!H || !x || !y) return fail(MG_ERR_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    KRUN(K_APPLY, 0, 0, launch_stencil<double>(dev<double>(H->lev[0]), 0, nullptr, x, y, nullptr, s));
+    return MG_OK;
+}
+
+extern "C" int mg_vcycle(mg_handle *H, const double *r, double *e, void *stream)
+{
+    if (!H || !r || !e) return fail(MG_ERR_ARG, "null argument");
+    return vcycle_fine<double>(H, r, e, (cudaStream_t)stream);
+}
+
+extern "C" int mg_coeff_grad(mg_handle *H, const double *lam, const double *x, double *gh,
+                             double *gtx, double *gty, double *gtz, void *stream)
+{
+    if (!H || !lam || !x) return fail(MG_ERR_ARG, "null argument");
+    const mg_grid &g = H->grid;
+    cudaStream_t s = (cudaStream_t)stream;
+    KRUN(K_VEC, 0, 0, launch_coeff_grad(g.nlon, g.nlat, g.nz, lam, x, gh, gtx, gty, gtz, s));
+    return MG_OK;
+}
+
+extern "C" int mg_num_levels(const mg_handle *H) { return H ? H->L : 0; }
+
+extern "C" int mg_level_shape(const mg_handle *H, int level, int *nlon, int *nlat, int *nz)
+{
+    if (!H || level < 0 || level >= H->L) return fail(MG_ERR_ARG, "level out of range");
+    if (nlon) *nlon = H->lev[level].nlon;
+    if (nlat) *nlat = H->lev[level].nlat;
+    if (nz) *nz = H->lev[level].nz;
+    return MG_OK;
+}
+
+extern "C" double mg_fp32_scale(const mg_handle *H) { return H ? H->scale32 : 0.0; }
+
+extern "C" int mg_level_coeffs(mg_handle *H, int level, double *tx, double *ty, double *tz,
+                               double *hh, void *stream)
+{
+    if (!H || level < 0 || level >= H->L) return fail(MG_ERR_ARG, "level out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    const LevelHost &v = H->lev[level];
+    const size_t b = v.n * sizeof(double);
+    if (tx) CU(cudaMemcpyAsync(tx, v.tx, b, cudaMemcpyDeviceToDevice, s));
+    if (ty) CU(cudaMemcpyAsync(ty, v.ty, b, cudaMemcpyDeviceToDevice, s));
+    if (tz) CU(cudaMemcpyAsync(tz, v.tz, b, cudaMemcpyDeviceToDevice, s));
+    if (hh) CU(cudaMemcpyAsync(hh, v.h, b, cudaMemcpyDeviceToDevice, s));
+    return MG_OK;
+}
+
+static int level_check(mg_handle *H, int level, int prec, bool need_coarser)
+{
+    if (!H) return fail(MG_ERR_ARG, "null handle");
+    if (level < 0 || level >= H->L || (need_coarser && level + 1 >= H->L))
+        return fail(MG_ERR_ARG, "level %d out of range", level);
+    if (prec != MG_PREC_FP64 && prec != MG_PREC_FP32) return fail(MG_ERR_ARG, "bad precision");
+    if (prec == MG_PREC_FP32 && !H->p.mixed)
+        return fail(MG_ERR_ARG, "FP32 hierarchy not built (mixed=0)");
+    return MG_OK;
+}
+
+template <typename T>
+static int level_op(mg_handle *H, int level, int op, const void *a, const void *b, void *out,
+                    cudaStream_t s)
+{
+    LevelHost &v = H->lev[level];
+    const LevelDev<T> D = dev<T>(v);
+    constexpr int P = prec_of<T>();
+    switch (op) {
+    case 0:
+        KRUN(K_APPLY, level, P, launch_stencil<T>(D, 0, nullptr, (const T *)a, (T *)out, nullptr, s));
+        return MG_OK;
+    case 1:
+        KRUN(K_RESID, level, P,
+             launch_stencil<T>(D, 1, (const T *)a, (const T *)b, (T *)out, nullptr, s));
+        return MG_OK;
+    case 2:
+        KRUN(b ? K_SMOOTH : K_SMOOTH0, level, P,
+             launch_smooth<T>(D, (const T *)a, (const T *)b, (T *)out, H->p.omega, s));
+        return MG_OK;
+    case 3:
+        KRUN(K_RESTRICT, level, P, launch_restrict<T>(D, v.linkdev, (const T *)a, (T *)out, s));
+        return MG_OK;
+    case 4:
+        KRUN(K_PROLONG, level, P, launch_prolong_add<T>(D, v.linkdev, (const T *)a, (T *)out, s));
+        return MG_OK;
+    }
+    return fail(MG_ERR_ARG, "bad op");
+}
+
+static int level_dispatch(mg_handle *H, int level, int prec, int op, const void *a, const void *b,
+                          void *out, void *stream)
+{
+    CHK(level_check(H, level, prec, op >= 3));
+    if ((op != 2 && !a) || !out || (op == 1 && !b)) return fail(MG_ERR_ARG, "null argument");
+    if (op == 2 && (!a || a == out || b == out)) return fail(MG_ERR_ARG, "bad smoother buffers");
+    if (prec == MG_PREC_FP64) return level_op<double>(H, level, op, a, b, out, (cudaStream_t)stream);
+    return level_op<float>(H, level, op, a, b, out, (cudaStream_t)stream);
+}
+
+extern "C" int mg_level_apply(mg_handle *H, int level, int prec, const void *x, void *y,
+                              void *stream)
+{
+    return level_dispatch(H, level, prec, 0, x, nullptr, y, stream);
+}
+
+extern "C" int mg_level_residual(mg_handle *H, int level, int prec, const void *b, const void *u,
+                                 void *r, void *stream)
+{
+    return level_dispatch(H, level, prec, 1, b, u, r, stream);
+}
+
+extern "C" int mg_level_smooth(mg_handle *H, int level, int prec, const void *b, const void *u_in,
+                               void *u_out, void *stream)
+{
+    return level_dispatch(H, level, prec, 2, b, u_in, u_out, stream);
+}
+
+extern "C" int mg_level_restrict(mg_handle *H, int level, int prec, const void *r, void *bc,
+                                 void *stream)
+{
+    return level_dispatch(H, level, prec, 3, r, nullptr, bc, stream);
+}
+
+extern "C" int mg_level_prolong_add(mg_handle *H, int level, int prec, const void *ec, void *u,
+                                    void *stream)
+{
+    return level_dispatch(H, level, prec, 4, ec, nullptr, u, stream);
+}

@@ -1,0 +1,118 @@
+// Internal interface between the host driver (tpmg_api.cpp) and the CUDA
+// kernels (tpmg_kernels.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tpmg {
+
+// One multigrid level in one precision.  All pointers are device pointers
+// into the caller's workspace, [nz][nlat][nlon] unless noted.
+template <typename T>
+struct LevelDev {
+    int nlon, nlat, nz;
+    const T *tx, *ty, *tz, *h;  // coefficients (FP32 copies are scaled by a power of two)
+    const T *m;                 // 1 / p_k, pivot inverse of the column tridiagonal
+    const T *dq;                // q_k / p_k, p_k = q_k + tz_k (row-sum form of the pivot)
+};
+
+// Links from level l to level l+1 (device arrays, sizes in comments).
+struct LinkDev {
+    int nlat_c;                 // coarse rows
+    const int *j0;              // [nlat]   prolongation: fine row j takes w0*row j0
+    const double *w0;           // [nlat]
+    const int *j1;              // [nlat]   + w1*row j1 (j1 = -1: none)
+    const double *w1;           // [nlat]
+    const int *rptr;            // [nlat_c+1] restriction: coarse row J gathers rows
+    const int *rrow;            //            rrow[rptr[J]..rptr[J+1]) with weights rw
+    const double *rw;
+    const int *cfirst;          // [nlat_c] first fine row of coarse row J
+    const int *ccnt;            // [nlat_c] 1 or 2 fine rows
+    const double *sy;           // [nlat_c] coarse north-face distance ratio
+};
+
+// Device-side scalars of a conjugate-gradient iteration.
+struct CgScalars {
+    double rz, rz_new, dAd, rr, alpha, beta, maxabs, pad;
+};
+
+constexpr int kBlock = 128;          // threads per block, one column per thread
+constexpr int kReduceSlots = 65536;  // per-block partial sums kept in the workspace
+
+// ---- launchers (tpmg_kernels.cu); all asynchronous on `s` -----------------
+// y = H x (mode 0) or y = b - H x (mode 1).  If `partial` != null each block
+// writes sum(y*y) (mode 1) or sum(x*y) (mode 0) to partial[block]; returns
+// the number of blocks written (0 if partial == null).
+template <typename T>
+int launch_stencil(const LevelDev<T> &L, int mode, const T *b, const T *x, T *y,
+                   double *partial, cudaStream_t s);
+
+// One smoother sweep of Eq. (1) in the arrangement
+//   u_out = (1 - omega) u_in + omega H_z^{-1} (b - dH u_in)
+// (u_in == nullptr: zero initial guess).
+template <typename T>
+cudaError_t launch_smooth(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out,
+                          double omega, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_restrict(const LevelDev<T> &F, const LinkDev &K, const T *r, T *bc,
+                            cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_prolong_add(const LevelDev<T> &F, const LinkDev &K, const T *ec, T *u,
+                               cudaStream_t s);
+
+// Sum `n` partials in a fixed order into slots[which]; then (op) update
+// the CG scalars: 0 plain store, 1 alpha = rz / dAd, 2 beta = rz_new / rz
+// and rz = rz_new, 3 max instead of sum.
+cudaError_t launch_finalize(const double *partial, int n, CgScalars *sc, int which, int op,
+                            cudaStream_t s);
+
+// partial dot products: sum(a*b) per block.
+template <typename T>
+int launch_dot(const T *a, const T *b, size_t n, double *partial, cudaStream_t s);
+
+// per-block max |a|
+template <typename T>
+int launch_maxabs(const T *a, size_t n, double *partial, cudaStream_t s);
+
+// x += alpha d; r -= alpha Ad; partial sum(r*r).  alpha from sc->alpha.
+template <typename T>
+int launch_cg_update(T *x, T *r, const T *d, const T *Ad, size_t n, const CgScalars *sc,
+                     double *partial, cudaStream_t s);
+
+// d_out = z + beta d_in (beta from sc->beta; beta_zero: d_out = z).
+template <typename T>
+cudaError_t launch_cg_direction(const T *z, const T *d_in, T *d_out, size_t n,
+                                const CgScalars *sc, bool beta_zero, cudaStream_t s);
+
+// x += e (same precision)
+template <typename T>
+cudaError_t launch_add(T *x, const T *e, size_t n, cudaStream_t s);
+
+// r32 = (float)(r64 * inv_scale)
+cudaError_t launch_cast_scaled(const double *r, float *r32, double inv_scale, size_t n,
+                               cudaStream_t s);
+// x64 += scale * (double)e32
+cudaError_t launch_update_mixed(double *x, const float *e, double scale, size_t n,
+                                cudaStream_t s);
+
+// ---- setup ----
+// Validate fine coefficients; ORs error bits into *flag (device int).
+cudaError_t launch_validate(const LevelDev<double> &L, int *flag, cudaStream_t s);
+// Coarse coefficients of level l+1 from level l (sums; lon faces x sx, lat faces x sy[J]).
+cudaError_t launch_coarsen(const LevelDev<double> &F, const LinkDev &K, double sx, double *txc,
+                           double *tyc, double *tzc, double *hc, cudaStream_t s);
+// Column factors (m, dq) of every column of a level, in FP64.
+cudaError_t launch_column_lu(const LevelDev<double> &L, double *m, double *dq, cudaStream_t s);
+// FP32 copies: out = (float)(scale * in) for coefficients; m32 = (float)(m / scale);
+// dq32 = (float)dq.
+cudaError_t launch_to_float(const double *in, float *out, double scale, size_t n, cudaStream_t s);
+
+// Coefficient gradient (see mg_coeff_grad); outputs may be null.
+cudaError_t launch_coeff_grad(int nlon, int nlat, int nz, const double *lam, const double *x,
+                              double *gh, double *gtx, double *gty, double *gtz, cudaStream_t s);
+
+}  // namespace tpmg

@@ -1,0 +1,639 @@
+// CUDA kernels of the tensor-product multigrid (sm_103a).
+//
+// Data layout: every field is [nz][nlat][nlon], longitude fastest.  One
+// thread owns one vertical column (i, j) and walks k, so at every k the
+// threads of a warp touch consecutive addresses (coalesced, one 128-byte
+// line per warp per array in FP32, two in FP64).  Horizontal neighbours
+// (i +- 1, j +- 1) are re-reads of lines that neighbouring threads of the
+// same or an adjacent block load, served by L1/L2.
+//
+// The path is HBM-bound in FP32 and FP64-ALU-bound in FP64 on GB300
+// (~2 DFMA/clk/SM), so the FP64 kernels minimise FP64 operations: the
+// smoother takes the Jacobi arrangement of Eq. (1) (no vertical fluxes, ~10
+// FP64 ops per cell) and reads precomputed column factors.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tpmg_internal.h"
+
+namespace tpmg {
+
+// ------------------------------------------------------------------ reductions
+template <int OP>  // 0: sum, 1: max
+__device__ __forceinline__ double warp_reduce(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double w = __shfl_down_sync(0xffffffffu, v, o);
+        v = OP == 0 ? v + w : fmax(v, w);
+    }
+    return v;
+}
+
+// Deterministic block reduction; every thread of the block must call it.
+template <int OP>
+__device__ __forceinline__ void block_store(double v, double *partial)
+{
+    __shared__ double ws[32];
+    v = warp_reduce<OP>(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) ws[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+        v = warp_reduce<OP>(v);
+        if (lane == 0) partial[blockIdx.x] = v;
+    }
+}
+
+// ------------------------------------------------------------------ stencil
+// mode 0: y = H x;  mode 1: y = b - H x.  Flux form
+//   (H x)_c = h_c x_c + sum_f T_f (x_c - x_nb(f)).
+template <typename T, int MODE, bool RED>
+__global__ void __launch_bounds__(kBlock)
+k_stencil(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ y,
+          double *__restrict__ partial)
+{
+    const int nlon = L.nlon, nlat = L.nlat, nz = L.nz;
+    const int ncol = nlon * nlat;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    T acc = 0;
+    if (col < ncol) {
+        const int j = col / nlon, i = col - j * nlon;
+        const int ie = (i + 1 == nlon) ? col - i : col + 1;
+        const int iw = (i == 0) ? col + nlon - 1 : col - 1;
+        const bool hasN = j + 1 < nlat, hasS = j > 0;
+        const size_t plane = (size_t)ncol;
+        T xdn = 0, tdn = 0;
+        T xc = x[col];
+        for (int k = 0; k < nz; ++k) {
+            const size_t o = (size_t)k * plane;
+            const T xup = (k + 1 < nz) ? x[o + plane + col] : T(0);
+            const T tup = L.tz[o + col];
+            T v = L.h[o + col] * xc;
+            v = fma(L.tx[o + col], xc - x[o + ie], v);
+            v = fma(L.tx[o + iw], xc - x[o + iw], v);
+            if (hasN) v = fma(L.ty[o + col], xc - x[o + col + nlon], v);
+            if (hasS) v = fma(L.ty[o + col - nlon], xc - x[o + col - nlon], v);
+            v = fma(tup, xc - xup, v);
+            v = fma(tdn, xc - xdn, v);
+            const T out = MODE ? b[o + col] - v : v;
+            y[o + col] = out;
+            if (RED) acc = fma(out, MODE ? out : xc, acc);
+            xdn = xc;
+            xc = xup;
+            tdn = tup;
+        }
+    }
+    if (RED) block_store<0>((double)acc, partial);
+}
+
+template <typename T>
+int launch_stencil(const LevelDev<T> &L, int mode, const T *b, const T *x, T *y, double *partial,
+                   cudaStream_t s)
+{
+    const int ncol = L.nlon * L.nlat;
+    const int grid = (ncol + kBlock - 1) / kBlock;
+    if (partial) {
+        if (mode) k_stencil<T, 1, true><<<grid, kBlock, 0, s>>>(L, b, x, y, partial);
+        else k_stencil<T, 0, true><<<grid, kBlock, 0, s>>>(L, b, x, y, partial);
+        return grid;
+    }
+    if (mode) k_stencil<T, 1, false><<<grid, kBlock, 0, s>>>(L, b, x, y, nullptr);
+    else k_stencil<T, 0, false><<<grid, kBlock, 0, s>>>(L, b, x, y, nullptr);
+    return 0;
+}
+
+// ------------------------------------------------------------------ smoother
+// One sweep of Eq. (1), u_out = (1 - omega) u_in + omega H_z^{-1}(b - dH u_in),
+// with the column tridiagonal H_z (diagonal s_k + t_{k-1} + t_k, couplings
+// -t_k, s_k = h + the four horizontal couplings) solved by elimination with
+// pivots p_k = q_k + t_k:
+//   forward   y_k = (v_k + t_{k-1} y_{k-1}) / p_k
+//   backward  x_k = x_{k+1} + (y_k - (q_k / p_k) x_{k+1})
+// PRE: 1/p_k and q_k/p_k read from the setup factors (FP64, and FP32 zero-guess
+// sweeps); otherwise q_k = s_k + t_{k-1} q_{k-1}/p_{k-1} is formed on the fly
+// (FP32: one reciprocal per cell, cheaper than reading two more arrays).
+// The forward values y (and q/p on the fly) wait in shared memory for the
+// backward sweep: blockDim x nz values per array.
+template <typename T, bool ZERO, bool PRE>
+__global__ void __launch_bounds__(kBlock)
+k_smooth(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ uin, T *__restrict__ uout,
+         T omega)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nlon = L.nlon, nlat = L.nlat, nz = L.nz;
+    const int bd = blockDim.x, tid = threadIdx.x;
+    T *ys = reinterpret_cast<T *>(smraw);
+    T *ds = ys + (size_t)nz * bd;
+    const int ncol = nlon * nlat;
+    const int col = blockIdx.x * bd + tid;
+    if (col >= ncol) return;
+    const int j = col / nlon, i = col - j * nlon;
+    const int ie = (i + 1 == nlon) ? col - i : col + 1;
+    const int iw = (i == 0) ? col + nlon - 1 : col - 1;
+    const bool hasN = j + 1 < nlat, hasS = j > 0;
+    const size_t plane = (size_t)ncol;
+
+    T yprev = 0, tdn = 0, dprev = 0;
+    for (int k = 0; k < nz; ++k) {
+        const size_t o = (size_t)k * plane;
+        T v = b[o + col];
+        if (!ZERO) {
+            v = fma(L.tx[o + col], uin[o + ie], v);
+            v = fma(L.tx[o + iw], uin[o + iw], v);
+            if (hasN) v = fma(L.ty[o + col], uin[o + col + nlon], v);
+            if (hasS) v = fma(L.ty[o + col - nlon], uin[o + col - nlon], v);
+        }
+        const T tup = L.tz[o + col];
+        T y;
+        if (PRE) {
+            y = fma(tdn, yprev, v) * L.m[o + col];
+        } else {
+            T s = L.h[o + col] + L.tx[o + col] + L.tx[o + iw];
+            if (hasN) s += L.ty[o + col];
+            if (hasS) s += L.ty[o + col - nlon];
+            const T q = (k == 0) ? s : fma(tdn, dprev, s);
+            const T inv = T(1) / (q + tup);
+            y = fma(tdn, yprev, v) * inv;
+            dprev = q * inv;
+            ds[(size_t)k * bd + tid] = dprev;
+        }
+        ys[(size_t)k * bd + tid] = y;
+        yprev = y;
+        tdn = tup;
+    }
+    const T om1 = T(1) - omega;
+    T xk = yprev;
+    {
+        const size_t o = (size_t)(nz - 1) * plane + col;
+        uout[o] = ZERO ? omega * xk : fma(om1, uin[o], omega * xk);
+    }
+    for (int k = nz - 2; k >= 0; --k) {
+        const size_t o = (size_t)k * plane + col;
+        const T dqk = PRE ? L.dq[o] : ds[(size_t)k * bd + tid];
+        xk = xk + fma(-dqk, xk, ys[(size_t)k * bd + tid]);
+        uout[o] = ZERO ? omega * xk : fma(om1, uin[o], omega * xk);
+    }
+}
+
+template <typename T, bool ZERO, bool PRE>
+static cudaError_t launch_smooth_impl(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out,
+                                      double omega, cudaStream_t s)
+{
+    const size_t smem = (size_t)L.nz * kBlock * sizeof(T) * (PRE ? 1 : 2);
+    static bool attr_set = false;  // one attribute set per instantiation (per process)
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_smooth<T, ZERO, PRE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int ncol = L.nlon * L.nlat;
+    const int grid = (ncol + kBlock - 1) / kBlock;
+    k_smooth<T, ZERO, PRE><<<grid, kBlock, smem, s>>>(L, b, u_in, u_out, (T)omega);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_smooth(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out, double omega,
+                          cudaStream_t s)
+{
+    if (u_in == nullptr) return launch_smooth_impl<T, true, true>(L, b, u_in, u_out, omega, s);
+    if (sizeof(T) == 8) return launch_smooth_impl<T, false, true>(L, b, u_in, u_out, omega, s);
+    return launch_smooth_impl<T, false, false>(L, b, u_in, u_out, omega, s);
+}
+
+// ------------------------------------------------------------------ transfers
+// Restriction R = P^T as a gather: coarse column (I, J) sums, over the fine
+// rows listed for J with their latitude weights, the fine residuals at
+// longitudes 2I-1, 2I, 2I+1, 2I+2 (mod nlon) with weights 1/4, 3/4, 3/4, 1/4.
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ r, T *__restrict__ bc)
+{
+    const int nf = F.nlon, nc = nf / 2;
+    const int ncol_c = nc * K.nlat_c;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol_c) return;
+    const int J = col / nc, I = col - J * nc;
+    const int i0 = 2 * I, i1 = 2 * I + 1;
+    const int im = (i0 == 0) ? nf - 1 : i0 - 1;
+    const int ip = (i1 + 1 == nf) ? 0 : i1 + 1;
+    const size_t plane_f = (size_t)nf * F.nlat, plane_c = (size_t)ncol_c;
+    const int p0 = K.rptr[J], p1 = K.rptr[J + 1];
+    const T q1 = T(0.25), q3 = T(0.75);
+    for (int k = 0; k < F.nz; ++k) {
+        T acc = 0;
+        for (int p = p0; p < p1; ++p) {
+            const T *row = r + (size_t)k * plane_f + (size_t)K.rrow[p] * nf;
+            const T w = (T)K.rw[p];
+            acc = fma(w, fma(q1, row[im] + row[ip], q3 * (row[i0] + row[i1])), acc);
+        }
+        bc[(size_t)k * plane_c + col] = acc;
+    }
+}
+
+template <typename T>
+cudaError_t launch_restrict(const LevelDev<T> &F, const LinkDev &K, const T *r, T *bc,
+                            cudaStream_t s)
+{
+    const int ncol_c = (F.nlon / 2) * K.nlat_c;
+    k_restrict<T><<<(ncol_c + kBlock - 1) / kBlock, kBlock, 0, s>>>(F, K, r, bc);
+    return cudaGetLastError();
+}
+
+// Bilinear prolongation and correction: fine cell (i, j) adds
+//   sum_a w_a (3/4 e[J_a, i/2] + 1/4 e[J_a, i/2 -+ 1])
+// (the lon neighbour on the side of the fine cell, periodic).
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_prolong_add(LevelDev<T> F, LinkDev K, const T *__restrict__ ec, T *__restrict__ u)
+{
+    const int nf = F.nlon, nc = nf / 2;
+    const int ncol = nf * F.nlat;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol) return;
+    const int j = col / nf, i = col - j * nf;
+    const int I = i >> 1;
+    const int In = (i & 1) ? (I + 1 == nc ? 0 : I + 1) : (I == 0 ? nc - 1 : I - 1);
+    const int Ja = K.j0[j], Jb = K.j1[j];
+    const T wa = (T)K.w0[j], wb = Jb >= 0 ? (T)K.w1[j] : T(0);
+    const int Jb_ = Jb >= 0 ? Jb : Ja;
+    const size_t plane_f = (size_t)ncol, plane_c = (size_t)nc * K.nlat_c;
+    const T q1 = T(0.25), q3 = T(0.75);
+    for (int k = 0; k < F.nz; ++k) {
+        const T *ea = ec + (size_t)k * plane_c + (size_t)Ja * nc;
+        const T *eb = ec + (size_t)k * plane_c + (size_t)Jb_ * nc;
+        T add = wa * fma(q3, ea[I], q1 * ea[In]);
+        if (Jb >= 0) add = fma(wb, fma(q3, eb[I], q1 * eb[In]), add);
+        u[(size_t)k * plane_f + col] += add;
+    }
+}
+
+template <typename T>
+cudaError_t launch_prolong_add(const LevelDev<T> &F, const LinkDev &K, const T *ec, T *u,
+                               cudaStream_t s)
+{
+    const int ncol = F.nlon * F.nlat;
+    k_prolong_add<T><<<(ncol + kBlock - 1) / kBlock, kBlock, 0, s>>>(F, K, ec, u);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ vectors
+static inline int red_grid(size_t n)
+{
+    size_t g = (n + (size_t)kBlock * 8 - 1) / ((size_t)kBlock * 8);
+    if (g < 1) g = 1;
+    if (g > (size_t)kReduceSlots) g = kReduceSlots;
+    return (int)g;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_dot(const T *__restrict__ a, const T *__restrict__ b, size_t n, double *partial)
+{
+    T acc = 0;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+         c += (size_t)gridDim.x * blockDim.x)
+        acc = fma(a[c], b[c], acc);
+    block_store<0>((double)acc, partial);
+}
+
+template <typename T>
+int launch_dot(const T *a, const T *b, size_t n, double *partial, cudaStream_t s)
+{
+    const int g = red_grid(n);
+    k_dot<T><<<g, kBlock, 0, s>>>(a, b, n, partial);
+    return g;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_maxabs(const T *__restrict__ a, size_t n, double *partial)
+{
+    double m = 0;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+         c += (size_t)gridDim.x * blockDim.x) {
+        const double v = fabs((double)a[c]);
+        m = v > m ? v : (v != v ? v : m);  // propagate NaN
+    }
+    block_store<1>(m, partial);
+}
+
+template <typename T>
+int launch_maxabs(const T *a, size_t n, double *partial, cudaStream_t s)
+{
+    const int g = red_grid(n);
+    k_maxabs<T><<<g, kBlock, 0, s>>>(a, n, partial);
+    return g;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_cg_update(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ d, const T *__restrict__ Ad,
+            size_t n, const CgScalars *sc, double *partial)
+{
+    const T alpha = (T)sc->alpha;
+    T acc = 0;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+         c += (size_t)gridDim.x * blockDim.x) {
+        x[c] = fma(alpha, d[c], x[c]);
+        const T rv = fma(-alpha, Ad[c], r[c]);
+        r[c] = rv;
+        acc = fma(rv, rv, acc);
+    }
+    block_store<0>((double)acc, partial);
+}
+
+template <typename T>
+int launch_cg_update(T *x, T *r, const T *d, const T *Ad, size_t n, const CgScalars *sc,
+                     double *partial, cudaStream_t s)
+{
+    const int g = red_grid(n);
+    k_cg_update<T><<<g, kBlock, 0, s>>>(x, r, d, Ad, n, sc, partial);
+    return g;
+}
+
+template <typename T, bool BZ>
+__global__ void __launch_bounds__(kBlock)
+k_cg_direction(const T *__restrict__ z, const T *__restrict__ din, T *__restrict__ dout, size_t n,
+               const CgScalars *sc)
+{
+    const T beta = BZ ? T(0) : (T)sc->beta;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+         c += (size_t)gridDim.x * blockDim.x)
+        dout[c] = BZ ? z[c] : fma(beta, din[c], z[c]);
+}
+
+template <typename T>
+cudaError_t launch_cg_direction(const T *z, const T *d_in, T *d_out, size_t n, const CgScalars *sc,
+                                bool beta_zero, cudaStream_t s)
+{
+    const int g = red_grid(n) * 2;
+    if (beta_zero) k_cg_direction<T, true><<<g, kBlock, 0, s>>>(z, d_in, d_out, n, sc);
+    else k_cg_direction<T, false><<<g, kBlock, 0, s>>>(z, d_in, d_out, n, sc);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_add(T *__restrict__ x, const T *__restrict__ e, size_t n)
+{
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+         c += (size_t)gridDim.x * blockDim.x)
+        x[c] += e[c];
+}
+
+template <typename T>
+cudaError_t launch_add(T *x, const T *e, size_t n, cudaStream_t s)
+{
+    k_add<T><<<red_grid(n) * 2, kBlock, 0, s>>>(x, e, n);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_cast_scaled(const double *__restrict__ r, float *__restrict__ r32, double inv, size_t n)
+{
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+         c += (size_t)gridDim.x * blockDim.x)
+        r32[c] = (float)(r[c] * inv);
+}
+
+cudaError_t launch_cast_scaled(const double *r, float *r32, double inv_scale, size_t n,
+                               cudaStream_t s)
+{
+    k_cast_scaled<<<red_grid(n) * 2, kBlock, 0, s>>>(r, r32, inv_scale, n);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_update_mixed(double *__restrict__ x, const float *__restrict__ e, double scale, size_t n)
+{
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+         c += (size_t)gridDim.x * blockDim.x)
+        x[c] = fma(scale, (double)e[c], x[c]);
+}
+
+cudaError_t launch_update_mixed(double *x, const float *e, double scale, size_t n, cudaStream_t s)
+{
+    k_update_mixed<<<red_grid(n) * 2, kBlock, 0, s>>>(x, e, scale, n);
+    return cudaGetLastError();
+}
+
+// Fixed-order final reduction of per-block partials and the CG scalar update.
+__global__ void __launch_bounds__(1024)
+k_finalize(const double *__restrict__ partial, int n, CgScalars *sc, int which, int op)
+{
+    __shared__ double ws[32];
+    double v = 0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x)
+        v = op == 3 ? (partial[c] > v || partial[c] != partial[c] ? partial[c] : v) : v + partial[c];
+    if (op == 3) v = warp_reduce<1>(v);
+    else v = warp_reduce<0>(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) ws[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+        if (op == 3) v = warp_reduce<1>(v);
+        else v = warp_reduce<0>(v);
+        if (lane == 0) {
+            double *slots = reinterpret_cast<double *>(sc);
+            slots[which] = v;
+            if (op == 1) sc->alpha = sc->rz / v;
+            if (op == 2) {
+                sc->beta = v / sc->rz;
+                sc->rz = v;
+            }
+        }
+    }
+}
+
+cudaError_t launch_finalize(const double *partial, int n, CgScalars *sc, int which, int op,
+                            cudaStream_t s)
+{
+    k_finalize<<<1, 1024, 0, s>>>(partial, n, sc, which, op);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ setup
+// Error bits: 1 h <= 0 or non-finite; 2 T < 0 or non-finite; 4 non-zero pole/top face.
+__global__ void __launch_bounds__(kBlock) k_validate(LevelDev<double> L, int *flag)
+{
+    const size_t n = (size_t)L.nz * L.nlat * L.nlon;
+    const size_t plane = (size_t)L.nlat * L.nlon;
+    int bits = 0;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+         c += (size_t)gridDim.x * blockDim.x) {
+        const double h = L.h[c], tx = L.tx[c], ty = L.ty[c], tz = L.tz[c];
+        if (!(h > 0.0) || !isfinite(h)) bits |= 1;
+        if (!(tx >= 0.0) || !isfinite(tx) || !(ty >= 0.0) || !isfinite(ty) || !(tz >= 0.0) ||
+            !isfinite(tz))
+            bits |= 2;
+        const size_t k = c / plane;
+        const size_t j = (c - k * plane) / L.nlon;
+        if (j + 1 == (size_t)L.nlat && ty != 0.0) bits |= 4;
+        if (k + 1 == (size_t)L.nz && tz != 0.0) bits |= 4;
+    }
+    if (bits) atomicOr(flag, bits);
+}
+
+cudaError_t launch_validate(const LevelDev<double> &L, int *flag, cudaStream_t s)
+{
+    const size_t n = (size_t)L.nz * L.nlat * L.nlon;
+    k_validate<<<red_grid(n), kBlock, 0, s>>>(L, flag);
+    return cudaGetLastError();
+}
+
+// Coarse coefficients (rediscretisation of the same flux form on the coarse
+// cells): h and tz summed over the children; the coarse east face sums the
+// fine east faces of the children at i = 2I+1 (times sx = 1/2, the ratio of
+// the centre distances); the coarse north face sums the north faces of the
+// top child row (times sy[J]); the north-pole face is zero.
+__global__ void __launch_bounds__(kBlock)
+k_coarsen(LevelDev<double> F, LinkDev K, double sx, double *__restrict__ txc,
+          double *__restrict__ tyc, double *__restrict__ tzc, double *__restrict__ hc)
+{
+    const int nf = F.nlon, nc = nf / 2;
+    const int ncol_c = nc * K.nlat_c;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol_c) return;
+    const int J = col / nc, I = col - J * nc;
+    const int j0 = K.cfirst[J], cnt = K.ccnt[J], top = j0 + cnt - 1;
+    const size_t plane_f = (size_t)nf * F.nlat, plane_c = (size_t)ncol_c;
+    for (int k = 0; k < F.nz; ++k) {
+        const size_t of = (size_t)k * plane_f;
+        double hs = 0, zs = 0, xs = 0;
+        for (int j = j0; j <= top; ++j) {
+            const size_t a = of + (size_t)j * nf + 2 * I;
+            hs += F.h[a];
+            hs += F.h[a + 1];
+            zs += F.tz[a];
+            zs += F.tz[a + 1];
+            xs += F.tx[a + 1];
+        }
+        const size_t t = of + (size_t)top * nf + 2 * I;
+        double ys = 0;
+        ys += F.ty[t];
+        ys += F.ty[t + 1];
+        const size_t oc = (size_t)k * plane_c + col;
+        hc[oc] = hs;
+        tzc[oc] = zs;
+        txc[oc] = xs * sx;
+        tyc[oc] = (J == K.nlat_c - 1) ? 0.0 : ys * K.sy[J];
+    }
+}
+
+cudaError_t launch_coarsen(const LevelDev<double> &F, const LinkDev &K, double sx, double *txc,
+                           double *tyc, double *tzc, double *hc, cudaStream_t s)
+{
+    const int ncol_c = (F.nlon / 2) * K.nlat_c;
+    k_coarsen<<<(ncol_c + kBlock - 1) / kBlock, kBlock, 0, s>>>(F, K, sx, txc, tyc, tzc, hc);
+    return cudaGetLastError();
+}
+
+// Column factors: q_0 = s_0, q_k = s_k + t_{k-1} q_{k-1} / p_{k-1}, p_k = q_k + t_k;
+// store m = 1/p and dq = q/p.
+__global__ void __launch_bounds__(kBlock)
+k_column_lu(LevelDev<double> L, double *__restrict__ m, double *__restrict__ dq)
+{
+    const int nlon = L.nlon, nlat = L.nlat;
+    const int ncol = nlon * nlat;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol) return;
+    const int j = col / nlon, i = col - j * nlon;
+    const int iw = (i == 0) ? col + nlon - 1 : col - 1;
+    const size_t plane = (size_t)ncol;
+    double qp = 0, pp = 1, tdn = 0;
+    for (int k = 0; k < L.nz; ++k) {
+        const size_t o = (size_t)k * plane;
+        double s = L.h[o + col] + L.tx[o + col] + L.tx[o + iw] + L.ty[o + col];
+        if (j > 0) s += L.ty[o + col - nlon];
+        const double q = (k == 0) ? s : s + tdn * qp / pp;
+        const double tup = L.tz[o + col];
+        const double p = q + tup;
+        m[o + col] = 1.0 / p;
+        dq[o + col] = q / p;
+        qp = q;
+        pp = p;
+        tdn = tup;
+    }
+}
+
+cudaError_t launch_column_lu(const LevelDev<double> &L, double *m, double *dq, cudaStream_t s)
+{
+    const int ncol = L.nlon * L.nlat;
+    k_column_lu<<<(ncol + kBlock - 1) / kBlock, kBlock, 0, s>>>(L, m, dq);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_to_float(const double *__restrict__ in, float *__restrict__ out, double scale, size_t n)
+{
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+         c += (size_t)gridDim.x * blockDim.x)
+        out[c] = (float)(in[c] * scale);
+}
+
+cudaError_t launch_to_float(const double *in, float *out, double scale, size_t n, cudaStream_t s)
+{
+    k_to_float<<<red_grid(n) * 2, kBlock, 0, s>>>(in, out, scale, n);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ gradient
+__global__ void __launch_bounds__(kBlock)
+k_coeff_grad(int nlon, int nlat, int nz, const double *__restrict__ lam,
+             const double *__restrict__ x, double *gh, double *gtx, double *gty, double *gtz)
+{
+    const int ncol = nlon * nlat;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol) return;
+    const int j = col / nlon, i = col - j * nlon;
+    const int ie = (i + 1 == nlon) ? col - i : col + 1;
+    const size_t plane = (size_t)ncol;
+    for (int k = 0; k < nz; ++k) {
+        const size_t o = (size_t)k * plane + col;
+        const double l = lam[o], xv = x[o];
+        if (gh) gh[o] = -l * xv;
+        if (gtx) {
+            const size_t e = (size_t)k * plane + ie;
+            gtx[o] = -(l - lam[e]) * (xv - x[e]);
+        }
+        if (gty) gty[o] = (j + 1 < nlat) ? -(l - lam[o + nlon]) * (xv - x[o + nlon]) : 0.0;
+        if (gtz) gtz[o] = (k + 1 < nz) ? -(l - lam[o + plane]) * (xv - x[o + plane]) : 0.0;
+    }
+}
+
+cudaError_t launch_coeff_grad(int nlon, int nlat, int nz, const double *lam, const double *x,
+                              double *gh, double *gtx, double *gty, double *gtz, cudaStream_t s)
+{
+    const int ncol = nlon * nlat;
+    k_coeff_grad<<<(ncol + kBlock - 1) / kBlock, kBlock, 0, s>>>(nlon, nlat, nz, lam, x, gh, gtx,
+                                                                gty, gtz);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ instantiations
+#define TPMG_INST(T)                                                                              \
+    template int launch_stencil<T>(const LevelDev<T> &, int, const T *, const T *, T *, double *, \
+                                   cudaStream_t);                                                 \
+    template cudaError_t launch_smooth<T>(const LevelDev<T> &, const T *, const T *, T *, double,  \
+                                          cudaStream_t);                                          \
+    template cudaError_t launch_restrict<T>(const LevelDev<T> &, const LinkDev &, const T *, T *,  \
+                                            cudaStream_t);                                        \
+    template cudaError_t launch_prolong_add<T>(const LevelDev<T> &, const LinkDev &, const T *,    \
+                                               T *, cudaStream_t);                                \
+    template int launch_dot<T>(const T *, const T *, size_t, double *, cudaStream_t);             \
+    template int launch_maxabs<T>(const T *, size_t, double *, cudaStream_t);                     \
+    template int launch_cg_update<T>(T *, T *, const T *, const T *, size_t, const CgScalars *,    \
+                                     double *, cudaStream_t);                                     \
+    template cudaError_t launch_cg_direction<T>(const T *, const T *, T *, size_t,                \
+                                                const CgScalars *, bool, cudaStream_t);           \
+    template cudaError_t launch_add<T>(T *, const T *, size_t, cudaStream_t);
+
+TPMG_INST(double)
+TPMG_INST(float)
+
+}  // namespace tpmg

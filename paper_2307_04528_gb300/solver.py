@@ -1,0 +1,198 @@
+"""Python face of libtpmg: a handle over the C ABI and the differentiable solve.
+
+Torch provides device memory (the workspace and the fields) and the current
+CUDA stream; every numerical step runs in libtpmg's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _field(t, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name}: need contiguous {dtype} {tuple(shape)}, got "
+                         f"{t.dtype} {tuple(t.shape)}")
+    return t
+
+
+class MGHandle:
+    """Multigrid hierarchy for H u = b on an [nz, nlat, nlon] lat-lon grid.
+
+    tx, ty, tz, h: CUDA float64 tensors (copied into the workspace at setup).
+    params: keyword overrides of mg_params (levels, nu1, nu2, coarse_iters,
+    method, mixed, maxit, inner_maxit, omega, alpha_c, inner_tol).
+    """
+
+    def __init__(self, tx, ty, tz, h, stream=None, **params):
+        self.lib = L.load()
+        nz, nlat, nlon = h.shape
+        self.shape = (nz, nlat, nlon)
+        for name, t in (("tx", tx), ("ty", ty), ("tz", tz), ("h", h)):
+            _field(t, torch.float64, self.shape, name)
+        self.device = h.device
+        self.grid = L.mg_grid(nlon, nlat, nz)
+        self.params = L.default_params(**params)
+        nbytes = ctypes.c_size_t(0)
+        L.check(self.lib.mg_workspace_bytes(ctypes.byref(self.grid), ctypes.byref(self.params),
+                                            ctypes.byref(nbytes)))
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        co = L.mg_coeffs(tx.data_ptr(), ty.data_ptr(), tz.data_ptr(), h.data_ptr())
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            L.check(self.lib.mg_setup(ctypes.byref(self.grid), ctypes.byref(co),
+                                      ctypes.byref(self.params), _ptr(self.workspace),
+                                      nbytes, _stream(stream), ctypes.byref(self._h)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self.lib.mg_destroy(h)
+            self._h = None
+
+    # ------------------------------------------------------------- queries
+    @property
+    def num_levels(self) -> int:
+        return int(self.lib.mg_num_levels(self._h))
+
+    def level_shape(self, level: int):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        L.check(self.lib.mg_level_shape(self._h, level, ctypes.byref(a), ctypes.byref(b),
+                                        ctypes.byref(c)))
+        return (c.value, b.value, a.value)
+
+    def level_coeffs(self, level: int):
+        shp = self.level_shape(level)
+        out = [torch.empty(shp, dtype=torch.float64, device=self.device) for _ in range(4)]
+        L.check(self.lib.mg_level_coeffs(self._h, level, *map(_ptr, out), _stream()))
+        return out
+
+    @property
+    def fp32_scale(self) -> float:
+        return float(self.lib.mg_fp32_scale(self._h))
+
+    # ------------------------------------------------------------- fine level
+    def apply(self, x, y=None):
+        _field(x, torch.float64, self.shape, "x")
+        y = torch.empty_like(x) if y is None else y
+        L.check(self.lib.mg_apply(self._h, _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def vcycle(self, r, e=None):
+        _field(r, torch.float64, self.shape, "r")
+        e = torch.empty_like(r) if e is None else e
+        L.check(self.lib.mg_vcycle(self._h, _ptr(r), _ptr(e), _stream()))
+        return e
+
+    def _solve(self, fn, b, x, tol, history_cap, raise_on):
+        _field(b, torch.float64, self.shape, "b")
+        x = torch.zeros_like(b) if x is None else x
+        _field(x, torch.float64, self.shape, "x")
+        hist = (ctypes.c_double * history_cap)()
+        st = L.mg_stats(0, 0, 0.0, hist, history_cap, 0)
+        status = fn(self._h, _ptr(b), _ptr(x), float(tol), ctypes.byref(st), _stream())
+        if raise_on:
+            L.check(status)
+        info = dict(status=status, iterations=st.iterations, inner_iterations=st.inner_iterations,
+                    rel_res=st.rel_res, history=[hist[i] for i in range(st.history_len)])
+        return x, info
+
+    def solve(self, b, x=None, tol=1e-10, history_cap=512, raise_on_error=True):
+        """FP64 multigrid solve; x is the initial guess and is overwritten."""
+        return self._solve(self.lib.mg_solve, b, x, tol, history_cap, raise_on_error)
+
+    def solve_mixed(self, b, x=None, tol=1e-10, history_cap=512, raise_on_error=True):
+        """FP32 multigrid inside FP64 refinement (needs mixed=1 at setup)."""
+        return self._solve(self.lib.mg_solve_mixed, b, x, tol, history_cap, raise_on_error)
+
+    def coeff_grad(self, lam, x):
+        outs = [torch.empty_like(x) for _ in range(4)]
+        L.check(self.lib.mg_coeff_grad(self._h, _ptr(lam), _ptr(x), *map(_ptr, outs), _stream()))
+        return tuple(outs)  # gh, gtx, gty, gtz
+
+    # ------------------------------------------------------------- measurement
+    def profile(self, on: bool = True):
+        L.check(self.lib.mg_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, kind: int, level: int, prec: int):
+        n, ms = ctypes.c_int(0), ctypes.c_double(0.0)
+        L.check(self.lib.mg_profile_read(self._h, kind, level, prec, ctypes.byref(n),
+                                         ctypes.byref(ms)))
+        return n.value, ms.value
+
+    # ------------------------------------------------------------- per level
+    def _dt(self, prec):
+        return torch.float64 if prec == L.MG_PREC_FP64 else torch.float32
+
+    def level_apply(self, level, x, prec=L.MG_PREC_FP64):
+        y = torch.empty_like(x)
+        L.check(self.lib.mg_level_apply(self._h, level, prec, _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def level_residual(self, level, b, u, prec=L.MG_PREC_FP64):
+        r = torch.empty_like(b)
+        L.check(self.lib.mg_level_residual(self._h, level, prec, _ptr(b), _ptr(u), _ptr(r),
+                                           _stream()))
+        return r
+
+    def level_smooth(self, level, b, u_in=None, prec=L.MG_PREC_FP64):
+        out = torch.empty_like(b)
+        L.check(self.lib.mg_level_smooth(self._h, level, prec, _ptr(b), _ptr(u_in), _ptr(out),
+                                         _stream()))
+        return out
+
+    def level_restrict(self, level, r, prec=L.MG_PREC_FP64):
+        shp = self.level_shape(level + 1)
+        bc = torch.empty(shp, dtype=r.dtype, device=r.device)
+        L.check(self.lib.mg_level_restrict(self._h, level, prec, _ptr(r), _ptr(bc), _stream()))
+        return bc
+
+    def level_prolong_add(self, level, ec, u, prec=L.MG_PREC_FP64):
+        L.check(self.lib.mg_level_prolong_add(self._h, level, prec, _ptr(ec), _ptr(u), _stream()))
+        return u
+
+
+class MGSolveFn(torch.autograd.Function):
+    """x = H(h, tx, ty, tz)^{-1} b as a differentiable function.
+
+    Backward solves the adjoint system H^T lambda = dL/dx with the same
+    hierarchy (H is symmetric: each face couples its two cells with one
+    coefficient, so the transposed stencil is the stencil) and forms the
+    coefficient gradient with one fused kernel; only the solution x is kept
+    from the forward pass, no iterate."""
+
+    @staticmethod
+    def forward(ctx, b, h, tx, ty, tz, tol=1e-12, params=None):
+        params = dict(params or {})
+        handle = MGHandle(tx.detach().contiguous(), ty.detach().contiguous(),
+                          tz.detach().contiguous(), h.detach().contiguous(), **params)
+        x, _ = handle.solve(b.detach().contiguous(), tol=tol)
+        ctx.handle = handle
+        ctx.tol = tol
+        ctx.save_for_backward(x)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        lam, _ = ctx.handle.solve(gx.contiguous(), tol=ctx.tol)
+        gh, gtx, gty, gtz = ctx.handle.coeff_grad(lam, x)
+        return lam, gh, gtx, gty, gtz, None, None
+
+
+def mg_solve_fn(b, h, tx, ty, tz, tol=1e-12, **params):
+    return MGSolveFn.apply(b, h, tx, ty, tz, tol, params)

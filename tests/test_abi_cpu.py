@@ -1,0 +1,88 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every
+function include/tpmg.h declares, and its host-only entry points (parameter
+defaults, workspace sizing, argument validation) behave without a GPU."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tpmg.h")
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and
+                                not os.path.exists(os.path.join(
+                                    ROOT, "paper_2307_04528_gb300", "_lib", "libtpmg.so")),
+                                reason="needs nvcc or a built libtpmg.so")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2307_04528_gb300 import build
+    from paper_2307_04528_gb300 import _lib as L
+    build.build()
+    return L.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mg_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 18
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_params(lib):
+    from paper_2307_04528_gb300 import _lib as L
+    p = L.default_params()
+    assert (p.levels, p.nu1, p.nu2, p.coarse_iters, p.method, p.mixed) == (0, 1, 1, 8, 0, 0)
+    assert p.omega == 0.8 and p.alpha_c == 0.5 and p.maxit == 200
+
+
+def _bytes(lib, nlon, nlat, nz, **kw):
+    from paper_2307_04528_gb300 import _lib as L
+    g = L.mg_grid(nlon, nlat, nz)
+    p = L.default_params(**kw)
+    n = ctypes.c_size_t(0)
+    st = lib.mg_workspace_bytes(ctypes.byref(g), ctypes.byref(p), ctypes.byref(n))
+    return st, n.value
+
+
+def test_workspace_sizing(lib):
+    st, n1 = _bytes(lib, 64, 32, 16)
+    assert st == 0 and n1 > 64 * 32 * 16 * 8 * 10
+    st, n2 = _bytes(lib, 64, 32, 16, mixed=1)
+    assert st == 0 and n2 > n1
+    st, n3 = _bytes(lib, 1536, 1152, 70, mixed=1)
+    assert st == 0
+    # about 200 B per fine cell with the FP32 hierarchy, under 30 GB
+    cells = 1536 * 1152 * 70
+    assert 150 * cells < n3 < 30e9
+
+
+@pytest.mark.parametrize("shape,kw", [((64, 31, 16), {}),        # odd nlat
+                                      ((2, 32, 16), {}),         # nlon < 4
+                                      ((64, 32, 0), {}),         # nz < 1
+                                      ((64, 32, 300), {}),       # nz > MG_MAX_NZ
+                                      ((48, 32, 4), {"levels": 6}),  # 48 not divisible by 32
+                                      ((64, 32, 4), {"omega": 2.5}),
+                                      ((64, 32, 4), {"nu1": 0})])
+def test_bad_arguments_rejected_on_host(lib, shape, kw):
+    st, _ = _bytes(lib, *shape, **kw)
+    assert st == 1
+    assert lib.mg_last_error()
+
+
+def test_level_counts_follow_nlon(lib):
+    from paper_2307_04528_gb300 import _lib as L
+    # nlon 1536 = 3 * 2^9 -> coarsest nlon 6 after 8 halvings: 9 levels
+    st, _ = _bytes(lib, 1536, 1152, 70)
+    assert st == 0
+    st, _ = _bytes(lib, 1536, 1152, 70, levels=4)
+    assert st == 0

@@ -1,0 +1,155 @@
+"""GPU (libtpmg through its C ABI) vs the CPU oracle, element by element.
+
+Tolerances: FP64 operator apply, residual, smoother sweep and transfers 1e-13
+relative (max norm); a V-cycle 1e-12 (a composition of ~20 such steps);
+converged FP64 and mixed-precision solutions 1e-10 relative 2-norm error.
+FP32 kernels against the oracle's float instance: 2e-5 relative (rounding
+order in single precision).  Integer structure (row maps, level shapes) and
+the coarse coefficients (same summation order on both sides) are exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import dev, handle_for, host, oracle_levels, problem, rel_2, rel_inf
+from oracle import tpmg as O
+
+pytestmark = pytest.mark.gpu
+
+# several column tiles of 128 threads and a ragged tail; odd level counts
+SHAPES = [(64, 32, 16), (96, 46, 9), (24, 10, 5), (256, 128, 12)]
+
+
+@pytest.fixture(scope="module", params=SHAPES, ids=lambda s: "x".join(map(str, s)))
+def case(request):
+    P = problem(*request.param, sigma=0.2, seed=sum(request.param))
+    lev, p = oracle_levels(P)
+    H = handle_for(P)
+    return P, lev, p, H
+
+
+def test_hierarchy_shapes_and_coarse_coefficients_exact(case):
+    P, lev, p, H = case
+    assert H.num_levels == len(lev)
+    for l, ol in enumerate(lev):
+        assert H.level_shape(l) == ol.shape
+        got = [host(t) for t in H.level_coeffs(l)]
+        for g, want in zip(got, ol.coeffs()):
+            assert np.array_equal(g, want)
+
+
+def test_apply_and_residual_fp64(case):
+    P, lev, p, H = case
+    rng = np.random.default_rng(1)
+    for l, ol in enumerate(lev):
+        x = rng.standard_normal(ol.shape)
+        b = rng.standard_normal(ol.shape)
+        y = host(H.level_apply(l, dev(x)))
+        assert rel_inf(y, O.apply(ol, x)) <= 1e-13
+        r = host(H.level_residual(l, dev(b), dev(x)))
+        assert rel_inf(r, O.residual(ol, b, x)) <= 1e-13
+    y0 = host(H.apply(dev(lev[0].h * 0 + 1.0)))
+    assert np.array_equal(y0, P["h"])  # H 1 = h exactly
+
+
+def test_smoother_fp64(case):
+    P, lev, p, H = case
+    rng = np.random.default_rng(2)
+    for l, ol in enumerate(lev):
+        b = rng.standard_normal(ol.shape)
+        u = rng.standard_normal(ol.shape)
+        got0 = host(H.level_smooth(l, dev(b)))
+        ref0 = np.zeros(ol.shape)
+        O.smooth(ol, b, ref0, p.omega)
+        assert rel_inf(got0, ref0) <= 1e-13
+        got = host(H.level_smooth(l, dev(b), dev(u)))
+        ref = u.copy()
+        O.smooth(ol, b, ref, p.omega)
+        assert rel_inf(got, ref) <= 1e-13
+
+
+def test_transfers_fp64(case):
+    P, lev, p, H = case
+    rng = np.random.default_rng(3)
+    for l in range(len(lev) - 1):
+        f, c = lev[l], lev[l + 1]
+        r = rng.standard_normal(f.shape)
+        assert rel_inf(host(H.level_restrict(l, dev(r))), O.restrict(f, r)) <= 1e-13
+        e = rng.standard_normal(c.shape)
+        u = rng.standard_normal(f.shape)
+        ref = u.copy()
+        O.prolong_add(f, e, ref)
+        assert rel_inf(host(H.level_prolong_add(l, dev(e), dev(u))), ref) <= 1e-13
+
+
+def test_fp32_kernels(case):
+    P, lev, p, H = case
+    l32 = O.float_levels(lev)
+    assert H.fp32_scale == l32[0].scale
+    rng = np.random.default_rng(4)
+    f32 = lambda a: dev(a, torch.float32)
+    for l, ol in enumerate(l32):
+        x = rng.standard_normal(ol.shape).astype(np.float32)
+        b = rng.standard_normal(ol.shape).astype(np.float32)
+        assert rel_inf(host(H.level_apply(l, f32(x), prec=1)), O.apply(ol, x)) <= 2e-5
+        ref = x.copy()
+        O.smooth(ol, b, ref, np.float32(p.omega))
+        assert rel_inf(host(H.level_smooth(l, f32(b), f32(x), prec=1)), ref) <= 2e-5
+        ref0 = np.zeros_like(x)
+        O.smooth(ol, b, ref0, np.float32(p.omega))
+        assert rel_inf(host(H.level_smooth(l, f32(b), prec=1)), ref0) <= 2e-5
+        if l + 1 < len(l32):
+            assert rel_inf(host(H.level_restrict(l, f32(x), prec=1)), O.restrict(ol, x)) <= 2e-5
+
+
+def test_vcycle_fp64(case):
+    P, lev, p, H = case
+    rng = np.random.default_rng(5)
+    r = rng.standard_normal(lev[0].shape)
+    assert rel_inf(host(H.vcycle(dev(r))), O.vcycle(lev, r, p)) <= 1e-12
+
+
+@pytest.mark.parametrize("method", ["cg", "stationary"])
+def test_solve_fp64_matches_oracle(method):
+    P = problem(64, 32, 16, sigma=0.1, seed=1000)
+    lev, p = oracle_levels(P, method=method)
+    H = handle_for(P, method=0 if method == "cg" else 1)
+    xr, hr, sr = O.solve(lev, P["b"], 1e-11, params=p)
+    x, info = H.solve(dev(P["b"]), tol=1e-11)
+    assert sr == O.OK and info["status"] == 0
+    assert info["rel_res"] <= 1e-11
+    assert abs(len(info["history"]) - len(hr)) <= 1
+    assert rel_2(host(x), xr) <= 1e-10
+    # the residual the library reports is the oracle's residual of its x
+    assert O.norm2(O.residual(lev[0], P["b"], host(x))) / O.norm2(P["b"]) <= 1.5e-11
+
+
+def test_solve_mixed_matches_fp64_oracle():
+    P = problem(64, 32, 16, sigma=0.1, seed=1000)
+    lev, p = oracle_levels(P)
+    H = handle_for(P)
+    xr, _, _ = O.solve(lev, P["b"], 1e-12, params=p)
+    x, info = H.solve_mixed(dev(P["b"]), tol=1e-11)
+    assert info["status"] == 0 and info["rel_res"] <= 1e-11
+    assert rel_2(host(x), xr) <= 1e-10
+    xo, ho, so = O.solve_mixed(lev, P["b"], 1e-11, params=p)
+    assert so == O.OK
+    assert abs(len(info["history"]) - len(ho)) <= 2
+
+
+def test_degenerate_single_layer_and_two_rows():
+    for shape in [(16, 2, 3), (32, 8, 1)]:
+        P = problem(*shape, sigma=0.1, seed=3)
+        lev, p = oracle_levels(P)
+        H = handle_for(P)
+        x, info = H.solve(dev(P["b"]), tol=1e-10)
+        xr, _, _ = O.solve(lev, P["b"], 1e-10, params=p)
+        assert info["status"] == 0
+        assert rel_2(host(x), xr) <= 1e-9
+
+
+def test_zero_rhs_gives_zero():
+    P = problem(16, 8, 4)
+    H = handle_for(P)
+    x, info = H.solve(torch.zeros(P["h"].shape, dtype=torch.float64, device="cuda"))
+    assert info["status"] == 0 and float(x.abs().max()) == 0.0
