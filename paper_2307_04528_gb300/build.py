@@ -63,7 +63,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for src in HOST_SOURCES:
         obj = os.path.join(BUILD, src + ".o")
         objs.append(obj)
-        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", "-I" + INCLUDE,
+        jobs.append(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-Wall",
+                     "-I" + INCLUDE,
                      "-I" + os.path.join(cuda, "include"), "-c", os.path.join(CSRC, src),
                      "-o", obj])
 
