@@ -167,6 +167,34 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- GPU arm
+# algorithmic words moved per fine cell by each fine-level kernel class
+# (reads + writes of distinct arrays; horizontal neighbours counted once)
+KERNEL_WORDS = {
+    # (kind, prec): (name, words per cell)
+    (0, 1): ("smooth fp32 (on-the-fly pivots)", 7),   # u b tx ty tz h -> u
+    (1, 1): ("smooth fp32 zero guess", 5),            # b tz m dq -> u
+    (2, 1): ("residual fp32", 7),                     # u b tx ty tz h -> r
+    (3, 1): ("apply fp32", 6),                        # x tx ty tz h -> y
+    (0, 0): ("smooth fp64", 8),                       # u b tx ty tz m dq -> u
+    (1, 0): ("smooth fp64 zero guess", 5),
+    (2, 0): ("residual fp64", 7),
+    (3, 0): ("apply fp64", 6),
+}
+
+
+def kernel_table(H, L, N):
+    rows = []
+    for (kind, prec), (name, words) in KERNEL_WORDS.items():
+        n, ms = H.profile_read(kind, 0, prec)
+        if n == 0:
+            continue
+        avg = ms / n
+        nbytes = words * (4 if prec == 1 else 8) * N
+        rows.append({"kernel": name, "launches": n, "avg_ms": round(avg, 4),
+                     "alg_bytes": nbytes, "gbs": round(nbytes / (avg * 1e-3) / 1e9, 1)})
+    return rows
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -243,6 +271,7 @@ def run_ours(args):
     ms_prof, _ = timed(mixed_step, args.steps)
     sm_calls, sm_ms = H.profile_read(L.K_SMOOTH, 0, L.MG_PREC_FP32)
     res_calls, res_ms = H.profile_read(L.K_RESID, 0, L.MG_PREC_FP64)
+    kernels = kernel_table(H, L, N)
     H.profile(False)
     ms_prof = max_over_ranks(ms_prof / args.steps)
 
@@ -298,6 +327,7 @@ def run_ours(args):
                    "levels": H.num_levels, "setup_ms": setup_ms,
                    "fp64_residual_kernel_avg_ms": res_avg},
         "gpu_launches": int(launches),
+        "kernels_fine_level": kernels,
         "clocks": clk,
         "roofline": roofline,
     }

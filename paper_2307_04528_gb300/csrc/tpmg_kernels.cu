@@ -117,6 +117,41 @@ int launch_stencil(const LevelDev<T> &L, int mode, const T *b, const T *x, T *y,
 // (FP32: one reciprocal per cell, cheaper than reading two more arrays).
 // The forward values y (and q/p on the fly) wait in shared memory for the
 // backward sweep: blockDim x nz values per array.
+//
+// Shared memory caps residency at ~3 blocks of 128 columns per SM, so the
+// loads of layers k+1..k+kDepth are issued before layer k is computed (a
+// register pipeline) to keep enough bytes in flight to cover HBM latency.
+constexpr int kDepth = 3;
+
+template <typename T>
+struct SmoothLoads {
+    T b, tz, m, h, txc, txw, tyn, tys, ue, uw, un, us;
+};
+
+template <typename T, bool ZERO, bool PRE>
+__device__ __forceinline__ void smooth_load(SmoothLoads<T> &s, const LevelDev<T> &L,
+                                            const T *__restrict__ b, const T *__restrict__ uin,
+                                            size_t o, int col, int ie, int iw, int nlon, bool hasN,
+                                            bool hasS)
+{
+    s.b = __ldg(b + o + col);
+    s.tz = __ldg(L.tz + o + col);
+    if (PRE) s.m = __ldg(L.m + o + col);
+    if (!PRE) s.h = __ldg(L.h + o + col);
+    if (!ZERO || !PRE) {
+        s.txc = __ldg(L.tx + o + col);
+        s.txw = __ldg(L.tx + o + iw);
+        s.tyn = hasN ? __ldg(L.ty + o + col) : T(0);
+        s.tys = hasS ? __ldg(L.ty + o + col - nlon) : T(0);
+    }
+    if (!ZERO) {
+        s.ue = __ldg(uin + o + ie);
+        s.uw = __ldg(uin + o + iw);
+        s.un = hasN ? __ldg(uin + o + col + nlon) : T(0);
+        s.us = hasS ? __ldg(uin + o + col - nlon) : T(0);
+    }
+}
+
 template <typename T, bool ZERO, bool PRE>
 __global__ void __launch_bounds__(kBlock)
 k_smooth(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ uin, T *__restrict__ uout,
@@ -136,45 +171,81 @@ k_smooth(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ uin, T *_
     const bool hasN = j + 1 < nlat, hasS = j > 0;
     const size_t plane = (size_t)ncol;
 
+    SmoothLoads<T> st[kDepth];
+#pragma unroll
+    for (int d = 0; d < kDepth; ++d)
+        if (d < nz)
+            smooth_load<T, ZERO, PRE>(st[d], L, b, uin, (size_t)d * plane, col, ie, iw, nlon,
+                                      hasN, hasS);
+
     T yprev = 0, tdn = 0, dprev = 0;
-    for (int k = 0; k < nz; ++k) {
-        const size_t o = (size_t)k * plane;
-        T v = b[o + col];
-        if (!ZERO) {
-            v = fma(L.tx[o + col], uin[o + ie], v);
-            v = fma(L.tx[o + iw], uin[o + iw], v);
-            if (hasN) v = fma(L.ty[o + col], uin[o + col + nlon], v);
-            if (hasS) v = fma(L.ty[o + col - nlon], uin[o + col - nlon], v);
+    for (int k0 = 0; k0 < nz; k0 += kDepth) {
+#pragma unroll
+        for (int d = 0; d < kDepth; ++d) {
+            const int k = k0 + d;
+            if (k < nz) {
+                SmoothLoads<T> &c = st[d];
+                T v = c.b;
+                if (!ZERO) {
+                    v = fma(c.txc, c.ue, v);
+                    v = fma(c.txw, c.uw, v);
+                    v = fma(c.tyn, c.un, v);
+                    v = fma(c.tys, c.us, v);
+                }
+                const T tup = c.tz;
+                T y;
+                if (PRE) {
+                    y = fma(tdn, yprev, v) * c.m;
+                } else {
+                    const T s = c.h + c.txc + c.txw + c.tyn + c.tys;
+                    const T q = (k == 0) ? s : fma(tdn, dprev, s);
+                    const T inv = T(1) / (q + tup);
+                    y = fma(tdn, yprev, v) * inv;
+                    dprev = q * inv;
+                    ds[(size_t)k * bd + tid] = dprev;
+                }
+                ys[(size_t)k * bd + tid] = y;
+                yprev = y;
+                tdn = tup;
+                if (k + kDepth < nz)
+                    smooth_load<T, ZERO, PRE>(c, L, b, uin, (size_t)(k + kDepth) * plane, col, ie,
+                                              iw, nlon, hasN, hasS);
+            }
         }
-        const T tup = L.tz[o + col];
-        T y;
-        if (PRE) {
-            y = fma(tdn, yprev, v) * L.m[o + col];
-        } else {
-            T s = L.h[o + col] + L.tx[o + col] + L.tx[o + iw];
-            if (hasN) s += L.ty[o + col];
-            if (hasS) s += L.ty[o + col - nlon];
-            const T q = (k == 0) ? s : fma(tdn, dprev, s);
-            const T inv = T(1) / (q + tup);
-            y = fma(tdn, yprev, v) * inv;
-            dprev = q * inv;
-            ds[(size_t)k * bd + tid] = dprev;
-        }
-        ys[(size_t)k * bd + tid] = y;
-        yprev = y;
-        tdn = tup;
     }
+
     const T om1 = T(1) - omega;
     T xk = yprev;
-    {
-        const size_t o = (size_t)(nz - 1) * plane + col;
-        uout[o] = ZERO ? omega * xk : fma(om1, uin[o], omega * xk);
+    // backward sweep: prefetch u_in (and the precomputed q/p) kDepth layers ahead
+    T up[kDepth], dqp[kDepth];
+#pragma unroll
+    for (int d = 0; d < kDepth; ++d) {
+        const int k = nz - 1 - d;
+        if (k >= 0) {
+            const size_t o = (size_t)k * plane + col;
+            up[d] = ZERO ? T(0) : __ldg(uin + o);
+            dqp[d] = PRE ? __ldg(L.dq + o) : T(0);
+        }
     }
-    for (int k = nz - 2; k >= 0; --k) {
-        const size_t o = (size_t)k * plane + col;
-        const T dqk = PRE ? L.dq[o] : ds[(size_t)k * bd + tid];
-        xk = xk + fma(-dqk, xk, ys[(size_t)k * bd + tid]);
-        uout[o] = ZERO ? omega * xk : fma(om1, uin[o], omega * xk);
+    for (int k0 = nz - 1; k0 >= 0; k0 -= kDepth) {
+#pragma unroll
+        for (int d = 0; d < kDepth; ++d) {
+            const int k = k0 - d;
+            if (k >= 0) {
+                const size_t o = (size_t)k * plane + col;
+                if (k < nz - 1) {
+                    const T dqk = PRE ? dqp[d] : ds[(size_t)k * bd + tid];
+                    xk = xk + fma(-dqk, xk, ys[(size_t)k * bd + tid]);
+                }
+                uout[o] = ZERO ? omega * xk : fma(om1, up[d], omega * xk);
+                const int kn = k - kDepth;
+                if (kn >= 0) {
+                    const size_t on = (size_t)kn * plane + col;
+                    if (!ZERO) up[d] = __ldg(uin + on);
+                    if (PRE) dqp[d] = __ldg(L.dq + on);
+                }
+            }
+        }
     }
 }
 
