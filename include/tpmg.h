@@ -194,6 +194,25 @@ double mg_fp32_scale(const mg_handle *h);
 int mg_profile_enable(mg_handle *h, int on);
 int mg_profile_read(mg_handle *h, int kind, int level, int prec, int *launches, double *ms);
 
+/* Residual without any device allocation.  Computes r = b - H x on the fine
+ * grid given directly by `coeffs` (no handle, no workspace) and returns
+ * *rel_out = ||r||_2 / ||b||_2 (||r||_2 if b = 0) on the host.  The paper
+ * has no counterpart: this exists for callers that cannot allocate device
+ * memory when they need the check -- a forecast model that owns every
+ * device buffer through its own pool and forbids further cudaMalloc, or C
+ * or Fortran host code with no device allocator for a workspace.
+ * The reduction scratch is a file-scope __device__ array of 256 KB that
+ * every GPU loading the library keeps until exit; grids with more than
+ * 16384 * 128 = 2,097,152 columns (nlon * nlat) are rejected (MG_ERR_ARG).
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and leave their partial sums in it: calls that
+ * overlap on the GPU (other streams, other host threads) race.  Calls
+ * cudaMalloc/cudaFree never.  b, x, r: device FP64 fields; rel_out: host.
+ * Synchronises `stream`. */
+int mg_residual_norm_noalloc(const mg_grid *grid, const mg_coeffs *coeffs, const double *b,
+                             const double *x, double *r, double *rel_out, void *stream);
+
 /* Kernel launches issued by this library in this process so far. */
 unsigned long long mg_launch_count(void);
 

@@ -91,6 +91,8 @@ def load() -> ctypes.CDLL:
         "mg_profile_enable": (I, [H, I]),
         "mg_profile_read": (I, [H, I, I, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "mg_launch_count": (ctypes.c_ulonglong, []),
+        "mg_residual_norm_noalloc": (I, [ctypes.POINTER(mg_grid), ctypes.POINTER(mg_coeffs), P, P,
+                                         P, ctypes.POINTER(D), P]),
         "mg_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():

@@ -34,6 +34,8 @@ static int fail(int code, const char *fmt, ...)
     return code;
 }
 
+void tpmg::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
 #define CU(call)                                                                          \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \

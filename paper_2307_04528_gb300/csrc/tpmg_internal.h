@@ -115,4 +115,7 @@ cudaError_t launch_to_float(const double *in, float *out, double scale, size_t n
 cudaError_t launch_coeff_grad(int nlon, int nlat, int nz, const double *lam, const double *x,
                               double *gh, double *gtx, double *gty, double *gtz, cudaStream_t s);
 
+// Set the thread-local message mg_last_error() returns.
+void set_last_error(const char *msg);
+
 }  // namespace tpmg
