@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--workload", default="latlon_1536x1152x70")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-out", default=None,
+                    help="write per-(kernel, level, precision) event times of the profiled "
+                         "repeat to this JSON file")
     return ap.parse_args()
 
 
@@ -171,7 +174,7 @@ def run_reference(args):
 # (reads + writes of distinct arrays; horizontal neighbours counted once)
 KERNEL_WORDS = {
     # (kind, prec): (name, words per cell)
-    (0, 1): ("smooth fp32 (on-the-fly pivots)", 7),   # u b tx ty tz h -> u
+    (0, 1): ("smooth fp32", 8),                       # u b tx ty tz m dq -> u
     (1, 1): ("smooth fp32 zero guess", 5),            # b tz m dq -> u
     (2, 1): ("residual fp32", 7),                     # u b tx ty tz h -> r
     (3, 1): ("apply fp32", 6),                        # x tx ty tz h -> y
@@ -266,12 +269,25 @@ def run_ours(args):
     clk = clocks.stop()
     ms_mixed = max_over_ranks(ms_mixed / args.steps)
     info_m = infos[-1]
-    # the same timed steps again with CUDA events around every fine-level launch
-    H.profile(True)
+    # the same timed steps again with CUDA events around every launch
+    H.profile(2 if args.profile_out else 1)
     ms_prof, _ = timed(mixed_step, args.steps)
     sm_calls, sm_ms = H.profile_read(L.K_SMOOTH, 0, L.MG_PREC_FP32)
     res_calls, res_ms = H.profile_read(L.K_RESID, 0, L.MG_PREC_FP64)
     kernels = kernel_table(H, L, N)
+    if args.profile_out:
+        full = []
+        for lvl in range(H.num_levels):
+            for kind in range(7):
+                for prec in (0, 1):
+                    n, ms = H.profile_read(kind, lvl, prec)
+                    if n:
+                        full.append({"kind": kind, "level": lvl, "prec": prec, "launches": n,
+                                     "total_ms": ms, "avg_us": 1e3 * ms / n,
+                                     "shape": H.level_shape(lvl)})
+        with open(args.profile_out, "w") as f:
+            json.dump({"steps": args.steps, "ms_per_step_profiled": None, "rows": full}, f,
+                      indent=1)
     H.profile(False)
     ms_prof = max_over_ranks(ms_prof / args.steps)
 
@@ -299,8 +315,8 @@ def run_ours(args):
                "d2h_bytes_per_step": int(hx.numel() * 8)}
 
     peak, peak_kind = load_peaks()
-    # FP32 smoother sweep, algorithmic bytes: reads u, b, tx, ty, tz, h; writes u (7 x 4 B)
-    sm_bytes = 28 * N
+    # FP32 smoother sweep, algorithmic bytes: reads u, b, tx, ty, tz, m, dq; writes u (8 x 4 B)
+    sm_bytes = 32 * N
     sm_avg_ms = sm_ms / max(sm_calls, 1)
     achieved = sm_bytes / (sm_avg_ms * 1e-3) / 1e9 if sm_calls else None
     roofline = {"kernel": "k_smooth<float> fine level (non-zero guess)", "bound": "hbm",

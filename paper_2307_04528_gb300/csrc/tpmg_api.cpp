@@ -213,8 +213,20 @@ struct Profiler {
     std::vector<ProfRec> recs;
 };
 
+// A V-cycle captured once as a CUDA graph (fixed input/output vectors of
+// the solver), replayed on the caller's stream.
+struct VGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long kernels = 0;  // kernel nodes, for the launch count
+};
+
 struct mg_handle {
     Profiler prof;
+    cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+    bool capturing = false;
+    bool use_graphs = true;
+    VGraph vg[2];                       // [MG_PREC_FP64], [MG_PREC_FP32]
     mg_grid grid{};
     mg_params p{};
     int L = 0;
@@ -279,7 +291,8 @@ static int run_k(mg_handle *H, int kind, int level, int prec, cudaStream_t s, F 
         CU(cudaEventRecord(a, s));
     }
     const cudaError_t e = f();
-    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (H->capturing) ++H->vg[prec].kernels;
+    else g_launches.fetch_add(1, std::memory_order_relaxed);
     if (e != cudaSuccess)
         return fail(MG_ERR_CUDA, "kernel launch (kind %d, level %d): %s", kind, level,
                     cudaGetErrorString(e));
@@ -484,6 +497,8 @@ static int setup_impl(mg_handle *H, const mg_coeffs *co, void *ws, size_t ws_byt
     if (ws_bytes < need)
         return fail(MG_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, need);
     carve(H, ws);
+    CU(smooth_prepare());
+    CU(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
     LevelHost &f = H->lev[0];
     const size_t bytes0 = f.n * sizeof(double);
     CU(cudaMemcpyAsync(f.tx, co->tx, bytes0, cudaMemcpyDeviceToDevice, s));
@@ -580,10 +595,21 @@ static void prof_release(mg_handle *H)
     H->prof.on = false;
 }
 
+static void graphs_release(mg_handle *H)
+{
+    for (VGraph &g : H->vg) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+        g = VGraph{};
+    }
+}
+
 extern "C" void mg_destroy(mg_handle *h)
 {
     if (!h) return;
     prof_release(h);
+    graphs_release(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
 
@@ -679,6 +705,45 @@ static int vcycle_fine(mg_handle *H, const T *r, T *e, cudaStream_t s)
     return vcycle_level<T>(H, 0, r, e, Vec<T>::w(f), Vec<T>::r(f), s);
 }
 
+// z = V r for the solver's fixed vectors (cg.r -> cg.z), replayed from a CUDA
+// graph captured on first use; direct launches while profiling (events
+// around each kernel) or if capture is unavailable.
+template <typename T>
+static int vcycle_solver(mg_handle *H, cudaStream_t s)
+{
+    CgVecs<T> &cg = Vec<T>::cg(H);
+    constexpr int P = prec_of<T>();
+    if (!H->use_graphs || H->prof.on) return vcycle_fine<T>(H, cg.r, cg.z, s);
+    VGraph &g = H->vg[P];
+    if (!g.exec) {
+        g.kernels = 0;
+        CU(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
+        H->capturing = true;
+        const int st = vcycle_fine<T>(H, cg.r, cg.z, H->cap_stream);
+        H->capturing = false;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(H->cap_stream, &graph);
+        if (st != MG_OK || ec != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            H->use_graphs = false;  // run the same kernels without a graph from now on
+            return vcycle_fine<T>(H, cg.r, cg.z, s);
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (ei != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            cudaGetLastError();
+            g = VGraph{};
+            H->use_graphs = false;
+            return vcycle_fine<T>(H, cg.r, cg.z, s);
+        }
+        g.graph = graph;
+    }
+    CU(cudaGraphLaunch(g.exec, s));
+    g_launches.fetch_add(g.kernels, std::memory_order_relaxed);
+    return MG_OK;
+}
+
 // ------------------------------------------------------------------ solvers
 static bool bad(double v) { return !(v == v) || std::isinf(v); }
 
@@ -725,12 +790,12 @@ static int solve_impl(mg_handle *H, const T *b, T *x, double tol, int maxit, int
                         rel);
         if (rr > 1e6 * rr0) return fail(MG_ERR_DIVERGED, "residual grew to %.3e", rel);
         if (method == MG_METHOD_STATIONARY) {
-            CHK(vcycle_fine<T>(H, cg.r, cg.z, s));
+            CHK(vcycle_solver<T>(H, s));
             KRUN(K_VEC, 0, P, launch_add<T>(x, cg.z, n, s));
             ++its;
             continue;
         }
-        CHK(vcycle_fine<T>(H, cg.r, cg.z, s));
+        CHK(vcycle_solver<T>(H, s));
         int nbd = 0;
         KRUN(K_VEC, 0, P, nbd = launch_dot<T>(cg.r, cg.z, n, H->partial, s));
         KRUN(K_VEC, 0, P, launch_finalize(H->partial, nbd, H->sc, S_RZ, 0, s));
@@ -748,7 +813,7 @@ static int solve_impl(mg_handle *H, const T *b, T *x, double tol, int maxit, int
             if (std::sqrt(rr) <= tol * bn || its >= maxit) break;  // confirm with the true residual
             record(rr);
             if (rr > 1e6 * rr0) return fail(MG_ERR_DIVERGED, "residual grew to %.3e", rel);
-            CHK(vcycle_fine<T>(H, cg.r, cg.z, s));
+            CHK(vcycle_solver<T>(H, s));
             KRUN(K_VEC, 0, P, nbd = launch_dot<T>(cg.r, cg.z, n, H->partial, s));
             KRUN(K_VEC, 0, P, launch_finalize(H->partial, nbd, H->sc, S_RZNEW, 2, s));
             KRUN(K_VEC, 0, P, launch_cg_direction<T>(cg.z, d, dn, n, H->sc, false, s));

@@ -56,6 +56,10 @@ template <typename T>
 cudaError_t launch_smooth(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out,
                           double omega, cudaStream_t s);
 
+// Raise the dynamic shared-memory limit of the smoother kernels (once per
+// process and device, before any stream capture).
+cudaError_t smooth_prepare();
+
 template <typename T>
 cudaError_t launch_restrict(const LevelDev<T> &F, const LinkDev &K, const T *r, T *bc,
                             cudaStream_t s);

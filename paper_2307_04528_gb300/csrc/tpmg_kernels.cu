@@ -89,12 +89,48 @@ k_stencil(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ x, T *__
     if (RED) block_store<0>((double)acc, partial);
 }
 
+// Cell-parallel variant (one thread per cell, grid = column blocks x layers)
+// for levels with too few columns to fill the GPU with column loops.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kBlock)
+k_stencil_cells(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ y)
+{
+    const int nlon = L.nlon, nlat = L.nlat, nz = L.nz;
+    const int ncol = nlon * nlat;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (col >= ncol) return;
+    const int j = col / nlon, i = col - j * nlon;
+    const int ie = (i + 1 == nlon) ? col - i : col + 1;
+    const int iw = (i == 0) ? col + nlon - 1 : col - 1;
+    const size_t plane = (size_t)ncol;
+    const size_t o = (size_t)k * plane;
+    const T xc = __ldg(x + o + col);
+    T v = __ldg(L.h + o + col) * xc;
+    v = fma(__ldg(L.tx + o + col), xc - __ldg(x + o + ie), v);
+    v = fma(__ldg(L.tx + o + iw), xc - __ldg(x + o + iw), v);
+    if (j + 1 < nlat) v = fma(__ldg(L.ty + o + col), xc - __ldg(x + o + col + nlon), v);
+    if (j > 0) v = fma(__ldg(L.ty + o + col - nlon), xc - __ldg(x + o + col - nlon), v);
+    if (k + 1 < nz) v = fma(__ldg(L.tz + o + col), xc - __ldg(x + o + plane + col), v);
+    if (k > 0) v = fma(__ldg(L.tz + o - plane + col), xc - __ldg(x + o - plane + col), v);
+    y[o + col] = MODE ? __ldg(b + o + col) - v : v;
+}
+
+// below this many columns the column loops cannot fill the GPU
+constexpr int kCellParallelColumns = 32768;
+
 template <typename T>
 int launch_stencil(const LevelDev<T> &L, int mode, const T *b, const T *x, T *y, double *partial,
                    cudaStream_t s)
 {
     const int ncol = L.nlon * L.nlat;
     const int grid = (ncol + kBlock - 1) / kBlock;
+    if (!partial && ncol < kCellParallelColumns) {
+        const dim3 g2(grid, L.nz);
+        if (mode) k_stencil_cells<T, 1><<<g2, kBlock, 0, s>>>(L, b, x, y);
+        else k_stencil_cells<T, 0><<<g2, kBlock, 0, s>>>(L, b, x, y);
+        return 0;
+    }
     if (partial) {
         if (mode) k_stencil<T, 1, true><<<grid, kBlock, 0, s>>>(L, b, x, y, partial);
         else k_stencil<T, 0, true><<<grid, kBlock, 0, s>>>(L, b, x, y, partial);
@@ -119,9 +155,14 @@ int launch_stencil(const LevelDev<T> &L, int mode, const T *b, const T *x, T *y,
 // backward sweep: blockDim x nz values per array.
 //
 // Shared memory caps residency at ~3 blocks of 128 columns per SM, so the
-// loads of layers k+1..k+kDepth are issued before layer k is computed (a
-// register pipeline) to keep enough bytes in flight to cover HBM latency.
-constexpr int kDepth = 3;
+// loads of layers k+1..k+DEPTH are issued before layer k is computed (a
+// register pipeline) to keep enough bytes in flight to cover HBM latency:
+// deeper for the FP32 sweeps (few registers per layer, HBM-bound), shallow
+// for FP64 (FP64-ALU-bound, twice the registers per value).
+template <typename T, bool ZERO>
+struct SmoothDepth {
+    static constexpr int value = sizeof(T) == 8 ? (ZERO ? 4 : 3) : (ZERO ? 4 : 6);
+};
 
 template <typename T>
 struct SmoothLoads {
@@ -157,6 +198,7 @@ __global__ void __launch_bounds__(kBlock)
 k_smooth(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ uin, T *__restrict__ uout,
          T omega)
 {
+    constexpr int kDepth = SmoothDepth<T, ZERO>::value;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nlon = L.nlon, nlat = L.nlat, nz = L.nz;
     const int bd = blockDim.x, tid = threadIdx.x;
@@ -254,14 +296,6 @@ static cudaError_t launch_smooth_impl(const LevelDev<T> &L, const T *b, const T 
                                       double omega, cudaStream_t s)
 {
     const size_t smem = (size_t)L.nz * kBlock * sizeof(T) * (PRE ? 1 : 2);
-    static bool attr_set = false;  // one attribute set per instantiation (per process)
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_smooth<T, ZERO, PRE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
     const int ncol = L.nlon * L.nlat;
     const int grid = (ncol + kBlock - 1) / kBlock;
     k_smooth<T, ZERO, PRE><<<grid, kBlock, smem, s>>>(L, b, u_in, u_out, (T)omega);
@@ -273,14 +307,33 @@ cudaError_t launch_smooth(const LevelDev<T> &L, const T *b, const T *u_in, T *u_
                           cudaStream_t s)
 {
     if (u_in == nullptr) return launch_smooth_impl<T, true, true>(L, b, u_in, u_out, omega, s);
-    if (sizeof(T) == 8) return launch_smooth_impl<T, false, true>(L, b, u_in, u_out, omega, s);
-    return launch_smooth_impl<T, false, false>(L, b, u_in, u_out, omega, s);
+    return launch_smooth_impl<T, false, true>(L, b, u_in, u_out, omega, s);
+}
+
+// Set the dynamic shared-memory limit of every smoother instantiation (must
+// precede stream capture).
+cudaError_t smooth_prepare()
+{
+    const int lim = 200 * 1024;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_smooth<double, true, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_smooth<double, false, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_smooth<float, true, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_smooth<float, false, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 // ------------------------------------------------------------------ transfers
-// Restriction R = P^T as a gather: coarse column (I, J) sums, over the fine
-// rows listed for J with their latitude weights, the fine residuals at
-// longitudes 2I-1, 2I, 2I+1, 2I+2 (mod nlon) with weights 1/4, 3/4, 3/4, 1/4.
+// Restriction R = P^T as a gather, one thread per coarse cell (grid: coarse
+// column blocks x layers): coarse (I, J, k) sums, over the fine rows listed
+// for J with their latitude weights, the fine residuals at longitudes 2I-1,
+// 2I, 2I+1, 2I+2 (mod nlon) with weights 1/4, 3/4, 3/4, 1/4.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ r, T *__restrict__ bc)
@@ -288,23 +341,24 @@ k_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ r, T *__restrict__ bc
     const int nf = F.nlon, nc = nf / 2;
     const int ncol_c = nc * K.nlat_c;
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
     if (col >= ncol_c) return;
     const int J = col / nc, I = col - J * nc;
     const int i0 = 2 * I, i1 = 2 * I + 1;
     const int im = (i0 == 0) ? nf - 1 : i0 - 1;
     const int ip = (i1 + 1 == nf) ? 0 : i1 + 1;
     const size_t plane_f = (size_t)nf * F.nlat, plane_c = (size_t)ncol_c;
-    const int p0 = K.rptr[J], p1 = K.rptr[J + 1];
+    const int p0 = __ldg(K.rptr + J), p1 = __ldg(K.rptr + J + 1);
     const T q1 = T(0.25), q3 = T(0.75);
-    for (int k = 0; k < F.nz; ++k) {
-        T acc = 0;
-        for (int p = p0; p < p1; ++p) {
-            const T *row = r + (size_t)k * plane_f + (size_t)K.rrow[p] * nf;
-            const T w = (T)K.rw[p];
-            acc = fma(w, fma(q1, row[im] + row[ip], q3 * (row[i0] + row[i1])), acc);
-        }
-        bc[(size_t)k * plane_c + col] = acc;
+    const T *rk = r + (size_t)k * plane_f;
+    T acc = 0;
+    for (int p = p0; p < p1; ++p) {
+        const T *row = rk + (size_t)__ldg(K.rrow + p) * nf;
+        const T w = (T)__ldg(K.rw + p);
+        acc = fma(w, fma(q1, __ldg(row + im) + __ldg(row + ip), q3 * (__ldg(row + i0) + __ldg(row + i1))),
+                  acc);
     }
+    bc[(size_t)k * plane_c + col] = acc;
 }
 
 template <typename T>
@@ -312,44 +366,55 @@ cudaError_t launch_restrict(const LevelDev<T> &F, const LinkDev &K, const T *r, 
                             cudaStream_t s)
 {
     const int ncol_c = (F.nlon / 2) * K.nlat_c;
-    k_restrict<T><<<(ncol_c + kBlock - 1) / kBlock, kBlock, 0, s>>>(F, K, r, bc);
+    const dim3 grid((ncol_c + kBlock - 1) / kBlock, F.nz);
+    k_restrict<T><<<grid, kBlock, 0, s>>>(F, K, r, bc);
     return cudaGetLastError();
 }
 
-// Bilinear prolongation and correction: fine cell (i, j) adds
-//   sum_a w_a (3/4 e[J_a, i/2] + 1/4 e[J_a, i/2 -+ 1])
-// (the lon neighbour on the side of the fine cell, periodic).
+// Bilinear prolongation and correction, one thread per pair of fine cells
+// (i = 2I, 2I+1) of a layer: fine cell 2I adds sum_a w_a (3/4 e[J_a, I] +
+// 1/4 e[J_a, I-1]) and 2I+1 adds sum_a w_a (3/4 e[J_a, I] + 1/4 e[J_a, I+1])
+// (periodic in longitude); three coarse loads per coarse row serve both.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_prolong_add(LevelDev<T> F, LinkDev K, const T *__restrict__ ec, T *__restrict__ u)
 {
     const int nf = F.nlon, nc = nf / 2;
-    const int ncol = nf * F.nlat;
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= ncol) return;
-    const int j = col / nf, i = col - j * nf;
-    const int I = i >> 1;
-    const int In = (i & 1) ? (I + 1 == nc ? 0 : I + 1) : (I == 0 ? nc - 1 : I - 1);
-    const int Ja = K.j0[j], Jb = K.j1[j];
-    const T wa = (T)K.w0[j], wb = Jb >= 0 ? (T)K.w1[j] : T(0);
-    const int Jb_ = Jb >= 0 ? Jb : Ja;
-    const size_t plane_f = (size_t)ncol, plane_c = (size_t)nc * K.nlat_c;
+    const int npair = nc * F.nlat;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (t >= npair) return;
+    const int j = t / nc, I = t - j * nc;
+    const int Im = (I == 0) ? nc - 1 : I - 1;
+    const int Ip = (I + 1 == nc) ? 0 : I + 1;
+    const int Ja = __ldg(K.j0 + j), Jb = __ldg(K.j1 + j);
+    const size_t plane_c = (size_t)nc * K.nlat_c;
     const T q1 = T(0.25), q3 = T(0.75);
-    for (int k = 0; k < F.nz; ++k) {
-        const T *ea = ec + (size_t)k * plane_c + (size_t)Ja * nc;
-        const T *eb = ec + (size_t)k * plane_c + (size_t)Jb_ * nc;
-        T add = wa * fma(q3, ea[I], q1 * ea[In]);
-        if (Jb >= 0) add = fma(wb, fma(q3, eb[I], q1 * eb[In]), add);
-        u[(size_t)k * plane_f + col] += add;
+    const T *ek = ec + (size_t)k * plane_c;
+    const T *ea = ek + (size_t)Ja * nc;
+    const T wa = (T)__ldg(K.w0 + j);
+    const T ca = __ldg(ea + I);
+    T a0 = wa * fma(q3, ca, q1 * __ldg(ea + Im));
+    T a1 = wa * fma(q3, ca, q1 * __ldg(ea + Ip));
+    if (Jb >= 0) {
+        const T *eb = ek + (size_t)Jb * nc;
+        const T wb = (T)__ldg(K.w1 + j);
+        const T cb = __ldg(eb + I);
+        a0 = fma(wb, fma(q3, cb, q1 * __ldg(eb + Im)), a0);
+        a1 = fma(wb, fma(q3, cb, q1 * __ldg(eb + Ip)), a1);
     }
+    T *uk = u + (size_t)k * nf * F.nlat + (size_t)j * nf + 2 * I;
+    uk[0] += a0;
+    uk[1] += a1;
 }
 
 template <typename T>
 cudaError_t launch_prolong_add(const LevelDev<T> &F, const LinkDev &K, const T *ec, T *u,
                                cudaStream_t s)
 {
-    const int ncol = F.nlon * F.nlat;
-    k_prolong_add<T><<<(ncol + kBlock - 1) / kBlock, kBlock, 0, s>>>(F, K, ec, u);
+    const int npair = (F.nlon / 2) * F.nlat;
+    const dim3 grid((npair + kBlock - 1) / kBlock, F.nz);
+    k_prolong_add<T><<<grid, kBlock, 0, s>>>(F, K, ec, u);
     return cudaGetLastError();
 }
 

@@ -125,8 +125,9 @@ class MGHandle:
         return tuple(outs)  # gh, gtx, gty, gtz
 
     # ------------------------------------------------------------- measurement
-    def profile(self, on: bool = True):
-        L.check(self.lib.mg_profile_enable(self._h, 1 if on else 0))
+    def profile(self, on=True):
+        """on: False/0 off, True/1 fine-level launches, 2 every level."""
+        L.check(self.lib.mg_profile_enable(self._h, int(on)))
 
     def profile_read(self, kind: int, level: int, prec: int):
         n, ms = ctypes.c_int(0), ctypes.c_double(0.0)
@@ -166,6 +167,21 @@ class MGHandle:
         return u
 
 
+# A solve that stops on `maxit` with the residual stuck at the FP64 rounding
+# floor (rounding of x times the vertical couplings: ~1e-12..1e-10 relative,
+# higher for smooth right-hand sides such as an adjoint dL/dx) still
+# returns an accurate solution; accept it below this relative residual.
+FLOOR_ACCEPT = 1e-8
+
+
+def _solve_checked(handle, b, tol):
+    x, info = handle.solve(b, tol=tol, raise_on_error=False)
+    st = info["status"]
+    if st != L.MG_OK and not (st == L.MG_ERR_NOT_CONVERGED and info["rel_res"] <= FLOOR_ACCEPT):
+        L.check(st)
+    return x, info
+
+
 class MGSolveFn(torch.autograd.Function):
     """x = H(h, tx, ty, tz)^{-1} b as a differentiable function.
 
@@ -176,11 +192,11 @@ class MGSolveFn(torch.autograd.Function):
     from the forward pass, no iterate."""
 
     @staticmethod
-    def forward(ctx, b, h, tx, ty, tz, tol=1e-12, params=None):
+    def forward(ctx, b, h, tx, ty, tz, tol=1e-11, params=None):
         params = dict(params or {})
         handle = MGHandle(tx.detach().contiguous(), ty.detach().contiguous(),
                           tz.detach().contiguous(), h.detach().contiguous(), **params)
-        x, _ = handle.solve(b.detach().contiguous(), tol=tol)
+        x, _ = _solve_checked(handle, b.detach().contiguous(), tol)
         ctx.handle = handle
         ctx.tol = tol
         ctx.save_for_backward(x)
@@ -189,10 +205,10 @@ class MGSolveFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
-        lam, _ = ctx.handle.solve(gx.contiguous(), tol=ctx.tol)
+        lam, _ = _solve_checked(ctx.handle, gx.contiguous(), ctx.tol)
         gh, gtx, gty, gtz = ctx.handle.coeff_grad(lam, x)
         return lam, gh, gtx, gty, gtz, None, None
 
 
-def mg_solve_fn(b, h, tx, ty, tz, tol=1e-12, **params):
+def mg_solve_fn(b, h, tx, ty, tz, tol=1e-11, **params):
     return MGSolveFn.apply(b, h, tx, ty, tz, tol, params)
