@@ -182,6 +182,46 @@ int mg_level_prolong_add(mg_handle *h, int level, int prec, const void *ec, void
  * scaled (FP32 level l holds c * coefficients); 0 when not built. */
 double mg_fp32_scale(const mg_handle *h);
 
+/* ---- batched ensemble of independent systems (spec batching form).
+ * n systems of possibly different shapes share one device workspace and the
+ * same parameters; every V-cycle step and fine-level vector operation of all
+ * systems is one persistent-kernel launch over a precomputed work list of
+ * (system level, column tile), the batched V-cycle is replayed from one CUDA
+ * graph, and converged systems are switched off by device-side flags.
+ * mg_batch_setup autotunes the smoother's column-tile width and the
+ * persistent grid sizes on the batch itself (mg_batch_tuning reports them). */
+typedef struct mg_batch mg_batch;
+
+/* Workspace bytes for n systems with these grids and common params. */
+int mg_batch_workspace_bytes(int n, const mg_grid *grids, const mg_params *params,
+                             size_t *bytes);
+
+/* Set up the n hierarchies (as mg_setup, each from coeffs[i]) and the batched
+ * work lists, then autotune.  Synchronises `stream`.  On failure *out = NULL. */
+int mg_batch_setup(int n, const mg_grid *grids, const mg_coeffs *coeffs,
+                   const mg_params *params, void *workspace, size_t ws_bytes, void *stream,
+                   mg_batch **out);
+
+/* Release the batch (host memory; the workspace stays the caller's). */
+void mg_batch_destroy(mg_batch *b);
+
+/* The handle of system i (owned by the batch; valid until mg_batch_destroy). */
+int mg_batch_handle(mg_batch *b, int i, mg_handle **out);
+
+/* Tuned launch shapes: smoother column-tile width (threads per block) and
+ * persistent grid sizes of the smoother, cell-parallel and vector steps. */
+int mg_batch_tuning(const mg_batch *b, int *smooth_block, int *smooth_grid, int *cell_grid,
+                    int *vec_grid);
+
+/* Solve all systems: b[i], x[i] are HOST arrays of n device pointers (FP64
+ * fields of system i; x[i] in = initial guess, out = solution), each to
+ * ||b_i - H_i x_i|| <= tol ||b_i||.  mixed = 1: FP32 multigrid inside FP64
+ * refinement (needs params->mixed at setup); 0: FP64.  stats (n entries) and
+ * status (n ints) may be NULL.  Returns MG_OK when every system converged,
+ * else the first failing status. */
+int mg_batch_solve(mg_batch *b, const double *const *bs, double *const *xs, double tol,
+                   int mixed, mg_stats *stats, int *status, void *stream);
+
 /* ---- measurement hooks (off by default; no effect on results).
  * When profiling is on (on = 1: fine-level launches only; on = 2: every
  * level), each kernel launch of this handle is bracketed by CUDA events on

@@ -94,6 +94,16 @@ def load() -> ctypes.CDLL:
         "mg_residual_norm_noalloc": (I, [ctypes.POINTER(mg_grid), ctypes.POINTER(mg_coeffs), P, P,
                                          P, ctypes.POINTER(D), P]),
         "mg_last_error": (ctypes.c_char_p, []),
+        "mg_batch_workspace_bytes": (I, [I, ctypes.POINTER(mg_grid), ctypes.POINTER(mg_params),
+                                         ctypes.POINTER(S)]),
+        "mg_batch_setup": (I, [I, ctypes.POINTER(mg_grid), ctypes.POINTER(mg_coeffs),
+                               ctypes.POINTER(mg_params), P, S, P, ctypes.POINTER(H)]),
+        "mg_batch_destroy": (None, [H]),
+        "mg_batch_handle": (I, [H, I, ctypes.POINTER(H)]),
+        "mg_batch_tuning": (I, [H, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                                ctypes.POINTER(I)]),
+        "mg_batch_solve": (I, [H, ctypes.POINTER(P), ctypes.POINTER(P), D, I,
+                               ctypes.POINTER(mg_stats), ctypes.POINTER(I), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/tpmg.h"
+#include "tpmg_handle.h"
 #include "tpmg_internal.h"
 
 using namespace tpmg;
@@ -23,7 +24,7 @@ using namespace tpmg;
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_last_error;
 
-static int fail(int code, const char *fmt, ...)
+int tpmg::fail(int code, const char *fmt, ...)
 {
     char buf[512];
     va_list ap;
@@ -36,28 +37,10 @@ static int fail(int code, const char *fmt, ...)
 
 void tpmg::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
 
-#define CU(call)                                                                          \
-    do {                                                                                  \
-        cudaError_t e_ = (call);                                                          \
-        if (e_ != cudaSuccess)                                                            \
-            return fail(MG_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),      \
-                        __FILE__, __LINE__);                                              \
-    } while (0)
-
-#define CHK(expr)                  \
-    do {                           \
-        int st_ = (expr);          \
-        if (st_ != MG_OK) return st_; \
-    } while (0)
+std::atomic<unsigned long long> tpmg::g_launches{0};
 
 // ------------------------------------------------------------------ hierarchy (host)
 namespace {
-
-struct LinkHost {
-    int nlat_c = 0;
-    std::vector<int> cfirst, ccnt, j0, j1, rptr, rrow;
-    std::vector<double> w0, w1, rw, sy;
-};
 
 struct LevelShape {
     int nlon, nlat;
@@ -180,137 +163,6 @@ struct Carver {
 };
 
 }  // namespace
-
-// ------------------------------------------------------------------ handle
-struct LevelHost {
-    int nlon = 0, nlat = 0, nz = 0;
-    size_t n = 0;
-    double *tx = nullptr, *ty = nullptr, *tz = nullptr, *h = nullptr, *m = nullptr, *dq = nullptr;
-    float *tx32 = nullptr, *ty32 = nullptr, *tz32 = nullptr, *h32 = nullptr, *m32 = nullptr,
-          *dq32 = nullptr;
-    // V-cycle vectors: rhs, result, ping-pong scratch, residual
-    double *b = nullptr, *u = nullptr, *w = nullptr, *r = nullptr;
-    float *b32 = nullptr, *u32 = nullptr, *w32 = nullptr, *r32 = nullptr;
-    LinkHost link;
-    LinkDev linkdev{};
-};
-
-template <typename T>
-struct CgVecs {
-    T *r = nullptr, *z = nullptr, *d0 = nullptr, *d1 = nullptr, *Ad = nullptr, *x = nullptr;
-};
-
-struct ProfRec {
-    int key;
-    cudaEvent_t a, b;
-};
-
-struct Profiler {
-    bool on = false;
-    bool all_levels = false;
-    std::vector<cudaEvent_t> pool;
-    size_t next = 0;
-    std::vector<ProfRec> recs;
-};
-
-// A V-cycle captured once as a CUDA graph (fixed input/output vectors of
-// the solver), replayed on the caller's stream.
-struct VGraph {
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    unsigned long long kernels = 0;  // kernel nodes, for the launch count
-};
-
-struct mg_handle {
-    Profiler prof;
-    cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
-    bool capturing = false;
-    bool use_graphs = true;
-    VGraph vg[2];                       // [MG_PREC_FP64], [MG_PREC_FP32]
-    mg_grid grid{};
-    mg_params p{};
-    int L = 0;
-    std::vector<LevelHost> lev;
-    CgVecs<double> cg64;
-    CgVecs<float> cg32;
-    double *partial = nullptr;
-    CgScalars *sc = nullptr;
-    int *flag = nullptr;
-    double scale32 = 0.0;
-};
-
-template <typename T>
-static LevelDev<T> dev(const LevelHost &l);
-template <>
-LevelDev<double> dev<double>(const LevelHost &l)
-{
-    return {l.nlon, l.nlat, l.nz, l.tx, l.ty, l.tz, l.h, l.m, l.dq};
-}
-template <>
-LevelDev<float> dev<float>(const LevelHost &l)
-{
-    return {l.nlon, l.nlat, l.nz, l.tx32, l.ty32, l.tz32, l.h32, l.m32, l.dq32};
-}
-template <typename T>
-struct Vec;
-template <>
-struct Vec<double> {
-    static double *b(LevelHost &l) { return l.b; }
-    static double *u(LevelHost &l) { return l.u; }
-    static double *w(LevelHost &l) { return l.w; }
-    static double *r(LevelHost &l) { return l.r; }
-    static CgVecs<double> &cg(mg_handle *h) { return h->cg64; }
-};
-template <>
-struct Vec<float> {
-    static float *b(LevelHost &l) { return l.b32; }
-    static float *u(LevelHost &l) { return l.u32; }
-    static float *w(LevelHost &l) { return l.w32; }
-    static float *r(LevelHost &l) { return l.r32; }
-    static CgVecs<float> &cg(mg_handle *h) { return h->cg32; }
-};
-
-static std::atomic<unsigned long long> g_launches{0};
-
-enum { K_SMOOTH = 0, K_SMOOTH0 = 1, K_RESID = 2, K_APPLY = 3, K_RESTRICT = 4, K_PROLONG = 5,
-       K_VEC = 6 };
-
-static int prof_key(int kind, int level, int prec) { return (kind * 64 + level) * 2 + prec; }
-
-// Run one launcher (which may issue one kernel); count it and, when
-// profiling is on, bracket it with events on its stream.
-template <typename F>
-static int run_k(mg_handle *H, int kind, int level, int prec, cudaStream_t s, F &&f)
-{
-    Profiler &P = H->prof;
-    const bool rec = P.on && (P.all_levels || level == 0) && P.next + 2 <= P.pool.size();
-    cudaEvent_t a = nullptr, b = nullptr;
-    if (rec) {
-        a = P.pool[P.next++];
-        b = P.pool[P.next++];
-        CU(cudaEventRecord(a, s));
-    }
-    const cudaError_t e = f();
-    if (H->capturing) ++H->vg[prec].kernels;
-    else g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (e != cudaSuccess)
-        return fail(MG_ERR_CUDA, "kernel launch (kind %d, level %d): %s", kind, level,
-                    cudaGetErrorString(e));
-    if (rec) {
-        CU(cudaEventRecord(b, s));
-        P.recs.push_back({prof_key(kind, level, prec), a, b});
-    }
-    return MG_OK;
-}
-
-static inline cudaError_t to_err(cudaError_t e) { return e != cudaSuccess ? e : cudaGetLastError(); }
-static inline cudaError_t to_err(int) { return cudaGetLastError(); }
-
-#define KRUN(kind, level, prec, expr) \
-    CHK(run_k(H, kind, level, prec, s, [&]() -> cudaError_t { return to_err(expr); }))
-
-template <typename T>
-static constexpr int prec_of() { return sizeof(T) == 8 ? MG_PREC_FP64 : MG_PREC_FP32; }
 
 static int check_grid(const mg_grid *g, const mg_params *p, int *L_out)
 {
@@ -479,7 +331,6 @@ static int read_scalar(mg_handle *H, int which, double *out, cudaStream_t s)
     return MG_OK;
 }
 
-enum { S_RZ = 0, S_RZNEW = 1, S_DAD = 2, S_RR = 3, S_ALPHA = 4, S_BETA = 5, S_MAX = 6 };
 
 static int device_max(mg_handle *H, const double *a, size_t n, double *out, cudaStream_t s)
 {
@@ -561,6 +412,31 @@ static int setup_impl(mg_handle *H, const mg_coeffs *co, void *ws, size_t ws_byt
     }
     CU(cudaStreamSynchronize(s));
     return MG_OK;
+}
+
+int tpmg::handle_plan(const mg_grid *g, const mg_params *p, void *ws, size_t *bytes, mg_handle **out)
+{
+    int L = 0;
+    CHK(check_grid(g, p, &L));
+    mg_handle *H = new mg_handle;
+    H->grid = *g;
+    H->p = *p;
+    H->L = L;
+    build_shapes(g, p, L, H->lev);
+    *bytes = carve(H, nullptr);
+    if (ws) carve(H, ws);
+    *out = H;
+    return MG_OK;
+}
+
+int tpmg::handle_setup(mg_handle *H, const mg_coeffs *co, void *ws, size_t ws_bytes, cudaStream_t s)
+{
+    return setup_impl(H, co, ws, ws_bytes, s);
+}
+
+int tpmg::read_scalars(mg_handle *H, int which, double *out, cudaStream_t s)
+{
+    return read_scalar(H, which, out, s);
 }
 
 extern "C" int mg_setup(const mg_grid *grid, const mg_coeffs *coeffs, const mg_params *params,
@@ -749,9 +625,13 @@ static bool bad(double v) { return !(v == v) || std::isinf(v); }
 
 // Conjugate gradients preconditioned by one V-cycle, or the stationary
 // iteration x <- x + V(b - H x) (Section 2).  Scalars in FP64.
+// inner: the inner solve of the mixed-precision refinement: x enters as 0
+// (so r = b without a stencil) and the recursively updated residual decides
+// (the FP64 outer residual is the check), no confirming residual.
 template <typename T>
 static int solve_impl(mg_handle *H, const T *b, T *x, double tol, int maxit, int method,
-                      std::vector<double> *hist, int *its_out, double *rel_out, cudaStream_t s)
+                      std::vector<double> *hist, int *its_out, double *rel_out, cudaStream_t s,
+                      bool inner = false)
 {
     LevelHost &f = H->lev[0];
     const LevelDev<T> D = dev<T>(f);
@@ -773,12 +653,19 @@ static int solve_impl(mg_handle *H, const T *b, T *x, double tol, int maxit, int
         rel = bn > 0 ? std::sqrt(rr) / bn : 0.0;
         if (hist) hist->push_back(rel);
     };
+    bool first = true;
     while (true) {
-        int nb = 0;
-        KRUN(K_RESID, 0, P, nb = launch_stencil<T>(D, 1, b, x, cg.r, H->partial, s));
-        KRUN(K_VEC, 0, P, launch_finalize(H->partial, nb, H->sc, S_RR, 0, s));
         double rr;
-        CHK(read_scalar(H, S_RR, &rr, s));
+        if (inner && first) {
+            KRUN(K_VEC, 0, P, launch_cg_direction<T>(b, nullptr, cg.r, n, H->sc, true, s));
+            rr = bb;
+        } else {
+            int nb = 0;
+            KRUN(K_RESID, 0, P, nb = launch_stencil<T>(D, 1, b, x, cg.r, H->partial, s));
+            KRUN(K_VEC, 0, P, launch_finalize(H->partial, nb, H->sc, S_RR, 0, s));
+            CHK(read_scalar(H, S_RR, &rr, s));
+        }
+        first = false;
         if (bad(rr)) return fail(MG_ERR_NONFINITE, "non-finite residual");
         if (rr0 < 0) rr0 = rr;
         record(rr);
@@ -810,7 +697,15 @@ static int solve_impl(mg_handle *H, const T *b, T *x, double tol, int maxit, int
             KRUN(K_VEC, 0, P, launch_finalize(H->partial, nu, H->sc, S_RR, 0, s));
             CHK(read_scalar(H, S_RR, &rr, s));
             if (bad(rr)) return fail(MG_ERR_NONFINITE, "non-finite residual");
-            if (std::sqrt(rr) <= tol * bn || its >= maxit) break;  // confirm with the true residual
+            if (std::sqrt(rr) <= tol * bn || its >= maxit) {
+                if (inner) {
+                    record(rr);
+                    *its_out = its;
+                    *rel_out = rel;
+                    return std::sqrt(rr) <= tol * bn ? MG_OK : MG_ERR_NOT_CONVERGED;
+                }
+                break;  // confirm with the true residual
+            }
             record(rr);
             if (rr > 1e6 * rr0) return fail(MG_ERR_DIVERGED, "residual grew to %.3e", rel);
             CHK(vcycle_solver<T>(H, s));
@@ -907,7 +802,7 @@ extern "C" int mg_solve_mixed(mg_handle *H, const double *b, double *x, double t
         int its_in = 0;
         double rel_in = 0;
         const int rin = solve_impl<float>(H, f.b32, H->cg32.x, H->p.inner_tol, H->p.inner_maxit,
-                                          H->p.method, nullptr, &its_in, &rel_in, s);
+                                          H->p.method, nullptr, &its_in, &rel_in, s, true);
         if (rin != MG_OK && rin != MG_ERR_NOT_CONVERGED && rin != MG_ERR_DIVERGED) {
             rc = rin;
             break;

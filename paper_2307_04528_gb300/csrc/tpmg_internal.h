@@ -119,6 +119,75 @@ cudaError_t launch_to_float(const double *in, float *out, double scale, size_t n
 cudaError_t launch_coeff_grad(int nlon, int nlat, int nz, const double *lam, const double *x,
                               double *gh, double *gtx, double *gty, double *gtz, cudaStream_t s);
 
+// ---- batched ensemble (tpmg_batch.cu) -----------------------------------------
+// One participant of a batched step: one level of one system and the vectors
+// the step reads and writes.
+template <typename T>
+struct BOp {
+    LevelDev<T> L;   // the level (the fine level of a transfer)
+    LinkDev K;       // link to the next coarser level (transfers)
+    const T *a;      // right-hand side / source
+    const T *x;      // second input (smoother u_in, nullptr = zero guess; stencil x)
+    T *y;            // output
+    int sys;         // system index (activity flag, per-system reductions)
+    int nblk;        // thread blocks per layer (cell tiles) or per level (column tiles)
+};
+
+// A work item: participant `op`, tile `tile` (a column block, or
+// layer * nblk + column block for the cell-parallel kernels).
+struct BItem {
+    int op, tile;
+};
+
+// One fine-level vector operation of one system (roles depend on the kernel).
+template <typename T>
+struct BVec {
+    T *a, *b, *c, *d;
+    size_t n;
+    int sys, nchunk;
+};
+
+// FP64 <-> FP32 transfer of the mixed-precision refinement of one system.
+struct BMix {
+    double *x;          // FP64 solution (update)
+    const double *r;    // FP64 residual (cast)
+    float *r32;         // FP32 right-hand side of the inner solve (cast)
+    const float *e32;   // FP32 correction (update)
+    size_t n;
+    int sys, nchunk;
+};
+
+constexpr int kVecChunk = kBlock * 16;  // elements per vector work item
+
+enum { BV_DOT = 0, BV_UPDATE = 1, BV_DIR = 2, BV_DIR0 = 3, BV_ADD = 4, BV_MAXABS = 5 };
+
+template <typename T>
+cudaError_t launch_bsmooth(const BOp<T> *ops, const BItem *items, int nitems, bool zero,
+                           double omega, const int *active, int grid, int block, int nzmax,
+                           cudaStream_t s);
+// kind: 0 residual y = a - H x (cells), 1 restriction (cells), 2 prolongation (cell pairs)
+template <typename T>
+cudaError_t launch_bcells(int kind, const BOp<T> *ops, const BItem *items, int nitems,
+                          const int *active, int grid, cudaStream_t s);
+// Column-loop stencil with one partial sum per item (mode 1: residual + sum r^2;
+// mode 0: apply + sum x*y).
+template <typename T>
+cudaError_t launch_bstencil_red(int mode, const BOp<T> *ops, const BItem *items, int nitems,
+                                double *partial, const int *active, int grid, cudaStream_t s);
+// Vector kernels over per-system chunks; per-item partials where the op reduces.
+template <typename T>
+cudaError_t launch_bvec(int op, const BVec<T> *v, const BItem *items, int nitems,
+                        const CgScalars *sc, double *partial, const int *active, int grid,
+                        cudaStream_t s);
+// mode 0: r32 = (float)(r * sdata[sys]); mode 1: x += sdata[sys] * (double)e32
+cudaError_t launch_bmix(int mode, const BMix *v, const BItem *items, int nitems,
+                        const double *sdata, const int *active, int grid, cudaStream_t s);
+// Per-system fixed-order sum of partial[off[s] .. off[s+1]) into sc[s] (ops
+// as launch_finalize; op 3 = max); inactive systems are skipped.
+cudaError_t launch_bfinalize(const double *partial, const int *off, int nsys, CgScalars *sc,
+                             int which, int op, const int *active, cudaStream_t s);
+cudaError_t bsmooth_prepare();
+
 // Set the thread-local message mg_last_error() returns.
 void set_last_error(const char *msg);
 

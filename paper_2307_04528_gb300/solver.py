@@ -38,6 +38,22 @@ class MGHandle:
     method, mixed, maxit, inner_maxit, omega, alpha_c, inner_tol).
     """
 
+    @classmethod
+    def borrow(cls, ptr, shape, device, owner):
+        """Wrap a handle owned by `owner` (e.g. one system of an MGBatch)."""
+        self = cls.__new__(cls)
+        self.lib = L.load()
+        self.shape = tuple(shape)
+        self.device = device
+        self._h = None          # not ours to destroy
+        self._borrowed = ctypes.c_void_p(ptr)
+        self._owner = owner
+        return self
+
+    @property
+    def _hh(self):
+        return self._h if self._h is not None else self._borrowed
+
     def __init__(self, tx, ty, tz, h, stream=None, **params):
         self.lib = L.load()
         nz, nlat, nlon = h.shape
@@ -67,35 +83,35 @@ class MGHandle:
     # ------------------------------------------------------------- queries
     @property
     def num_levels(self) -> int:
-        return int(self.lib.mg_num_levels(self._h))
+        return int(self.lib.mg_num_levels(self._hh))
 
     def level_shape(self, level: int):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        L.check(self.lib.mg_level_shape(self._h, level, ctypes.byref(a), ctypes.byref(b),
+        L.check(self.lib.mg_level_shape(self._hh, level, ctypes.byref(a), ctypes.byref(b),
                                         ctypes.byref(c)))
         return (c.value, b.value, a.value)
 
     def level_coeffs(self, level: int):
         shp = self.level_shape(level)
         out = [torch.empty(shp, dtype=torch.float64, device=self.device) for _ in range(4)]
-        L.check(self.lib.mg_level_coeffs(self._h, level, *map(_ptr, out), _stream()))
+        L.check(self.lib.mg_level_coeffs(self._hh, level, *map(_ptr, out), _stream()))
         return out
 
     @property
     def fp32_scale(self) -> float:
-        return float(self.lib.mg_fp32_scale(self._h))
+        return float(self.lib.mg_fp32_scale(self._hh))
 
     # ------------------------------------------------------------- fine level
     def apply(self, x, y=None):
         _field(x, torch.float64, self.shape, "x")
         y = torch.empty_like(x) if y is None else y
-        L.check(self.lib.mg_apply(self._h, _ptr(x), _ptr(y), _stream()))
+        L.check(self.lib.mg_apply(self._hh, _ptr(x), _ptr(y), _stream()))
         return y
 
     def vcycle(self, r, e=None):
         _field(r, torch.float64, self.shape, "r")
         e = torch.empty_like(r) if e is None else e
-        L.check(self.lib.mg_vcycle(self._h, _ptr(r), _ptr(e), _stream()))
+        L.check(self.lib.mg_vcycle(self._hh, _ptr(r), _ptr(e), _stream()))
         return e
 
     def _solve(self, fn, b, x, tol, history_cap, raise_on):
@@ -104,7 +120,7 @@ class MGHandle:
         _field(x, torch.float64, self.shape, "x")
         hist = (ctypes.c_double * history_cap)()
         st = L.mg_stats(0, 0, 0.0, hist, history_cap, 0)
-        status = fn(self._h, _ptr(b), _ptr(x), float(tol), ctypes.byref(st), _stream())
+        status = fn(self._hh, _ptr(b), _ptr(x), float(tol), ctypes.byref(st), _stream())
         if raise_on:
             L.check(status)
         info = dict(status=status, iterations=st.iterations, inner_iterations=st.inner_iterations,
@@ -121,17 +137,17 @@ class MGHandle:
 
     def coeff_grad(self, lam, x):
         outs = [torch.empty_like(x) for _ in range(4)]
-        L.check(self.lib.mg_coeff_grad(self._h, _ptr(lam), _ptr(x), *map(_ptr, outs), _stream()))
+        L.check(self.lib.mg_coeff_grad(self._hh, _ptr(lam), _ptr(x), *map(_ptr, outs), _stream()))
         return tuple(outs)  # gh, gtx, gty, gtz
 
     # ------------------------------------------------------------- measurement
     def profile(self, on=True):
         """on: False/0 off, True/1 fine-level launches, 2 every level."""
-        L.check(self.lib.mg_profile_enable(self._h, int(on)))
+        L.check(self.lib.mg_profile_enable(self._hh, int(on)))
 
     def profile_read(self, kind: int, level: int, prec: int):
         n, ms = ctypes.c_int(0), ctypes.c_double(0.0)
-        L.check(self.lib.mg_profile_read(self._h, kind, level, prec, ctypes.byref(n),
+        L.check(self.lib.mg_profile_read(self._hh, kind, level, prec, ctypes.byref(n),
                                          ctypes.byref(ms)))
         return n.value, ms.value
 
@@ -141,29 +157,29 @@ class MGHandle:
 
     def level_apply(self, level, x, prec=L.MG_PREC_FP64):
         y = torch.empty_like(x)
-        L.check(self.lib.mg_level_apply(self._h, level, prec, _ptr(x), _ptr(y), _stream()))
+        L.check(self.lib.mg_level_apply(self._hh, level, prec, _ptr(x), _ptr(y), _stream()))
         return y
 
     def level_residual(self, level, b, u, prec=L.MG_PREC_FP64):
         r = torch.empty_like(b)
-        L.check(self.lib.mg_level_residual(self._h, level, prec, _ptr(b), _ptr(u), _ptr(r),
+        L.check(self.lib.mg_level_residual(self._hh, level, prec, _ptr(b), _ptr(u), _ptr(r),
                                            _stream()))
         return r
 
     def level_smooth(self, level, b, u_in=None, prec=L.MG_PREC_FP64):
         out = torch.empty_like(b)
-        L.check(self.lib.mg_level_smooth(self._h, level, prec, _ptr(b), _ptr(u_in), _ptr(out),
+        L.check(self.lib.mg_level_smooth(self._hh, level, prec, _ptr(b), _ptr(u_in), _ptr(out),
                                          _stream()))
         return out
 
     def level_restrict(self, level, r, prec=L.MG_PREC_FP64):
         shp = self.level_shape(level + 1)
         bc = torch.empty(shp, dtype=r.dtype, device=r.device)
-        L.check(self.lib.mg_level_restrict(self._h, level, prec, _ptr(r), _ptr(bc), _stream()))
+        L.check(self.lib.mg_level_restrict(self._hh, level, prec, _ptr(r), _ptr(bc), _stream()))
         return bc
 
     def level_prolong_add(self, level, ec, u, prec=L.MG_PREC_FP64):
-        L.check(self.lib.mg_level_prolong_add(self._h, level, prec, _ptr(ec), _ptr(u), _stream()))
+        L.check(self.lib.mg_level_prolong_add(self._hh, level, prec, _ptr(ec), _ptr(u), _stream()))
         return u
 
 
@@ -180,6 +196,76 @@ def _solve_checked(handle, b, tol):
     if st != L.MG_OK and not (st == L.MG_ERR_NOT_CONVERGED and info["rel_res"] <= FLOOR_ACCEPT):
         L.check(st)
     return x, info
+
+
+class MGBatch:
+    """Ensemble of independent systems of uneven sizes solved together.
+
+    systems: list of (tx, ty, tz, h) CUDA float64 tensors, one tuple per
+    system.  params: keyword overrides of mg_params (common to all)."""
+
+    def __init__(self, systems, stream=None, **params):
+        self.lib = L.load()
+        self.n = len(systems)
+        self.shapes = []
+        grids = (L.mg_grid * self.n)()
+        coeffs = (L.mg_coeffs * self.n)()
+        for i, (tx, ty, tz, h) in enumerate(systems):
+            shp = tuple(h.shape)
+            for name, t in (("tx", tx), ("ty", ty), ("tz", tz), ("h", h)):
+                _field(t, torch.float64, shp, name)
+            self.shapes.append(shp)
+            grids[i] = L.mg_grid(shp[2], shp[1], shp[0])
+            coeffs[i] = L.mg_coeffs(tx.data_ptr(), ty.data_ptr(), tz.data_ptr(), h.data_ptr())
+        self.device = systems[0][3].device
+        self.params = L.default_params(**params)
+        nbytes = ctypes.c_size_t(0)
+        L.check(self.lib.mg_batch_workspace_bytes(self.n, grids, ctypes.byref(self.params),
+                                                  ctypes.byref(nbytes)))
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        self._b = ctypes.c_void_p()
+        L.check(self.lib.mg_batch_setup(self.n, grids, coeffs, ctypes.byref(self.params),
+                                        _ptr(self.workspace), nbytes, _stream(stream),
+                                        ctypes.byref(self._b)))
+
+    def __del__(self):
+        b = getattr(self, "_b", None)
+        if b is not None and b.value:
+            self.lib.mg_batch_destroy(b)
+            self._b = None
+
+    def handle(self, i):
+        """The handle of system i (for single-system calls on the same data)."""
+        out = ctypes.c_void_p()
+        L.check(self.lib.mg_batch_handle(self._b, i, ctypes.byref(out)))
+        return MGHandle.borrow(out.value, self.shapes[i], self.device, self)
+
+    def tuning(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        L.check(self.lib.mg_batch_tuning(self._b, *map(ctypes.byref, v)))
+        return dict(zip(("smooth_block", "smooth_grid", "cell_grid", "vec_grid"),
+                        (x.value for x in v)))
+
+    def solve(self, bs, xs=None, tol=1e-8, mixed=True, raise_on_error=True):
+        """Solve every system; bs, xs: lists of CUDA float64 tensors (xs is
+        the initial guess, overwritten).  Returns (xs, per-system infos)."""
+        if xs is None:
+            xs = [torch.zeros_like(b) for b in bs]
+        for i, (b, x) in enumerate(zip(bs, xs)):
+            _field(b, torch.float64, self.shapes[i], f"b[{i}]")
+            _field(x, torch.float64, self.shapes[i], f"x[{i}]")
+        bp = (ctypes.c_void_p * self.n)(*(b.data_ptr() for b in bs))
+        xp = (ctypes.c_void_p * self.n)(*(x.data_ptr() for x in xs))
+        stats = (L.mg_stats * self.n)()
+        status = (ctypes.c_int * self.n)()
+        st = self.lib.mg_batch_solve(self._b, bp, xp, float(tol), int(bool(mixed)), stats,
+                                     status, _stream())
+        if raise_on_error:
+            L.check(st)
+        infos = [dict(status=status[i], iterations=stats[i].iterations,
+                      inner_iterations=stats[i].inner_iterations, rel_res=stats[i].rel_res)
+                 for i in range(self.n)]
+        return xs, infos
 
 
 class MGSolveFn(torch.autograd.Function):

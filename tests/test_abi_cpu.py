@@ -86,3 +86,16 @@ def test_level_counts_follow_nlon(lib):
     assert st == 0
     st, _ = _bytes(lib, 1536, 1152, 70, levels=4)
     assert st == 0
+
+
+def test_batch_workspace_covers_every_system(lib):
+    from paper_2307_04528_gb300 import _lib as L
+    shapes = [(32, 16, 8), (64, 32, 16), (96, 46, 12)]
+    grids = (L.mg_grid * 3)(*(L.mg_grid(*s) for s in shapes))
+    p = L.default_params(mixed=1)
+    n = ctypes.c_size_t(0)
+    assert lib.mg_batch_workspace_bytes(3, grids, ctypes.byref(p), ctypes.byref(n)) == 0
+    singles = sum(_bytes(lib, *s, mixed=1)[1] for s in shapes)
+    assert n.value > singles
+    bad = (L.mg_grid * 1)(L.mg_grid(64, 31, 8))
+    assert lib.mg_batch_workspace_bytes(1, bad, ctypes.byref(p), ctypes.byref(n)) == 1
