@@ -80,8 +80,9 @@ typedef struct {
     int maxit;         /* outer iterations (200) */
     int inner_maxit;   /* mixed: FP32 iterations per FP64 refinement step (8) */
     double omega;      /* Eq. (1) relaxation factor (0.8) */
-    double alpha_c;    /* Section 2.2 anisotropy threshold for merging rows (0.5) */
-    double inner_tol;  /* mixed: FP32 relative tolerance per refinement step (1e-3) */
+    double alpha_c;    /* Section 2.2 anisotropy threshold for merging rows (0.6) */
+    double inner_tol;  /* mixed: FP32 relative tolerance per refinement step (3e-3; loosened
+                          when the outer target needs less) */
 } mg_params;
 
 typedef struct {
@@ -169,6 +170,12 @@ int mg_level_residual(mg_handle *h, int level, int prec, const void *b, const vo
  * u_in == NULL means the zero initial guess.  u_out must not alias u_in. */
 int mg_level_smooth(mg_handle *h, int level, int prec, const void *b, const void *u_in,
                     void *u_out, void *stream);
+
+/* The same sweep (u_in != NULL) also returning *dot = <b, u_out> (host
+ * double; FP64 accumulation of per-column sums): the last sweep of a V-cycle
+ * with the conjugate-gradient inner product <r, z> fused in.  Synchronises. */
+int mg_level_smooth_dot(mg_handle *h, int level, int prec, const void *b, const void *u_in,
+                        void *u_out, double *dot, void *stream);
 
 /* bc = R r: restriction from level l to l+1 (R = P^T). */
 int mg_level_restrict(mg_handle *h, int level, int prec, const void *r, void *bc,

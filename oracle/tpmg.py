@@ -70,10 +70,10 @@ class MGParams:
     nu2: int = 1               # post-smoothing sweeps
     omega: float = 0.8         # Eq. (1) relaxation factor (value not printed)
     coarse_iters: int = 8      # Section 2.3's "simple iterative method": block-Jacobi sweeps
-    alpha_c: float = 0.5       # Section 2.2 anisotropy threshold (value not printed)
+    alpha_c: float = 0.6       # Section 2.2 anisotropy threshold (value not printed; tuned)
     method: str = "cg"         # outer iteration: "cg" (V-cycle-preconditioned CG) or "stationary"
     maxit: int = 200
-    inner_tol: float = 1e-3    # mixed precision: FP32 inner relative tolerance per refinement step
+    inner_tol: float = 3e-3    # mixed precision: FP32 inner relative tolerance per refinement step
     inner_maxit: int = 8       # mixed precision: FP32 inner iterations per refinement step
 
 
@@ -411,8 +411,9 @@ def solve_mixed(levels, b, tol: float = 1e-10, params: MGParams | None = None,
     Outer loop in FP64: r = b - H x, stop when ||r||_2 <= tol ||b||_2; scale r
     by a power of two s (exact; keeps FP32 clear of under/overflow) and round
     to FP32; inner: solve (c H) e = r / s in FP32 storage and arithmetic
-    (FP64 scalars) to inner_tol, at most inner_maxit iterations, with the
-    same outer iteration as the FP64 solver; update x <- x + c s e in FP64,
+    (FP64 scalars) to max(inner_tol, 0.3 tol / (||r|| / ||b||)) (at most 0.5),
+    at most inner_maxit iterations, with the same outer iteration as the FP64
+    solver; update x <- x + c s e in FP64,
     c the power-of-two scale of the FP32 coefficient copies.
     ``track(x)`` is called after every update.  Returns (x, rel_history, status)."""
     p = params or MGParams()
@@ -433,7 +434,9 @@ def solve_mixed(levels, b, tol: float = 1e-10, params: MGParams | None = None,
         _, ex = np.frexp(np.max(np.abs(r)))
         s = float(np.ldexp(1.0, int(ex)))
         r32 = (r / s).astype(np.float32)
-        e, _, _ = solve(l32, r32, p.inner_tol, params=p, maxit=p.inner_maxit)
+        # no further than the outer target still needs (safety 0.3), at most 0.5
+        itol = min(max(p.inner_tol, 0.3 * tol / (rn / bn)), 0.5)
+        e, _, _ = solve(l32, r32, itol, params=p, maxit=p.inner_maxit)
         x += (c * s) * e.astype(np.float64)
         if track is not None:
             track(x)

@@ -294,8 +294,8 @@ extern "C" void mg_default_params(mg_params *p)
     p->maxit = 200;
     p->inner_maxit = 8;
     p->omega = 0.8;
-    p->alpha_c = 0.5;
-    p->inner_tol = 1e-3;
+    p->alpha_c = 0.6;
+    p->inner_tol = 3e-3;
 }
 
 extern "C" const char *mg_last_error(void) { return g_last_error.c_str(); }
@@ -349,6 +349,15 @@ static int setup_impl(mg_handle *H, const mg_coeffs *co, void *ws, size_t ws_byt
         return fail(MG_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, need);
     carve(H, ws);
     CU(smooth_prepare());
+    {
+        int dev = 0, lim = 0;
+        CU(cudaGetDevice(&dev));
+        CU(cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        // 256 bytes: static shared memory of the block reductions
+        if (smooth_smem_bytes(H->grid.nz, sizeof(double)) + 256 > (size_t)lim)
+            return fail(MG_ERR_ARG, "nz = %d needs more shared memory per block than the device has",
+                        H->grid.nz);
+    }
     CU(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
     LevelHost &f = H->lev[0];
     const size_t bytes0 = f.n * sizeof(double);
@@ -545,9 +554,14 @@ static int smooth_from_zero(mg_handle *H, int l, const LevelDev<T> &D, const T *
 }
 
 // out = V_l b (zero initial guess).  scratch, rbuf: level-l work vectors.
+// dot_blocks (level 0 only, may be null): fuse <b, out> into the last sweep
+// and set *dot_blocks to the number of partial sums written (0 if the cycle
+// ends without a non-zero-guess sweep on this level).
 template <typename T>
-static int vcycle_level(mg_handle *H, int l, const T *b, T *out, T *scratch, T *rbuf, cudaStream_t s)
+static int vcycle_level(mg_handle *H, int l, const T *b, T *out, T *scratch, T *rbuf, cudaStream_t s,
+                        int *dot_blocks = nullptr)
 {
+    if (dot_blocks) *dot_blocks = 0;
     LevelHost &v = H->lev[l];
     const LevelDev<T> D = dev<T>(v);
     const double om = H->p.omega;
@@ -568,34 +582,42 @@ static int vcycle_level(mg_handle *H, int l, const T *b, T *out, T *scratch, T *
     CHK(vcycle_level<T>(H, l + 1, Vec<T>::b(c), Vec<T>::u(c), Vec<T>::w(c), Vec<T>::r(c), s));
     KRUN(K_PROLONG, l, P, launch_prolong_add<T>(D, v.linkdev, Vec<T>::u(c), cur, s));
     for (int it = 0; it < H->p.nu2; ++it) {
-        KRUN(K_SMOOTH, l, P, launch_smooth<T>(D, b, cur, oth, om, s));
+        if (dot_blocks && it + 1 == H->p.nu2) {
+            int nb = 0;
+            KRUN(K_SMOOTH, l, P, nb = launch_smooth_dot<T>(D, b, cur, oth, om, H->partial, s));
+            *dot_blocks = nb;
+        } else {
+            KRUN(K_SMOOTH, l, P, launch_smooth<T>(D, b, cur, oth, om, s));
+        }
         std::swap(cur, oth);
     }
     return MG_OK;
 }
 
 template <typename T>
-static int vcycle_fine(mg_handle *H, const T *r, T *e, cudaStream_t s)
+static int vcycle_fine(mg_handle *H, const T *r, T *e, cudaStream_t s, int *dot_blocks = nullptr)
 {
     LevelHost &f = H->lev[0];
-    return vcycle_level<T>(H, 0, r, e, Vec<T>::w(f), Vec<T>::r(f), s);
+    return vcycle_level<T>(H, 0, r, e, Vec<T>::w(f), Vec<T>::r(f), s, dot_blocks);
 }
 
 // z = V r for the solver's fixed vectors (cg.r -> cg.z), replayed from a CUDA
 // graph captured on first use; direct launches while profiling (events
 // around each kernel) or if capture is unavailable.
+// *dot_blocks: partial sums of <cg.r, cg.z> left in H->partial by the fused
+// last sweep (0: none, compute the inner product separately).
 template <typename T>
-static int vcycle_solver(mg_handle *H, cudaStream_t s)
+static int vcycle_solver(mg_handle *H, cudaStream_t s, int *dot_blocks)
 {
     CgVecs<T> &cg = Vec<T>::cg(H);
     constexpr int P = prec_of<T>();
-    if (!H->use_graphs || H->prof.on) return vcycle_fine<T>(H, cg.r, cg.z, s);
+    if (!H->use_graphs || H->prof.on) return vcycle_fine<T>(H, cg.r, cg.z, s, dot_blocks);
     VGraph &g = H->vg[P];
     if (!g.exec) {
         g.kernels = 0;
         CU(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
         H->capturing = true;
-        const int st = vcycle_fine<T>(H, cg.r, cg.z, H->cap_stream);
+        const int st = vcycle_fine<T>(H, cg.r, cg.z, H->cap_stream, &g.dot_blocks);
         H->capturing = false;
         cudaGraph_t graph = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(H->cap_stream, &graph);
@@ -603,7 +625,7 @@ static int vcycle_solver(mg_handle *H, cudaStream_t s)
             if (graph) cudaGraphDestroy(graph);
             cudaGetLastError();
             H->use_graphs = false;  // run the same kernels without a graph from now on
-            return vcycle_fine<T>(H, cg.r, cg.z, s);
+            return vcycle_fine<T>(H, cg.r, cg.z, s, dot_blocks);
         }
         const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
         if (ei != cudaSuccess) {
@@ -611,11 +633,12 @@ static int vcycle_solver(mg_handle *H, cudaStream_t s)
             cudaGetLastError();
             g = VGraph{};
             H->use_graphs = false;
-            return vcycle_fine<T>(H, cg.r, cg.z, s);
+            return vcycle_fine<T>(H, cg.r, cg.z, s, dot_blocks);
         }
         g.graph = graph;
     }
     CU(cudaGraphLaunch(g.exec, s));
+    *dot_blocks = g.dot_blocks;
     g_launches.fetch_add(g.kernels, std::memory_order_relaxed);
     return MG_OK;
 }
@@ -631,7 +654,7 @@ static bool bad(double v) { return !(v == v) || std::isinf(v); }
 template <typename T>
 static int solve_impl(mg_handle *H, const T *b, T *x, double tol, int maxit, int method,
                       std::vector<double> *hist, int *its_out, double *rel_out, cudaStream_t s,
-                      bool inner = false)
+                      bool inner = false, bool x_zero = false)
 {
     LevelHost &f = H->lev[0];
     const LevelDev<T> D = dev<T>(f);
@@ -656,7 +679,7 @@ static int solve_impl(mg_handle *H, const T *b, T *x, double tol, int maxit, int
     bool first = true;
     while (true) {
         double rr;
-        if (inner && first) {
+        if ((inner || x_zero) && first) {  // x = 0: r = b
             KRUN(K_VEC, 0, P, launch_cg_direction<T>(b, nullptr, cg.r, n, H->sc, true, s));
             rr = bb;
         } else {
@@ -676,15 +699,16 @@ static int solve_impl(mg_handle *H, const T *b, T *x, double tol, int maxit, int
             return fail(MG_ERR_NOT_CONVERGED, "not converged after %d iterations (rel %.3e)", its,
                         rel);
         if (rr > 1e6 * rr0) return fail(MG_ERR_DIVERGED, "residual grew to %.3e", rel);
+        int vdot = 0;
         if (method == MG_METHOD_STATIONARY) {
-            CHK(vcycle_solver<T>(H, s));
+            CHK(vcycle_solver<T>(H, s, &vdot));
             KRUN(K_VEC, 0, P, launch_add<T>(x, cg.z, n, s));
             ++its;
             continue;
         }
-        CHK(vcycle_solver<T>(H, s));
-        int nbd = 0;
-        KRUN(K_VEC, 0, P, nbd = launch_dot<T>(cg.r, cg.z, n, H->partial, s));
+        CHK(vcycle_solver<T>(H, s, &vdot));
+        int nbd = vdot;
+        if (!nbd) KRUN(K_VEC, 0, P, nbd = launch_dot<T>(cg.r, cg.z, n, H->partial, s));
         KRUN(K_VEC, 0, P, launch_finalize(H->partial, nbd, H->sc, S_RZ, 0, s));
         T *d = cg.d0, *dn = cg.d1;
         KRUN(K_VEC, 0, P, launch_cg_direction<T>(cg.z, nullptr, d, n, H->sc, true, s));
@@ -708,13 +732,24 @@ static int solve_impl(mg_handle *H, const T *b, T *x, double tol, int maxit, int
             }
             record(rr);
             if (rr > 1e6 * rr0) return fail(MG_ERR_DIVERGED, "residual grew to %.3e", rel);
-            CHK(vcycle_solver<T>(H, s));
-            KRUN(K_VEC, 0, P, nbd = launch_dot<T>(cg.r, cg.z, n, H->partial, s));
+            CHK(vcycle_solver<T>(H, s, &vdot));
+            nbd = vdot;
+            if (!nbd) KRUN(K_VEC, 0, P, nbd = launch_dot<T>(cg.r, cg.z, n, H->partial, s));
             KRUN(K_VEC, 0, P, launch_finalize(H->partial, nbd, H->sc, S_RZNEW, 2, s));
             KRUN(K_VEC, 0, P, launch_cg_direction<T>(cg.z, d, dn, n, H->sc, false, s));
             std::swap(d, dn);
         }
     }
+}
+
+// Relative tolerance of the FP32 inner solve of a refinement step: the
+// configured inner_tol, loosened to 0.3 tol / rel when that already takes the
+// outer residual (now rel relative to b) below the target tol; at most 0.5.
+double tpmg::inner_tolerance(double inner_tol, double tol, double rel)
+{
+    double t = inner_tol;
+    if (rel > 0) t = std::max(t, 0.3 * tol / rel);
+    return std::min(t, 0.5);
 }
 
 static void fill_stats(mg_stats *st, const std::vector<double> &hist, int its, int inner,
@@ -740,8 +775,11 @@ extern "C" int mg_solve(mg_handle *H, const double *b, double *x, double tol, mg
     std::vector<double> hist;
     int its = 0;
     double rel = 0;
+    double xmax = 0;
+    CHK(device_max(H, x, H->lev[0].n, &xmax, (cudaStream_t)stream));
+    if (bad(xmax)) return fail(MG_ERR_NONFINITE, "non-finite initial guess");
     const int rc = solve_impl<double>(H, b, x, tol, H->p.maxit, H->p.method, &hist, &its, &rel,
-                                      (cudaStream_t)stream);
+                                      (cudaStream_t)stream, false, xmax == 0.0);
     fill_stats(st, hist, its, 0, rel);
     return rc;
 }
@@ -766,15 +804,40 @@ extern "C" int mg_solve_mixed(mg_handle *H, const double *b, double *x, double t
     }
     if (bad(bb)) return fail(MG_ERR_NONFINITE, "non-finite right-hand side");
     const double bn = std::sqrt(bb);
+    // a zero initial guess makes the first residual b itself
+    double xmax = 0;
+    CHK(device_max(H, x, n, &xmax, s));
+    if (bad(xmax)) return fail(MG_ERR_NONFINITE, "non-finite initial guess");
+    const bool x_zero = xmax == 0.0;
     int outer = 0, inner = 0;
     double rel = 0, rr0 = -1;
+    double pred = bn;  // expected ||b - H x|| of this step
     int rc = MG_OK;
     while (true) {
-        int nb = 0;
-        KRUN(K_RESID, 0, 0, nb = launch_stencil<double>(D, 1, b, x, H->cg64.r, H->partial, s));
-        KRUN(K_VEC, 0, 0, launch_finalize(H->partial, nb, H->sc, S_RR, 0, s));
+        // The FP32 right-hand side is r / sc with sc a power of two near the
+        // expected ||r||: exact scaling, so the FP32 solve sees the same
+        // significands for any such sc; sc is corrected when the measured
+        // norm lands outside [sc 2^-10, sc 2^10].
+        int ex = 0;
+        std::frexp(pred > 0 ? pred : 1.0, &ex);
+        double sc = std::ldexp(1.0, ex);
         double rr;
-        CHK(read_scalar(H, S_RR, &rr, s));
+        if (x_zero && outer == 0) {
+            KRUN(K_VEC, 0, 1, launch_cast_scaled(b, f.b32, 1.0 / sc, n, s));
+            rr = bb;
+        } else {
+            int nb = 0;
+            KRUN(K_RESID, 0, 0, nb = launch_residual_cast(D, b, x, f.b32, 1.0 / sc, H->partial, s));
+            KRUN(K_VEC, 0, 0, launch_finalize(H->partial, nb, H->sc, S_RR, 0, s));
+            CHK(read_scalar(H, S_RR, &rr, s));
+            const double rn = std::sqrt(rr);
+            if (!bad(rr) && rn > 0 && (rn > std::ldexp(sc, 10) || rn < std::ldexp(sc, -10))) {
+                std::frexp(rn, &ex);
+                sc = std::ldexp(1.0, ex);
+                KRUN(K_RESID, 0, 0,
+                     launch_residual_cast(D, b, x, f.b32, 1.0 / sc, H->partial, s));
+            }
+        }
         if (bad(rr)) {
             rc = fail(MG_ERR_NONFINITE, "non-finite residual");
             break;
@@ -791,17 +854,12 @@ extern "C" int mg_solve_mixed(mg_handle *H, const double *b, double *x, double t
             rc = fail(MG_ERR_DIVERGED, "residual grew to %.3e", rel);
             break;
         }
-        // scale by a power of two (exact) so that FP32 holds the residual at O(1)
-        double mx = 0;
-        CHK(device_max(H, H->cg64.r, n, &mx, s));
-        int ex = 0;
-        std::frexp(mx, &ex);
-        const double sc = std::ldexp(1.0, ex);
-        KRUN(K_VEC, 0, 1, launch_cast_scaled(H->cg64.r, f.b32, 1.0 / sc, n, s));
         CU(cudaMemsetAsync(H->cg32.x, 0, n * sizeof(float), s));
         int its_in = 0;
         double rel_in = 0;
-        const int rin = solve_impl<float>(H, f.b32, H->cg32.x, H->p.inner_tol, H->p.inner_maxit,
+        // solve no further than the outer target still needs (safety 0.3)
+        const double itol = inner_tolerance(H->p.inner_tol, tol, rel);
+        const int rin = solve_impl<float>(H, f.b32, H->cg32.x, itol, H->p.inner_maxit,
                                           H->p.method, nullptr, &its_in, &rel_in, s, true);
         if (rin != MG_OK && rin != MG_ERR_NOT_CONVERGED && rin != MG_ERR_DIVERGED) {
             rc = rin;
@@ -810,6 +868,7 @@ extern "C" int mg_solve_mixed(mg_handle *H, const double *b, double *x, double t
         inner += its_in;
         // the FP32 hierarchy holds c H: (c H) e = r / sc  =>  x += c sc e
         KRUN(K_VEC, 0, 0, launch_update_mixed(x, H->cg32.x, H->scale32 * sc, n, s));
+        pred = std::sqrt(rr) * std::max(rel_in, 1e-6);
         ++outer;
     }
     fill_stats(st, hist, outer, inner, rel);
@@ -946,4 +1005,27 @@ extern "C" int mg_level_prolong_add(mg_handle *H, int level, int prec, const voi
                                     void *stream)
 {
     return level_dispatch(H, level, prec, 4, ec, nullptr, u, stream);
+}
+
+extern "C" int mg_level_smooth_dot(mg_handle *H, int level, int prec, const void *b,
+                                   const void *u_in, void *u_out, double *dot, void *stream)
+{
+    CHK(level_check(H, level, prec, false));
+    if (!b || !u_in || !u_out || !dot || u_in == u_out || b == u_out)
+        return fail(MG_ERR_ARG, "bad smoother buffers");
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelHost &v = H->lev[level];
+    int nb = 0;
+    if (prec == MG_PREC_FP64) {
+        KRUN(K_SMOOTH, level, 0, nb = launch_smooth_dot<double>(dev<double>(v), (const double *)b,
+                                                            (const double *)u_in,
+                                                            (double *)u_out, H->p.omega,
+                                                            H->partial, s));
+    } else {
+        KRUN(K_SMOOTH, level, 1, nb = launch_smooth_dot<float>(dev<float>(v), (const float *)b,
+                                                           (const float *)u_in, (float *)u_out,
+                                                           H->p.omega, H->partial, s));
+    }
+    KRUN(K_VEC, level, prec, launch_finalize(H->partial, nb, H->sc, S_RZ, 0, s));
+    return read_scalar(H, S_RZ, dot, s);
 }

@@ -24,8 +24,11 @@ __global__ void __launch_bounds__(kBlock, 4) k_bsmooth(const BOp<T> *__restrict_
         const BItem item = items[it];
         const BOp<T> &op = ops[item.op];
         if (active && !active[op.sys]) continue;
-        smooth_column<T, ZERO, true>(op.L, op.a, op.x, op.y, omega,
-                                     item.tile * blockDim.x + threadIdx.x, smraw);
+        const int col = item.tile * blockDim.x + threadIdx.x;
+        if (ZERO)
+            smooth_staged<T, true>(op.L, op.a, nullptr, op.y, omega, col, smraw);
+        else
+            smooth_column<T, false, true>(op.L, op.a, op.x, op.y, omega, col, smraw);
     }
 }
 
@@ -35,29 +38,29 @@ cudaError_t launch_bsmooth(const BOp<T> *ops, const BItem *items, int nitems, bo
                            cudaStream_t s)
 {
     if (nitems <= 0) return cudaSuccess;
-    const size_t smem = (size_t)nzmax * block * sizeof(T);
-    if (zero)
+    if (zero) {
+        const size_t smem = ring_smem_bytes<T, true>(nzmax, block);
         k_bsmooth<T, true><<<grid, block, smem, s>>>(ops, items, nitems, (T)omega, active);
-    else
+    } else {
+        const size_t smem = (size_t)nzmax * block * sizeof(T);
         k_bsmooth<T, false><<<grid, block, smem, s>>>(ops, items, nitems, (T)omega, active);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t bsmooth_prepare()
 {
-    const int lim = 200 * 1024;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_bsmooth<double, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+    int dev = 0, lim = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
+        cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_bsmooth<double, false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_bsmooth<float, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(k_bsmooth<float, false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    const void *kernels[] = {(const void *)k_bsmooth<double, true>, (const void *)k_bsmooth<double, false>,
+                             (const void *)k_bsmooth<float, true>, (const void *)k_bsmooth<float, false>};
+    for (const void *k : kernels)
+        if ((e = set_dynamic_smem_limit(k, lim)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 template <typename T, int KIND>

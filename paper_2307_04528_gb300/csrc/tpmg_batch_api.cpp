@@ -991,7 +991,11 @@ extern "C" int mg_batch_solve(mg_batch *B, const double *const *b, double *const
                     CU(cudaMemsetAsync(B->h[i]->cg32.x, 0, B->h[i]->lev[0].n * sizeof(float), s));
             std::vector<int> ist, iits;
             std::vector<double> irel;
-            CHK(batch_cg<float>(B, act, B->p.inner_tol, B->p.inner_maxit, ist, iits, irel, s));
+            // one inner tolerance for the batch: the loosest any system can use
+            double itol = 0.5;
+            for (int i = 0; i < n; ++i)
+                if (act[i]) itol = std::min(itol, inner_tolerance(B->p.inner_tol, tol, relv[i]));
+            CHK(batch_cg<float>(B, act, itol, B->p.inner_maxit, ist, iits, irel, s));
             for (int i = 0; i < n; ++i) {
                 if (!act[i]) continue;
                 if (ist[i] == MG_ERR_NONFINITE) { st[i] = MG_ERR_NONFINITE; act[i] = 0; continue; }

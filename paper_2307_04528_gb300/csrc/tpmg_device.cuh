@@ -49,11 +49,43 @@ __device__ __forceinline__ void block_store(double v, double *partial)
 // ------------------------------------------------------------------ stencil
 // Column loop of the stencil: y = H x (MODE 0) or b - H x (MODE 1) for one
 // column; returns the column's contribution to sum(y*y) (MODE 1) or
-// sum(x*y) (MODE 0) when RED.
-template <typename T, int MODE, bool RED>
-__device__ __forceinline__ T stencil_column(const LevelDev<T> &L, const T *__restrict__ b,
-                                            const T *__restrict__ x, T *__restrict__ y, int col)
+// sum(x*y) (MODE 0) when RED.  Loads of layers k+1..k+DEPTH are in flight
+// while layer k is computed (register pipeline).
+template <typename T>
+struct StencilLoads {
+    T xc, tz, h, txc, txw, tyn, tys, xe, xw, xn, xs, b;
+};
+
+template <typename T, int MODE>
+__device__ __forceinline__ void stencil_load(StencilLoads<T> &s, const LevelDev<T> &L,
+                                             const T *__restrict__ b, const T *__restrict__ x,
+                                             size_t o, int col, int ie, int iw, int nlon,
+                                             bool hasN, bool hasS)
 {
+    s.xc = __ldg(x + o + col);
+    s.tz = __ldg(L.tz + o + col);
+    s.h = __ldg(L.h + o + col);
+    s.txc = __ldg(L.tx + o + col);
+    s.txw = __ldg(L.tx + o + iw);
+    s.xe = __ldg(x + o + ie);
+    s.xw = __ldg(x + o + iw);
+    s.tyn = hasN ? __ldg(L.ty + o + col) : T(0);
+    s.xn = hasN ? __ldg(x + o + col + nlon) : T(0);
+    s.tys = hasS ? __ldg(L.ty + o + col - nlon) : T(0);
+    s.xs = hasS ? __ldg(x + o + col - nlon) : T(0);
+    if (MODE) s.b = __ldg(b + o + col);
+}
+
+// TO != T: y receives the rounding of out * yscale (the FP64 residual
+// handed to the FP32 inner solve; yscale a power of two).  NARROW_MUL: the
+// product is formed in TO after the rounding, exact for a yscale that is a
+// normal TO value (one FP64 operation fewer per cell).  The reduction uses out.
+template <typename T, int MODE, bool RED, typename TO = T, bool NARROW_MUL = false>
+__device__ __forceinline__ T stencil_column(const LevelDev<T> &L, const T *__restrict__ b,
+                                            const T *__restrict__ x, TO *__restrict__ y, int col,
+                                            T yscale = T(1))
+{
+    constexpr int kDepth = sizeof(T) == 8 ? 2 : 4;
     const int nlon = L.nlon, nlat = L.nlat, nz = L.nz;
     const int ncol = nlon * nlat;
     T acc = 0;
@@ -63,25 +95,42 @@ __device__ __forceinline__ T stencil_column(const LevelDev<T> &L, const T *__res
         const int iw = (i == 0) ? col + nlon - 1 : col - 1;
         const bool hasN = j + 1 < nlat, hasS = j > 0;
         const size_t plane = (size_t)ncol;
+        StencilLoads<T> st[kDepth];
+#pragma unroll
+        for (int d = 0; d < kDepth; ++d)
+            if (d < nz)
+                stencil_load<T, MODE>(st[d], L, b, x, (size_t)d * plane, col, ie, iw, nlon, hasN,
+                                      hasS);
         T xdn = 0, tdn = 0;
-        T xc = x[col];
-        for (int k = 0; k < nz; ++k) {
-            const size_t o = (size_t)k * plane;
-            const T xup = (k + 1 < nz) ? x[o + plane + col] : T(0);
-            const T tup = L.tz[o + col];
-            T v = L.h[o + col] * xc;
-            v = fma(L.tx[o + col], xc - x[o + ie], v);
-            v = fma(L.tx[o + iw], xc - x[o + iw], v);
-            if (hasN) v = fma(L.ty[o + col], xc - x[o + col + nlon], v);
-            if (hasS) v = fma(L.ty[o + col - nlon], xc - x[o + col - nlon], v);
-            v = fma(tup, xc - xup, v);
-            v = fma(tdn, xc - xdn, v);
-            const T out = MODE ? b[o + col] - v : v;
-            y[o + col] = out;
-            if (RED) acc = fma(out, MODE ? out : xc, acc);
-            xdn = xc;
-            xc = xup;
-            tdn = tup;
+        for (int k0 = 0; k0 < nz; k0 += kDepth) {
+#pragma unroll
+            for (int d = 0; d < kDepth; ++d) {
+                const int k = k0 + d;
+                if (k < nz) {
+                    const StencilLoads<T> &c = st[d];
+                    const T xc = c.xc;
+                    const T xup = (k + 1 < nz) ? st[(d + 1) % kDepth].xc : T(0);
+                    T v = c.h * xc;
+                    v = fma(c.txc, xc - c.xe, v);
+                    v = fma(c.txw, xc - c.xw, v);
+                    if (hasN) v = fma(c.tyn, xc - c.xn, v);
+                    if (hasS) v = fma(c.tys, xc - c.xs, v);
+                    v = fma(c.tz, xc - xup, v);
+                    v = fma(tdn, xc - xdn, v);
+                    const T out = MODE ? c.b - v : v;
+                    if constexpr (sizeof(TO) == sizeof(T))
+                        y[(size_t)k * plane + col] = out;
+                    else
+                        y[(size_t)k * plane + col] =
+                            NARROW_MUL ? (TO)out * (TO)yscale : (TO)(out * yscale);
+                    if (RED) acc = fma(out, MODE ? out : xc, acc);
+                    xdn = xc;
+                    tdn = c.tz;
+                    if (k + kDepth < nz)
+                        stencil_load<T, MODE>(st[d], L, b, x, (size_t)(k + kDepth) * plane, col, ie,
+                                              iw, nlon, hasN, hasS);
+                }
+            }
         }
     }
     return acc;
@@ -131,7 +180,10 @@ __device__ __forceinline__ void stencil_cell(const LevelDev<T> &L, const T *__re
 // for FP64 (FP64-ALU-bound, twice the registers per value).
 template <typename T, bool ZERO>
 struct SmoothDepth {
-    static constexpr int value = sizeof(T) == 8 ? (ZERO ? 4 : 3) : (ZERO ? 4 : 6);
+    // forward sweep: layers of loads in flight per thread
+    static constexpr int value = sizeof(T) == 8 ? (ZERO ? 4 : 3) : (ZERO ? 16 : 6);
+    // backward sweep (one or two streams per layer): deeper
+    static constexpr int back = sizeof(T) == 8 ? 4 : (ZERO ? 16 : 12);
 };
 
 template <typename T>
@@ -164,11 +216,14 @@ __device__ __forceinline__ void smooth_load(SmoothLoads<T> &s, const LevelDev<T>
 }
 
 // One column of the sweep.  smraw: this block's dynamic shared memory
-// (nz * blockDim values of T per stored array).
-template <typename T, bool ZERO, bool PRE>
+// (nz * blockDim values of T per stored array).  DOT: also accumulate
+// sum_k b_k u_out,k of the column into *dacc (the CG inner product <r, z>
+// when the sweep is the last one of a V-cycle applied to r).
+template <typename T, bool ZERO, bool PRE, bool DOT = false>
 __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__restrict__ b,
                                               const T *__restrict__ uin, T *__restrict__ uout,
-                                              T omega, int col, unsigned char *smraw)
+                                              T omega, int col, unsigned char *smraw,
+                                              T *dacc = nullptr)
 {
     constexpr int kDepth = SmoothDepth<T, ZERO>::value;
     const int nlon = L.nlon, nlat = L.nlat, nz = L.nz;
@@ -228,20 +283,22 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
 
     const T om1 = T(1) - omega;
     T xk = yprev;
-    // backward sweep: prefetch u_in (and the precomputed q/p) kDepth layers ahead
-    T up[kDepth], dqp[kDepth];
+    // backward sweep: prefetch u_in (and the precomputed q/p) kBack layers ahead
+    constexpr int kBack = SmoothDepth<T, ZERO>::back;
+    T up[kBack], dqp[kBack], bp[kBack];
 #pragma unroll
-    for (int d = 0; d < kDepth; ++d) {
+    for (int d = 0; d < kBack; ++d) {
         const int k = nz - 1 - d;
         if (k >= 0) {
             const size_t o = (size_t)k * plane + col;
             up[d] = ZERO ? T(0) : __ldg(uin + o);
             dqp[d] = PRE ? __ldg(L.dq + o) : T(0);
+            bp[d] = DOT ? __ldg(b + o) : T(0);
         }
     }
-    for (int k0 = nz - 1; k0 >= 0; k0 -= kDepth) {
+    for (int k0 = nz - 1; k0 >= 0; k0 -= kBack) {
 #pragma unroll
-        for (int d = 0; d < kDepth; ++d) {
+        for (int d = 0; d < kBack; ++d) {
             const int k = k0 - d;
             if (k >= 0) {
                 const size_t o = (size_t)k * plane + col;
@@ -249,16 +306,204 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
                     const T dqk = PRE ? dqp[d] : ds[(size_t)k * bd + tid];
                     xk = xk + fma(-dqk, xk, ys[(size_t)k * bd + tid]);
                 }
-                uout[o] = ZERO ? omega * xk : fma(om1, up[d], omega * xk);
-                const int kn = k - kDepth;
+                const T uo = ZERO ? omega * xk : fma(om1, up[d], omega * xk);
+                uout[o] = uo;
+                if (DOT) *dacc = fma(bp[d], uo, *dacc);
+                const int kn = k - kBack;
                 if (kn >= 0) {
                     const size_t on = (size_t)kn * plane + col;
                     if (!ZERO) up[d] = __ldg(uin + on);
                     if (PRE) dqp[d] = __ldg(L.dq + on);
+                    if (DOT) bp[d] = __ldg(b + on);
                 }
             }
         }
     }
+}
+
+// ------------------------------------------------------------------ staged sweep
+// Asynchronous global->shared copies (cp.async, 4 or 8 bytes per thread).
+// Each thread stages and later reads only its own slots, so completion of
+// its own copy groups (cp.async.wait_group) is the only synchronisation.
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+template <typename T>
+__device__ __forceinline__ void stage(T *dst, const T *src)
+{
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte values");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "n"((int)sizeof(T))
+                 : "memory");
+}
+
+__device__ __forceinline__ void stage_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void stage_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Layers in flight per thread in the staged sweep, and values staged per
+// layer: forward b, t_z, 1/p (+ t_x east/west, t_y north/south and the four
+// horizontal neighbours of u_in unless the guess is zero); backward q/p
+// (+ u_in, + b for the fused inner product).
+constexpr int kRing = 8;
+
+template <bool ZERO>
+struct RingSlot {
+    static constexpr int NV = ZERO ? 3 : 11;
+    enum { B = 0, TZ = 1, M = 2, TXC = 3, TXW = 4, TYN = 5, TYS = 6, UE = 7, UW = 8, UN = 9, US = 10 };
+};
+
+// Shared memory of one block of the staged sweep: the ring and the forward
+// values y (nz per column).
+template <typename T, bool ZERO>
+__host__ __device__ constexpr size_t ring_smem_bytes(int nz, int block)
+{
+    return ((size_t)kRing * RingSlot<ZERO>::NV + (size_t)nz) * (size_t)block * sizeof(T);
+}
+
+// One column of the sweep of Eq. (1) on precomputed factors (m = 1/p,
+// dq = q/p), the same arithmetic in the same order as smooth_column, with
+// every load staged kRing layers ahead through shared memory by cp.async
+// (the copies hold no registers, so the depth of the pipeline is not left to
+// register allocation).  Horizontal neighbours missing at the poles read as 0
+// (their slots are zeroed once and never staged).
+template <typename T, bool ZERO, bool DOT = false>
+__device__ __forceinline__ void smooth_staged(const LevelDev<T> &L, const T *__restrict__ b,
+                                              const T *__restrict__ uin, T *__restrict__ uout,
+                                              T omega, int col, unsigned char *smraw,
+                                              T *dacc = nullptr)
+{
+    using S = RingSlot<ZERO>;
+    constexpr int NV = S::NV;
+    const int nlon = L.nlon, nlat = L.nlat, nz = L.nz;
+    const int ncol = nlon * nlat;
+    if (col >= ncol) return;
+    const int bd = blockDim.x;
+    T *ring = reinterpret_cast<T *>(smraw) + threadIdx.x;  // [kRing][NV][bd]
+    T *ys = reinterpret_cast<T *>(smraw) + (size_t)kRing * NV * bd + threadIdx.x;  // [nz][bd]
+    const int j = col / nlon, i = col - j * nlon;
+    const int ie = (i + 1 == nlon) ? col - i : col + 1;
+    const int iw = (i == 0) ? col + nlon - 1 : col - 1;
+    const bool hasN = j + 1 < nlat, hasS = j > 0;
+    const size_t plane = (size_t)ncol;
+
+    // sources of the next layer to stage (advanced by one plane per layer)
+    const T *pb = b + col, *pt = L.tz + col, *pm = L.m + col;
+    const T *ptc = L.tx + col, *ptw = L.tx + iw;
+    const T *pyn = L.ty + col, *pys = hasS ? L.ty + col - nlon : pyn;
+    const T *ub = ZERO ? b : uin;  // u_in is not read from a zero guess
+    const T *pue = ub + ie, *puw = ub + iw;
+    const T *pun = hasN ? ub + col + nlon : pue, *pus = hasS ? ub + col - nlon : pue;
+    if (!ZERO) {
+        for (int d = 0; d < kRing; ++d) {
+            T *sl = ring + (size_t)d * NV * bd;
+            if (!hasN) sl[S::TYN * bd] = sl[S::UN * bd] = T(0);
+            if (!hasS) sl[S::TYS * bd] = sl[S::US * bd] = T(0);
+        }
+    }
+    auto issue = [&](int slot) {
+        T *sl = ring + (size_t)slot * NV * bd;
+        stage(sl + S::B * bd, pb);
+        stage(sl + S::TZ * bd, pt);
+        stage(sl + S::M * bd, pm);
+        pb += plane;
+        pt += plane;
+        pm += plane;
+        if (!ZERO) {
+            stage(sl + S::TXC * bd, ptc);
+            stage(sl + S::TXW * bd, ptw);
+            stage(sl + S::UE * bd, pue);
+            stage(sl + S::UW * bd, puw);
+            if (hasN) {
+                stage(sl + S::TYN * bd, pyn);
+                stage(sl + S::UN * bd, pun);
+            }
+            if (hasS) {
+                stage(sl + S::TYS * bd, pys);
+                stage(sl + S::US * bd, pus);
+            }
+            ptc += plane;
+            ptw += plane;
+            pyn += plane;
+            pys += plane;
+            pue += plane;
+            puw += plane;
+            pun += plane;
+            pus += plane;
+        }
+    };
+    for (int d = 0; d < kRing; ++d) {
+        if (d < nz) issue(d);
+        stage_commit();
+    }
+    T yprev = 0, tdn = 0;
+    int slot = 0;
+    for (int k = 0; k < nz; ++k) {
+        stage_wait<kRing - 1>();  // layer k has landed
+        const T *sl = ring + (size_t)slot * NV * bd;
+        T v = sl[S::B * bd];
+        if (!ZERO) {
+            v = fma(sl[S::TXC * bd], sl[S::UE * bd], v);
+            v = fma(sl[S::TXW * bd], sl[S::UW * bd], v);
+            v = fma(sl[S::TYN * bd], sl[S::UN * bd], v);
+            v = fma(sl[S::TYS * bd], sl[S::US * bd], v);
+        }
+        const T y = fma(tdn, yprev, v) * sl[S::M * bd];
+        tdn = sl[S::TZ * bd];
+        ys[(size_t)k * bd] = y;
+        yprev = y;
+        if (k + kRing < nz) issue(slot);
+        stage_commit();
+        slot = (slot + 1 == kRing) ? 0 : slot + 1;
+    }
+    stage_wait<0>();
+
+    // backward sweep: stage q/p (+ u_in, + b) of layers nz-1, nz-2, ...
+    const size_t top = (size_t)(nz - 1) * plane + col;
+    const T *qq = L.dq + top, *qu = (ZERO ? b : uin) + top, *qb = b + top;
+    auto issue_back = [&](int sl_) {
+        T *sl = ring + (size_t)sl_ * NV * bd;
+        stage(sl, qq);
+        qq -= plane;
+        if (!ZERO) {
+            stage(sl + bd, qu);
+            qu -= plane;
+        }
+        if (DOT) {
+            stage(sl + 2 * bd, qb);
+            qb -= plane;
+        }
+    };
+    for (int d = 0; d < kRing; ++d) {
+        if (nz - 1 - d >= 0) issue_back(d);
+        stage_commit();
+    }
+    const T om1 = T(1) - omega;
+    T xk = yprev;
+    T *uo_p = uout + top;
+    slot = 0;
+    for (int k = nz - 1; k >= 0; --k) {
+        stage_wait<kRing - 1>();
+        const T *sl = ring + (size_t)slot * NV * bd;
+        if (k < nz - 1) xk = xk + fma(-sl[0], xk, ys[(size_t)k * bd]);
+        const T uo = ZERO ? omega * xk : fma(om1, sl[bd], omega * xk);
+        *uo_p = uo;
+        uo_p -= plane;
+        if (DOT) *dacc = fma(sl[2 * bd], uo, *dacc);
+        if (k - kRing >= 0) issue_back(slot);
+        stage_commit();
+        slot = (slot + 1 == kRing) ? 0 : slot + 1;
+    }
+    stage_wait<0>();
 }
 
 // ------------------------------------------------------------------ transfers
@@ -326,6 +571,94 @@ __device__ __forceinline__ void prolong_pair(const LevelDev<T> &F, const LinkDev
     T *uk = u + (size_t)k * nf * F.nlat + (size_t)j * nf + 2 * I;
     uk[0] += a0;
     uk[1] += a1;
+}
+
+// Layers k0 <= k < k1 of one coarse column of the restriction: the row
+// list of J (at most 4 fine rows for the semi-coarsening row maps) and the
+// longitude indices are read once, then every layer issues its loads
+// independently of the others.  Same arithmetic, same order as
+// restrict_cell.
+template <typename T>
+__device__ __forceinline__ void restrict_layers(const LevelDev<T> &F, const LinkDev &K,
+                                                const T *__restrict__ r, T *__restrict__ bc,
+                                                int col, int k0, int k1)
+{
+    const int nf = F.nlon, nc = nf / 2;
+    const int ncol_c = nc * K.nlat_c;
+    if (col >= ncol_c) return;
+    const int J = col / nc, I = col - J * nc;
+    const int i0 = 2 * I, i1 = 2 * I + 1;
+    const int im = (i0 == 0) ? nf - 1 : i0 - 1;
+    const int ip = (i1 + 1 == nf) ? 0 : i1 + 1;
+    const int p0 = __ldg(K.rptr + J), cnt = __ldg(K.rptr + J + 1) - p0;
+    if (cnt > 4) {  // general row lists
+        for (int k = k0; k < k1; ++k) restrict_cell<T>(F, K, r, bc, col, k);
+        return;
+    }
+    const size_t plane_f = (size_t)nf * F.nlat, plane_c = (size_t)ncol_c;
+    int off[4];
+    T w[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        off[a] = a < cnt ? __ldg(K.rrow + p0 + a) * nf : 0;
+        w[a] = a < cnt ? (T)__ldg(K.rw + p0 + a) : T(0);
+    }
+    const T q1 = T(0.25), q3 = T(0.75);
+#pragma unroll 2
+    for (int k = k0; k < k1; ++k) {
+        const T *rk = r + (size_t)k * plane_f;
+        T acc = 0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            if (a < cnt) {
+                const T *row = rk + off[a];
+                acc = fma(w[a],
+                          fma(q1, __ldg(row + im) + __ldg(row + ip),
+                              q3 * (__ldg(row + i0) + __ldg(row + i1))),
+                          acc);
+            }
+        }
+        bc[(size_t)k * plane_c + col] = acc;
+    }
+}
+
+// Layers k0 <= k < k1 of one pair of fine columns of the prolongation and
+// correction (row links read once); same arithmetic as prolong_pair.
+template <typename T>
+__device__ __forceinline__ void prolong_layers(const LevelDev<T> &F, const LinkDev &K,
+                                               const T *__restrict__ ec, T *__restrict__ u, int t,
+                                               int k0, int k1)
+{
+    const int nf = F.nlon, nc = nf / 2;
+    const int npair = nc * F.nlat;
+    if (t >= npair) return;
+    const int j = t / nc, I = t - j * nc;
+    const int Im = (I == 0) ? nc - 1 : I - 1;
+    const int Ip = (I + 1 == nc) ? 0 : I + 1;
+    const int Ja = __ldg(K.j0 + j), Jb = __ldg(K.j1 + j);
+    const size_t plane_c = (size_t)nc * K.nlat_c, plane_f = (size_t)nf * F.nlat;
+    const T q1 = T(0.25), q3 = T(0.75);
+    const T wa = (T)__ldg(K.w0 + j);
+    const T wb = Jb >= 0 ? (T)__ldg(K.w1 + j) : T(0);
+    const size_t oa = (size_t)Ja * nc, ob = (size_t)(Jb >= 0 ? Jb : Ja) * nc;
+    const size_t of = (size_t)j * nf + 2 * I;
+#pragma unroll 1
+    for (int k = k0; k < k1; ++k) {
+        const T *ek = ec + (size_t)k * plane_c;
+        const T *ea = ek + oa;
+        const T ca = __ldg(ea + I);
+        T a0 = wa * fma(q3, ca, q1 * __ldg(ea + Im));
+        T a1 = wa * fma(q3, ca, q1 * __ldg(ea + Ip));
+        if (Jb >= 0) {
+            const T *eb = ek + ob;
+            const T cb = __ldg(eb + I);
+            a0 = fma(wb, fma(q3, cb, q1 * __ldg(eb + Im)), a0);
+            a1 = fma(wb, fma(q3, cb, q1 * __ldg(eb + Ip)), a1);
+        }
+        T *uk = u + (size_t)k * plane_f + of;
+        uk[0] += a0;
+        uk[1] += a1;
+    }
 }
 
 }  // namespace tpmg

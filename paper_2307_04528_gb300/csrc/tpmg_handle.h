@@ -86,6 +86,7 @@ struct VGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned long long kernels = 0;  // kernel nodes, for the launch count
+    int dot_blocks = 0;              // partial sums of the fused <r, z> it leaves
 };
 
 struct mg_handle {
@@ -192,4 +193,5 @@ int handle_plan(const mg_grid *g, const mg_params *p, void *ws, size_t *bytes, m
 // hierarchy, factors, FP32 copies).
 int handle_setup(mg_handle *H, const mg_coeffs *co, void *ws, size_t ws_bytes, cudaStream_t s);
 int read_scalars(mg_handle *H, int which, double *out, cudaStream_t s);
+double inner_tolerance(double inner_tol, double tol, double rel);
 }  // namespace tpmg

@@ -56,9 +56,20 @@ template <typename T>
 cudaError_t launch_smooth(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out,
                           double omega, cudaStream_t s);
 
+// The same sweep (non-zero guess) writing the block sums of <b, u_out> to
+// partial[block]; returns the number of blocks.
+template <typename T>
+int launch_smooth_dot(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out, double omega,
+                      double *partial, cudaStream_t s);
+
 // Raise the dynamic shared-memory limit of the smoother kernels (once per
 // process and device, before any stream capture).
 cudaError_t smooth_prepare();
+// dynamic shared memory a kernel may use: lim less its static shared memory
+cudaError_t set_dynamic_smem_limit(const void *kernel, int lim);
+// dynamic shared memory of the largest smoother block for nz layers of
+// value_bytes-wide values
+size_t smooth_smem_bytes(int nz, size_t value_bytes);
 
 template <typename T>
 cudaError_t launch_restrict(const LevelDev<T> &F, const LinkDev &K, const T *r, T *bc,
@@ -97,6 +108,10 @@ template <typename T>
 cudaError_t launch_add(T *x, const T *e, size_t n, cudaStream_t s);
 
 // r32 = (float)(r64 * inv_scale)
+// r32 = (float)((b - H x) * inv_scale) and ||b - H x||^2 partial sums;
+// returns the number of partial sums.
+int launch_residual_cast(const LevelDev<double> &L, const double *b, const double *x, float *r32,
+                         double inv_scale, double *partial, cudaStream_t s);
 cudaError_t launch_cast_scaled(const double *r, float *r32, double inv_scale, size_t n,
                                cudaStream_t s);
 // x64 += scale * (double)e32

@@ -20,6 +20,10 @@
 
 namespace tpmg {
 
+// SM count of the device (set at setup; sizes the work split of the
+// cell-parallel transfers).
+static int g_sms = 152;
+
 // ------------------------------------------------------------------ stencil
 // mode 0: y = H x;  mode 1: y = b - H x.  Flux form
 //   (H x)_c = h_c x_c + sum_f T_f (x_c - x_nb(f)).
@@ -30,6 +34,33 @@ k_stencil(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ x, T *__
 {
     const T acc = stencil_column<T, MODE, RED>(L, b, x, y, blockIdx.x * blockDim.x + threadIdx.x);
     if (RED) block_store<0>((double)acc, partial);
+}
+
+// r32 = (float)((b - H x) * inv_scale) with the FP64 residual and the block
+// sums of ||b - H x||^2 (the outer step of the mixed-precision refinement:
+// no FP64 residual vector is stored).
+template <bool NARROW_MUL>
+__global__ void __launch_bounds__(kBlock)
+k_resid_cast(LevelDev<double> L, const double *__restrict__ b, const double *__restrict__ x,
+             float *__restrict__ r32, double inv_scale, double *__restrict__ partial)
+{
+    const double acc = stencil_column<double, 1, true, float, NARROW_MUL>(
+        L, b, x, r32, blockIdx.x * blockDim.x + threadIdx.x, inv_scale);
+    block_store<0>(acc, partial);
+}
+
+int launch_residual_cast(const LevelDev<double> &L, const double *b, const double *x, float *r32,
+                         double inv_scale, double *partial, cudaStream_t s)
+{
+    const int ncol = L.nlon * L.nlat;
+    const int grid = (ncol + kBlock - 1) / kBlock;
+    // Scaling after the rounding to float is exact while the residual's
+    // significant entries are normal floats: |r| <= ||r|| < 2^10 / inv_scale
+    // stays below 2^110, and entries down to 2^-56 ||r|| stay above 2^-126.
+    const bool narrow = inv_scale >= 0x1p-100 && inv_scale <= 0x1p60;
+    if (narrow) k_resid_cast<true><<<grid, kBlock, 0, s>>>(L, b, x, r32, inv_scale, partial);
+    else k_resid_cast<false><<<grid, kBlock, 0, s>>>(L, b, x, r32, inv_scale, partial);
+    return grid;
 }
 
 // Cell-parallel variant (one thread per cell, grid = column blocks x layers)
@@ -73,58 +104,115 @@ int launch_stencil(const LevelDev<T> &L, int mode, const T *b, const T *x, T *y,
 // pivots p_k = q_k + t_k:
 //   forward   y_k = (v_k + t_{k-1} y_{k-1}) / p_k
 //   backward  x_k = x_{k+1} + (y_k - (q_k / p_k) x_{k+1})
-// PRE: 1/p_k and q_k/p_k read from the setup factors (FP64, and FP32 zero-guess
-// sweeps); otherwise q_k = s_k + t_{k-1} q_{k-1}/p_{k-1} is formed on the fly
-// (FP32: one reciprocal per cell, cheaper than reading two more arrays).
-// The forward values y (and q/p on the fly) wait in shared memory for the
-// backward sweep: blockDim x nz values per array.
+// on the setup factors 1/p_k and q_k/p_k.  The forward values y wait in
+// shared memory for the backward sweep (blockDim x nz values).
 //
-template <typename T, bool ZERO, bool PRE>
+// Sweeps from a zero guess (the pre-smoother of every level) read four
+// streams per cell (b, t_z, 1/p, q/p) and are staged through shared memory
+// by cp.async, kRing layers ahead (smooth_staged); sweeps on a non-zero guess
+// read eleven values per cell, and the register pipeline of smooth_column
+// keeps more of them in flight than a shared-memory ring of the same depth
+// would at its occupancy.
+template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_smooth(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ uin, T *__restrict__ uout,
          T omega)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    smooth_column<T, ZERO, PRE>(L, b, uin, uout, omega, blockIdx.x * blockDim.x + threadIdx.x,
-                                smraw);
+    smooth_column<T, false, true>(L, b, uin, uout, omega, blockIdx.x * blockDim.x + threadIdx.x,
+                                  smraw);
 }
 
-template <typename T, bool ZERO, bool PRE>
-static cudaError_t launch_smooth_impl(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out,
-                                      double omega, cudaStream_t s)
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_smooth0(LevelDev<T> L, const T *__restrict__ b, T *__restrict__ uout, T omega)
 {
-    const size_t smem = (size_t)L.nz * kBlock * sizeof(T) * (PRE ? 1 : 2);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    smooth_staged<T, true>(L, b, nullptr, uout, omega, blockIdx.x * blockDim.x + threadIdx.x,
+                           smraw);
+}
+
+// The last sweep of a V-cycle applied to r, with the block sums of
+// <r, u_out> (the CG inner product) written to partial[block].
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_smooth_dot(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ uin,
+             T *__restrict__ uout, T omega, double *__restrict__ partial)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T acc = 0;
+    smooth_column<T, false, true, true>(L, b, uin, uout, omega,
+                                        blockIdx.x * blockDim.x + threadIdx.x, smraw, &acc);
+    block_store<0>((double)acc, partial);
+}
+
+template <typename T>
+int launch_smooth_dot(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out, double omega,
+                      double *partial, cudaStream_t s)
+{
+    const size_t smem = (size_t)L.nz * kBlock * sizeof(T);
     const int ncol = L.nlon * L.nlat;
     const int grid = (ncol + kBlock - 1) / kBlock;
-    k_smooth<T, ZERO, PRE><<<grid, kBlock, smem, s>>>(L, b, u_in, u_out, (T)omega);
-    return cudaGetLastError();
+    k_smooth_dot<T><<<grid, kBlock, smem, s>>>(L, b, u_in, u_out, (T)omega, partial);
+    return grid;
 }
 
 template <typename T>
 cudaError_t launch_smooth(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out, double omega,
                           cudaStream_t s)
 {
-    if (u_in == nullptr) return launch_smooth_impl<T, true, true>(L, b, u_in, u_out, omega, s);
-    return launch_smooth_impl<T, false, true>(L, b, u_in, u_out, omega, s);
+    const int ncol = L.nlon * L.nlat;
+    const int grid = (ncol + kBlock - 1) / kBlock;
+    if (u_in == nullptr) {
+        const size_t smem = ring_smem_bytes<T, true>(L.nz, kBlock);
+        k_smooth0<T><<<grid, kBlock, smem, s>>>(L, b, u_out, (T)omega);
+    } else {
+        const size_t smem = (size_t)L.nz * kBlock * sizeof(T);
+        k_smooth<T><<<grid, kBlock, smem, s>>>(L, b, u_in, u_out, (T)omega);
+    }
+    return cudaGetLastError();
 }
 
-// Set the dynamic shared-memory limit of every smoother instantiation (must
-// precede stream capture).
+// Allow a kernel the opt-in shared memory per block (lim) less its static
+// shared memory as dynamic shared memory.
+cudaError_t set_dynamic_smem_limit(const void *kernel, int lim)
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                lim - (int)a.sharedSizeBytes);
+}
+
+// Set the dynamic shared-memory limit of every smoother kernel to the
+// opt-in maximum (must precede stream capture) and record the SM count.
 cudaError_t smooth_prepare()
 {
-    const int lim = 200 * 1024;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_smooth<double, true, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+    int dev = 0, sms = 0, lim = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_smooth<double, false, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
+    if ((e = cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
+        cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_smooth<float, true, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(k_smooth<float, false, true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (sms > 0) g_sms = sms;
+    const void *kernels[] = {(const void *)k_smooth<double>,     (const void *)k_smooth<float>,
+                             (const void *)k_smooth0<double>,    (const void *)k_smooth0<float>,
+                             (const void *)k_smooth_dot<double>, (const void *)k_smooth_dot<float>};
+    for (const void *k : kernels)
+        if ((e = set_dynamic_smem_limit(k, lim)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+// Largest dynamic shared memory one smoother block of kBlock columns needs
+// for nz layers (checked against the device limit at setup).
+size_t smooth_smem_bytes(int nz, size_t value_bytes)
+{
+    const size_t ring = value_bytes == 8 ? ring_smem_bytes<double, true>(nz, kBlock)
+                                         : ring_smem_bytes<float, true>(nz, kBlock);
+    const size_t plain = (size_t)nz * kBlock * value_bytes;
+    return ring > plain ? ring : plain;
 }
 
 // ------------------------------------------------------------------ transfers
@@ -134,9 +222,23 @@ cudaError_t smooth_prepare()
 // 2I, 2I+1, 2I+2 (mod nlon) with weights 1/4, 3/4, 3/4, 1/4.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
-k_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ r, T *__restrict__ bc)
+k_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ r, T *__restrict__ bc, int kz)
 {
-    restrict_cell<T>(F, K, r, bc, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
+    const int k0 = blockIdx.y * kz;
+    restrict_layers<T>(F, K, r, bc, blockIdx.x * blockDim.x + threadIdx.x, k0,
+                       min(F.nz, k0 + kz));
+}
+
+// Layers per thread of the cell-parallel transfers: enough column-layer
+// blocks for two waves of 16 blocks on every SM, and at most 16 layers.
+
+static int layers_per_thread(size_t columns, int nz)
+{
+    const size_t target = (size_t)g_sms * 16 * kBlock * 2;
+    size_t kz = columns * (size_t)nz / target;
+    if (kz < 1) kz = 1;
+    if (kz > 16) kz = 16;
+    return (int)kz;
 }
 
 template <typename T>
@@ -144,20 +246,23 @@ cudaError_t launch_restrict(const LevelDev<T> &F, const LinkDev &K, const T *r, 
                             cudaStream_t s)
 {
     const int ncol_c = (F.nlon / 2) * K.nlat_c;
-    const dim3 grid((ncol_c + kBlock - 1) / kBlock, F.nz);
-    k_restrict<T><<<grid, kBlock, 0, s>>>(F, K, r, bc);
+    const int kz = layers_per_thread(ncol_c, F.nz);
+    const dim3 grid((ncol_c + kBlock - 1) / kBlock, (F.nz + kz - 1) / kz);
+    k_restrict<T><<<grid, kBlock, 0, s>>>(F, K, r, bc, kz);
     return cudaGetLastError();
 }
 
 // Bilinear prolongation and correction, one thread per pair of fine cells
-// (i = 2I, 2I+1) of a layer: fine cell 2I adds sum_a w_a (3/4 e[J_a, I] +
-// 1/4 e[J_a, I-1]) and 2I+1 adds sum_a w_a (3/4 e[J_a, I] + 1/4 e[J_a, I+1])
-// (periodic in longitude); three coarse loads per coarse row serve both.
+// (i = 2I, 2I+1) over a range of layers: fine cell 2I adds sum_a w_a
+// (3/4 e[J_a, I] + 1/4 e[J_a, I-1]) and 2I+1 adds sum_a w_a (3/4 e[J_a, I] +
+// 1/4 e[J_a, I+1]) (periodic in longitude); three coarse loads per coarse
+// row serve both.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
-k_prolong_add(LevelDev<T> F, LinkDev K, const T *__restrict__ ec, T *__restrict__ u)
+k_prolong_add(LevelDev<T> F, LinkDev K, const T *__restrict__ ec, T *__restrict__ u, int kz)
 {
-    prolong_pair<T>(F, K, ec, u, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
+    const int k0 = blockIdx.y * kz;
+    prolong_layers<T>(F, K, ec, u, blockIdx.x * blockDim.x + threadIdx.x, k0, min(F.nz, k0 + kz));
 }
 
 template <typename T>
@@ -165,8 +270,9 @@ cudaError_t launch_prolong_add(const LevelDev<T> &F, const LinkDev &K, const T *
                                cudaStream_t s)
 {
     const int npair = (F.nlon / 2) * F.nlat;
-    const dim3 grid((npair + kBlock - 1) / kBlock, F.nz);
-    k_prolong_add<T><<<grid, kBlock, 0, s>>>(F, K, ec, u);
+    const int kz = layers_per_thread(npair, F.nz);
+    const dim3 grid((npair + kBlock - 1) / kBlock, (F.nz + kz - 1) / kz);
+    k_prolong_add<T><<<grid, kBlock, 0, s>>>(F, K, ec, u, kz);
     return cudaGetLastError();
 }
 
@@ -509,6 +615,8 @@ cudaError_t launch_coeff_grad(int nlon, int nlat, int nz, const double *lam, con
                                    cudaStream_t);                                                 \
     template cudaError_t launch_smooth<T>(const LevelDev<T> &, const T *, const T *, T *, double,  \
                                           cudaStream_t);                                          \
+    template int launch_smooth_dot<T>(const LevelDev<T> &, const T *, const T *, T *, double,      \
+                                      double *, cudaStream_t);                                    \
     template cudaError_t launch_restrict<T>(const LevelDev<T> &, const LinkDev &, const T *, T *,  \
                                             cudaStream_t);                                        \
     template cudaError_t launch_prolong_add<T>(const LevelDev<T> &, const LinkDev &, const T *,    \

@@ -22,6 +22,7 @@ if ROOT not in sys.path:
 # kernel name -> (precision, per-level entry point, words per cell)
 KERNELS = {
     "smooth32": (1, "smooth", 8),
+    "smooth32_dot": (1, "smooth_dot", 8),
     "smooth32_zero": (1, "smooth0", 5),
     "resid32": (1, "residual", 7),
     "apply32": (1, "apply", 6),
@@ -63,6 +64,8 @@ def main():
     def run():
         if op == "smooth":
             return H.level_smooth(0, b, u, prec=prec)
+        if op == "smooth_dot":
+            return H.level_smooth_dot(0, b, u, prec=prec)
         if op == "smooth0":
             return H.level_smooth(0, b, None, prec=prec)
         if op == "residual":

@@ -172,6 +172,15 @@ class MGHandle:
                                          _stream()))
         return out
 
+    def level_smooth_dot(self, level, b, u_in, prec=L.MG_PREC_FP64):
+        """One sweep plus <b, u_out> (the V-cycle's last sweep with the CG
+        inner product fused in)."""
+        out = torch.empty_like(b)
+        dot = ctypes.c_double()
+        L.check(self.lib.mg_level_smooth_dot(self._hh, level, prec, _ptr(b), _ptr(u_in), _ptr(out),
+                                             ctypes.byref(dot), _stream()))
+        return out, dot.value
+
     def level_restrict(self, level, r, prec=L.MG_PREC_FP64):
         shp = self.level_shape(level + 1)
         bc = torch.empty(shp, dtype=r.dtype, device=r.device)

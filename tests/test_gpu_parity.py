@@ -68,6 +68,30 @@ def test_smoother_fp64(case):
         assert rel_inf(got, ref) <= 1e-13
 
 
+def test_smoother_with_fused_dot(case):
+    """The V-cycle's last sweep with <b, u_out> fused: same sweep, and the
+    inner product of the oracle's sweep result (FP64 1e-13, FP32 2e-5)."""
+    P, lev, p, H = case
+    rng = np.random.default_rng(12)
+    for l, ol in enumerate(lev[:2]):
+        b = rng.standard_normal(ol.shape)
+        u = rng.standard_normal(ol.shape)
+        got, dot = H.level_smooth_dot(l, dev(b), dev(u))
+        ref = u.copy()
+        O.smooth(ol, b, ref, p.omega)
+        assert rel_inf(host(got), ref) <= 1e-13
+        want = O.dot(b, ref)
+        assert abs(dot - want) <= 1e-12 * O.norm2(b) * O.norm2(ref)
+    l32 = O.float_levels(lev)
+    b = rng.standard_normal(lev[0].shape).astype(np.float32)
+    u = rng.standard_normal(lev[0].shape).astype(np.float32)
+    got, dot = H.level_smooth_dot(0, dev(b, torch.float32), dev(u, torch.float32), prec=1)
+    ref = u.copy()
+    O.smooth(l32[0], b, ref, np.float32(p.omega))
+    assert rel_inf(host(got), ref) <= 2e-5
+    assert abs(dot - O.dot(b, ref)) <= 1e-5 * O.norm2(b) * O.norm2(ref)
+
+
 def test_transfers_fp64(case):
     P, lev, p, H = case
     rng = np.random.default_rng(3)

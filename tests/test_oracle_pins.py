@@ -266,7 +266,7 @@ def test_row_maps_worked_example_64x32():
     (centres up to 50.6 deg; the next pair at 61.9 deg has cos < 1/2), level
     2 merges 4 pairs, level 3 merges 3 pairs."""
     P = make_problem(64, 32, 4, 0.1, 0)
-    lev, _ = levels_of(P, levels=4)
+    lev, _ = levels_of(P, levels=4, alpha_c=0.5)
     assert [(l.nlon, l.nlat) for l in lev] == [(64, 32), (32, 22), (16, 14), (8, 8)]
     # level 1: rows 16..25 merged in pairs, 26..31 single
     r = lev[0].row_of
