@@ -174,7 +174,7 @@ KERNEL_WORDS = {
     (0, 1): ("smooth fp32 (+ <r, z>)", 8),            # u b tx ty tz m dq -> u
     (1, 1): ("smooth fp32 zero guess", 5),            # b tz m dq -> u
     (2, 1): ("residual fp32", 7),                     # u b tx ty tz h -> r
-    (3, 1): ("apply fp32", 6),                        # x tx ty tz h -> y
+    (3, 1): ("direction update + apply fp32", 8),     # z d tx ty tz h -> d q
     (0, 0): ("smooth fp64", 8),                       # u b tx ty tz m dq -> u
     (1, 0): ("smooth fp64 zero guess", 5),
     (2, 0): ("residual fp64 -> scaled fp32", 6.5),    # x b tx ty tz h -> r32
@@ -449,7 +449,8 @@ def run_ensemble(args):
                    "refinement_steps": [i["iterations"] for i in infos_b],
                    "fp32_iterations": [i["inner_iterations"] for i in infos_b],
                    "max_rel_res": max(i["rel_res"] for i in infos_b),
-                   "sequential_max_rel_res": max(i["rel_res"] for i in infos_s)},
+                   "sequential_max_rel_res": max(i["rel_res"] for i in infos_s),
+                   "sequential_fp32_iterations": [i["inner_iterations"] for i in infos_s]},
         "gpu_launches": int(launches), "clocks": clk,
     }
     print(json.dumps(out))

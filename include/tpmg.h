@@ -78,10 +78,10 @@ typedef struct {
                           MG_METHOD_STATIONARY (x <- x + V(b - H x), Section 2) */
     int mixed;         /* 1: also build the FP32 hierarchy for mg_solve_mixed */
     int maxit;         /* outer iterations (200) */
-    int inner_maxit;   /* mixed: FP32 iterations per FP64 refinement step (8) */
-    double omega;      /* Eq. (1) relaxation factor (0.8) */
+    int inner_maxit;   /* mixed: FP32 iterations per FP64 refinement step (12) */
+    double omega;      /* Eq. (1) relaxation factor (0.85) */
     double alpha_c;    /* Section 2.2 anisotropy threshold for merging rows (0.6) */
-    double inner_tol;  /* mixed: FP32 relative tolerance per refinement step (3e-3; loosened
+    double inner_tol;  /* mixed: FP32 relative tolerance per refinement step (5e-4; loosened
                           when the outer target needs less) */
 } mg_params;
 
@@ -195,8 +195,9 @@ double mg_fp32_scale(const mg_handle *h);
  * systems is one persistent-kernel launch over a precomputed work list of
  * (system level, column tile), the batched V-cycle is replayed from one CUDA
  * graph, and converged systems are switched off by device-side flags.
- * mg_batch_setup autotunes the smoother's column-tile width and the
- * persistent grid sizes on the batch itself (mg_batch_tuning reports them). */
+ * mg_batch_setup autotunes the smoother's column-tile width and persistent
+ * grid on the batch itself (mg_batch_tuning reports them); the other steps
+ * run on persistent grids of as many blocks as the GPU holds at once. */
 typedef struct mg_batch mg_batch;
 
 /* Workspace bytes for n systems with these grids and common params. */
@@ -215,8 +216,10 @@ void mg_batch_destroy(mg_batch *b);
 /* The handle of system i (owned by the batch; valid until mg_batch_destroy). */
 int mg_batch_handle(mg_batch *b, int i, mg_handle **out);
 
-/* Tuned launch shapes: smoother column-tile width (threads per block) and
- * persistent grid sizes of the smoother, cell-parallel and vector steps. */
+/* Launch shapes: the tuned smoother column-tile width (threads per block)
+ * and persistent grid; cell_grid and vec_grid are upper bounds of the
+ * cell-type and vector steps' grids (each launch takes the smaller of the
+ * bound and the kernel's resident grid). */
 int mg_batch_tuning(const mg_batch *b, int *smooth_block, int *smooth_grid, int *cell_grid,
                     int *vec_grid);
 

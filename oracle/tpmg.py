@@ -68,13 +68,13 @@ class MGParams:
     #                            Section 2.3's shallow hierarchy is levels=4
     nu1: int = 1               # pre-smoothing sweeps, V(1,1)
     nu2: int = 1               # post-smoothing sweeps
-    omega: float = 0.8         # Eq. (1) relaxation factor (value not printed)
+    omega: float = 0.85        # Eq. (1) relaxation factor (value not printed; tuned)
     coarse_iters: int = 8      # Section 2.3's "simple iterative method": block-Jacobi sweeps
     alpha_c: float = 0.6       # Section 2.2 anisotropy threshold (value not printed; tuned)
     method: str = "cg"         # outer iteration: "cg" (V-cycle-preconditioned CG) or "stationary"
     maxit: int = 200
-    inner_tol: float = 3e-3    # mixed precision: FP32 inner relative tolerance per refinement step
-    inner_maxit: int = 8       # mixed precision: FP32 inner iterations per refinement step
+    inner_tol: float = 5e-4    # mixed precision: FP32 inner relative tolerance per refinement step
+    inner_maxit: int = 12      # mixed precision: FP32 inner iterations per refinement step
 
 
 MIN_COARSE_NLON = 4

@@ -292,10 +292,10 @@ extern "C" void mg_default_params(mg_params *p)
     p->method = MG_METHOD_CG;
     p->mixed = 0;
     p->maxit = 200;
-    p->inner_maxit = 8;
-    p->omega = 0.8;
+    p->inner_maxit = 12;
+    p->omega = 0.85;
     p->alpha_c = 0.6;
-    p->inner_tol = 3e-3;
+    p->inner_tol = 5e-4;
 }
 
 extern "C" const char *mg_last_error(void) { return g_last_error.c_str(); }
@@ -710,12 +710,27 @@ static int solve_impl(mg_handle *H, const T *b, T *x, double tol, int maxit, int
         int nbd = vdot;
         if (!nbd) KRUN(K_VEC, 0, P, nbd = launch_dot<T>(cg.r, cg.z, n, H->partial, s));
         KRUN(K_VEC, 0, P, launch_finalize(H->partial, nbd, H->sc, S_RZ, 0, s));
-        T *d = cg.d0, *dn = cg.d1;
-        KRUN(K_VEC, 0, P, launch_cg_direction<T>(cg.z, nullptr, d, n, H->sc, true, s));
+        // d: current direction (none yet).  FP32: the direction update
+        // d = z + beta d runs inside the apply of the next iteration (free in a
+        // bandwidth-bound kernel); FP64 (ALU-bound) keeps the separate update,
+        // one FMA per cell instead of five.
+        constexpr bool fuse_direction = sizeof(T) == 4;
+        T *d = nullptr, *dn = cg.d0;
         while (its < maxit) {
             ++its;
             int na = 0, nu = 0;
-            KRUN(K_APPLY, 0, P, na = launch_stencil<T>(D, 0, nullptr, d, cg.Ad, H->partial, s));
+            if (fuse_direction) {
+                KRUN(K_APPLY, 0, P,
+                     na = launch_dir_apply<T>(D, cg.z, d, H->sc, dn, cg.Ad, H->partial, s));
+            } else {
+                KRUN(K_VEC, 0, P,
+                     launch_cg_direction<T>(cg.z, d, dn, n, H->sc, d == nullptr, s));
+                KRUN(K_APPLY, 0, P,
+                     na = launch_stencil<T>(D, 0, nullptr, dn, cg.Ad, H->partial, s));
+            }
+            T *const fresh = dn;               // the direction just formed
+            dn = (d == nullptr) ? cg.d1 : d;   // the old one's buffer takes the next
+            d = fresh;
             KRUN(K_VEC, 0, P, launch_finalize(H->partial, na, H->sc, S_DAD, 1, s));
             KRUN(K_VEC, 0, P, nu = launch_cg_update<T>(x, cg.r, d, cg.Ad, n, H->sc, H->partial, s));
             KRUN(K_VEC, 0, P, launch_finalize(H->partial, nu, H->sc, S_RR, 0, s));
@@ -736,8 +751,6 @@ static int solve_impl(mg_handle *H, const T *b, T *x, double tol, int maxit, int
             nbd = vdot;
             if (!nbd) KRUN(K_VEC, 0, P, nbd = launch_dot<T>(cg.r, cg.z, n, H->partial, s));
             KRUN(K_VEC, 0, P, launch_finalize(H->partial, nbd, H->sc, S_RZNEW, 2, s));
-            KRUN(K_VEC, 0, P, launch_cg_direction<T>(cg.z, d, dn, n, H->sc, false, s));
-            std::swap(d, dn);
         }
     }
 }

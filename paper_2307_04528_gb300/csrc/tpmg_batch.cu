@@ -10,10 +10,35 @@
 // arithmetic is the single-system code of tpmg_device.cuh.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "tpmg_device.cuh"
 #include "tpmg_internal.h"
 
 namespace tpmg {
+
+// Blocks of `kernel` the whole GPU holds at once (persistent grid for the
+// column-walk work lists), cached per kernel and block size.
+static int resident_grid(const void *kernel, int block, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(kernel, block);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int dev = 0, sms = 1, per_sm = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess)
+        return 152;
+    const int g = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    cache[key] = g;
+    return g;
+}
 
 template <typename T, bool ZERO>
 __global__ void __launch_bounds__(kBlock, 4) k_bsmooth(const BOp<T> *__restrict__ ops, const BItem *__restrict__ items,
@@ -48,6 +73,34 @@ cudaError_t launch_bsmooth(const BOp<T> *ops, const BItem *items, int nitems, bo
     return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kBlock, 4) k_bsmooth_dot(const BOp<T> *__restrict__ ops, const BItem *__restrict__ items,
+                              int nitems, T omega, const int *__restrict__ active,
+                              double *__restrict__ partial)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BItem item = items[it];
+        const BOp<T> &op = ops[item.op];
+        if (active && !active[op.sys]) continue;
+        T acc = 0;
+        smooth_column<T, false, true, true, 6>(op.L, op.a, op.x, op.y, omega,
+                                               item.tile * blockDim.x + threadIdx.x, smraw, &acc);
+        block_store_at<0>((double)acc, partial, it);
+    }
+}
+
+template <typename T>
+cudaError_t launch_bsmooth_dot(const BOp<T> *ops, const BItem *items, int nitems, double omega,
+                               const int *active, int grid, int block, int nzmax,
+                               double *partial, cudaStream_t s)
+{
+    if (nitems <= 0) return cudaSuccess;
+    const size_t smem = (size_t)nzmax * block * sizeof(T);
+    k_bsmooth_dot<T><<<grid, block, smem, s>>>(ops, items, nitems, (T)omega, active, partial);
+    return cudaGetLastError();
+}
+
 cudaError_t bsmooth_prepare()
 {
     cudaError_t e;
@@ -57,7 +110,8 @@ cudaError_t bsmooth_prepare()
         cudaSuccess)
         return e;
     const void *kernels[] = {(const void *)k_bsmooth<double, true>, (const void *)k_bsmooth<double, false>,
-                             (const void *)k_bsmooth<float, true>, (const void *)k_bsmooth<float, false>};
+                             (const void *)k_bsmooth<float, true>, (const void *)k_bsmooth<float, false>,
+                             (const void *)k_bsmooth_dot<double>, (const void *)k_bsmooth_dot<float>};
     for (const void *k : kernels)
         if ((e = set_dynamic_smem_limit(k, lim)) != cudaSuccess) return e;
     return cudaSuccess;
@@ -72,14 +126,19 @@ k_bcells(const BOp<T> *__restrict__ ops, const BItem *__restrict__ items, int ni
         const BItem item = items[it];
         const BOp<T> &op = ops[item.op];
         if (active && !active[op.sys]) continue;
-        const int k = item.tile / op.nblk;
-        const int c = (item.tile - k * op.nblk) * blockDim.x + threadIdx.x;
+        const int zc = item.tile / op.nblk;
+        const int c = (item.tile - zc * op.nblk) * blockDim.x + threadIdx.x;
+        const int k0 = zc * op.kz, k1 = min(op.L.nz, k0 + op.kz);
         if (KIND == 0) {
-            if (c < op.L.nlon * op.L.nlat) stencil_cell<T, 1>(op.L, op.a, op.x, op.y, c, k);
+            if (op.kz >= op.L.nz) {
+                stencil_column<T, 1, false>(op.L, op.a, op.x, op.y, c);
+            } else if (c < op.L.nlon * op.L.nlat) {
+                for (int k = k0; k < k1; ++k) stencil_cell<T, 1>(op.L, op.a, op.x, op.y, c, k);
+            }
         } else if (KIND == 1) {
-            restrict_cell<T>(op.L, op.K, op.a, op.y, c, k);
+            restrict_layers<T>(op.L, op.K, op.a, op.y, c, k0, k1);
         } else {
-            prolong_pair<T>(op.L, op.K, op.a, op.y, c, k);
+            prolong_layers<T>(op.L, op.K, op.a, op.y, c, k0, k1);
         }
     }
 }
@@ -89,9 +148,76 @@ cudaError_t launch_bcells(int kind, const BOp<T> *ops, const BItem *items, int n
                           const int *active, int grid, cudaStream_t s)
 {
     if (nitems <= 0) return cudaSuccess;
+    const void *k = kind == 0 ? (const void *)k_bcells<T, 0>
+                              : (kind == 1 ? (const void *)k_bcells<T, 1> : (const void *)k_bcells<T, 2>);
+    grid = std::min(grid, resident_grid(k, kBlock, 0));
     if (kind == 0) k_bcells<T, 0><<<grid, kBlock, 0, s>>>(ops, items, nitems, active);
     else if (kind == 1) k_bcells<T, 1><<<grid, kBlock, 0, s>>>(ops, items, nitems, active);
     else k_bcells<T, 2><<<grid, kBlock, 0, s>>>(ops, items, nitems, active);
+    return cudaGetLastError();
+}
+
+template <typename T, bool BZ>
+__global__ void __launch_bounds__(kBlock)
+k_bdir_apply(const BOp<T> *__restrict__ ops, const BItem *__restrict__ items, int nitems,
+             const CgScalars *__restrict__ sc, double *__restrict__ partial,
+             const int *__restrict__ active)
+{
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BItem item = items[it];
+        const BOp<T> &op = ops[item.op];
+        if (active && !active[op.sys]) continue;
+        const T beta = BZ ? T(0) : (T)sc[op.sys].beta;
+        const T acc = dir_apply_column<T, BZ>(op.L, op.a, op.x, beta, op.y, op.w,
+                                              item.tile * blockDim.x + threadIdx.x);
+        block_store_at<0>((double)acc, partial, it);
+    }
+}
+
+template <typename T>
+cudaError_t launch_bdir_apply(bool bz, const BOp<T> *ops, const BItem *items, int nitems,
+                              const CgScalars *sc, double *partial, const int *active, int grid,
+                              cudaStream_t s)
+{
+    if (nitems <= 0) return cudaSuccess;
+    if (bz) {
+        grid = std::min(grid, resident_grid((const void *)k_bdir_apply<T, true>, kBlock, 0));
+        k_bdir_apply<T, true><<<grid, kBlock, 0, s>>>(ops, items, nitems, sc, partial, active);
+    } else {
+        grid = std::min(grid, resident_grid((const void *)k_bdir_apply<T, false>, kBlock, 0));
+        k_bdir_apply<T, false><<<grid, kBlock, 0, s>>>(ops, items, nitems, sc, partial, active);
+    }
+    return cudaGetLastError();
+}
+
+template <bool NARROW>
+__global__ void __launch_bounds__(kBlock)
+k_bresid_cast(const BResid32 *__restrict__ ops, const BItem *__restrict__ items, int nitems,
+              const double *__restrict__ sdata, double *__restrict__ partial,
+              const int *__restrict__ active)
+{
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BItem item = items[it];
+        const BResid32 &op = ops[item.op];
+        if (active && !active[op.sys]) continue;
+        const double acc = stencil_column<double, 1, true, float, NARROW>(
+            op.L, op.b, op.x, op.r32, item.tile * blockDim.x + threadIdx.x, sdata[op.sys]);
+        block_store_at<0>(acc, partial, it);
+    }
+}
+
+cudaError_t launch_bresid_cast(bool narrow, const BResid32 *ops, const BItem *items, int nitems,
+                               const double *sdata, double *partial, const int *active, int grid,
+                               cudaStream_t s)
+{
+    if (nitems <= 0) return cudaSuccess;
+    if (narrow) {
+        grid = std::min(grid, resident_grid((const void *)k_bresid_cast<true>, kBlock, 0));
+        k_bresid_cast<true><<<grid, kBlock, 0, s>>>(ops, items, nitems, sdata, partial, active);
+    } else {
+        grid = std::min(grid, resident_grid((const void *)k_bresid_cast<false>, kBlock, 0));
+        k_bresid_cast<false><<<grid, kBlock, 0, s>>>(ops, items, nitems, sdata, partial, active);
+    }
     return cudaGetLastError();
 }
 
@@ -115,8 +241,13 @@ cudaError_t launch_bstencil_red(int mode, const BOp<T> *ops, const BItem *items,
                                 double *partial, const int *active, int grid, cudaStream_t s)
 {
     if (nitems <= 0) return cudaSuccess;
-    if (mode) k_bstencil_red<T, 1><<<grid, kBlock, 0, s>>>(ops, items, nitems, partial, active);
-    else k_bstencil_red<T, 0><<<grid, kBlock, 0, s>>>(ops, items, nitems, partial, active);
+    if (mode) {
+        grid = std::min(grid, resident_grid((const void *)k_bstencil_red<T, 1>, kBlock, 0));
+        k_bstencil_red<T, 1><<<grid, kBlock, 0, s>>>(ops, items, nitems, partial, active);
+    } else {
+        grid = std::min(grid, resident_grid((const void *)k_bstencil_red<T, 0>, kBlock, 0));
+        k_bstencil_red<T, 0><<<grid, kBlock, 0, s>>>(ops, items, nitems, partial, active);
+    }
     return cudaGetLastError();
 }
 
@@ -127,6 +258,38 @@ cudaError_t launch_bstencil_red(int mode, const BOp<T> *ops, const BItem *items,
 //   BV_DIR0:   a = b
 //   BV_ADD:    a += b
 //   BV_MAXABS: partial = max |a|
+// The chunk loop takes the vectors as restrict-qualified arguments, so the
+// loads of later elements are not held behind the stores of earlier ones.
+template <typename T, int OP>
+__device__ __forceinline__ double bvec_chunk(T *__restrict__ a, T *__restrict__ b,
+                                             const T *__restrict__ c, const T *__restrict__ d,
+                                             size_t c0, size_t c1, T alpha, T beta)
+{
+    double acc = 0;
+    T tacc = 0;
+#pragma unroll 4
+    for (size_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+        if (OP == BV_DOT) {
+            tacc = fma(a[i], b[i], tacc);
+        } else if (OP == BV_UPDATE) {
+            a[i] = fma(alpha, c[i], a[i]);
+            const T rv = fma(-alpha, d[i], b[i]);
+            b[i] = rv;
+            tacc = fma(rv, rv, tacc);
+        } else if (OP == BV_DIR) {
+            a[i] = fma(beta, c[i], b[i]);
+        } else if (OP == BV_DIR0) {
+            a[i] = b[i];
+        } else if (OP == BV_ADD) {
+            a[i] += b[i];
+        } else {
+            const double m = fabs((double)a[i]);
+            acc = (m > acc || m != m) ? m : acc;
+        }
+    }
+    return OP == BV_MAXABS ? acc : (double)tacc;
+}
+
 template <typename T, int OP>
 __global__ void __launch_bounds__(kBlock)
 k_bvec(const BVec<T> *__restrict__ vs, const BItem *__restrict__ items, int nitems,
@@ -137,32 +300,12 @@ k_bvec(const BVec<T> *__restrict__ vs, const BItem *__restrict__ items, int nite
         const BItem item = items[it];
         const BVec<T> &v = vs[item.op];
         if (active && !active[v.sys]) continue;
-        const size_t c0 = (size_t)item.tile * kVecChunk;
-        const size_t c1 = c0 + kVecChunk < v.n ? c0 + kVecChunk : v.n;
-        double acc = 0;
-        T tacc = 0;
+        const size_t c0 = (size_t)item.tile * v.chunk;
+        const size_t c1 = c0 + v.chunk < v.n ? c0 + v.chunk : v.n;
         const T alpha = (OP == BV_UPDATE) ? (T)sc[v.sys].alpha : T(0);
         const T beta = (OP == BV_DIR) ? (T)sc[v.sys].beta : T(0);
-        for (size_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            if (OP == BV_DOT) {
-                tacc = fma(v.a[c], v.b[c], tacc);
-            } else if (OP == BV_UPDATE) {
-                v.a[c] = fma(alpha, v.c[c], v.a[c]);
-                const T rv = fma(-alpha, v.d[c], v.b[c]);
-                v.b[c] = rv;
-                tacc = fma(rv, rv, tacc);
-            } else if (OP == BV_DIR) {
-                v.a[c] = fma(beta, v.c[c], v.b[c]);
-            } else if (OP == BV_DIR0) {
-                v.a[c] = v.b[c];
-            } else if (OP == BV_ADD) {
-                v.a[c] += v.b[c];
-            } else {
-                const double m = fabs((double)v.a[c]);
-                acc = (m > acc || m != m) ? m : acc;
-            }
-        }
-        if (OP == BV_DOT || OP == BV_UPDATE) block_store_at<0>((double)tacc, partial, it);
+        const double acc = bvec_chunk<T, OP>(v.a, v.b, v.c, v.d, c0, c1, alpha, beta);
+        if (OP == BV_DOT || OP == BV_UPDATE) block_store_at<0>(acc, partial, it);
         if (OP == BV_MAXABS) block_store_at<1>(acc, partial, it);
     }
 }
@@ -173,6 +316,7 @@ cudaError_t launch_bvec(int op, const BVec<T> *v, const BItem *items, int nitems
                         cudaStream_t s)
 {
     if (nitems <= 0) return cudaSuccess;
+    grid = std::min(grid, resident_grid((const void *)k_bvec<T, BV_UPDATE>, kBlock, 0));
     switch (op) {
     case BV_DOT: k_bvec<T, BV_DOT><<<grid, kBlock, 0, s>>>(v, items, nitems, sc, partial, active); break;
     case BV_UPDATE: k_bvec<T, BV_UPDATE><<<grid, kBlock, 0, s>>>(v, items, nitems, sc, partial, active); break;
@@ -185,6 +329,18 @@ cudaError_t launch_bvec(int op, const BVec<T> *v, const BItem *items, int nitems
 }
 
 template <int MODE>
+__device__ __forceinline__ void bmix_chunk(double *__restrict__ x, const double *__restrict__ r,
+                                           float *__restrict__ r32, const float *__restrict__ e32,
+                                           size_t c0, size_t c1, double f)
+{
+#pragma unroll 4
+    for (size_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        if (MODE == 0) r32[c] = (float)(r[c] * f);
+        else x[c] = fma(f, (double)e32[c], x[c]);
+    }
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(kBlock)
 k_bmix(const BMix *__restrict__ vs, const BItem *__restrict__ items, int nitems,
        const double *__restrict__ sdata, const int *__restrict__ active)
@@ -193,13 +349,9 @@ k_bmix(const BMix *__restrict__ vs, const BItem *__restrict__ items, int nitems,
         const BItem item = items[it];
         const BMix &v = vs[item.op];
         if (active && !active[v.sys]) continue;
-        const double f = sdata[v.sys];
-        const size_t c0 = (size_t)item.tile * kVecChunk;
-        const size_t c1 = c0 + kVecChunk < v.n ? c0 + kVecChunk : v.n;
-        for (size_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            if (MODE == 0) v.r32[c] = (float)(v.r[c] * f);
-            else v.x[c] = fma(f, (double)v.e32[c], v.x[c]);
-        }
+        const size_t c0 = (size_t)item.tile * v.chunk;
+        const size_t c1 = c0 + v.chunk < v.n ? c0 + v.chunk : v.n;
+        bmix_chunk<MODE>(v.x, v.r, v.r32, v.e32, c0, c1, sdata[v.sys]);
     }
 }
 
@@ -207,18 +359,20 @@ cudaError_t launch_bmix(int mode, const BMix *v, const BItem *items, int nitems,
                         const double *sdata, const int *active, int grid, cudaStream_t s)
 {
     if (nitems <= 0) return cudaSuccess;
+    grid = std::min(grid, resident_grid((const void *)k_bmix<1>, kBlock, 0));
     if (mode == 0) k_bmix<0><<<grid, kBlock, 0, s>>>(v, items, nitems, sdata, active);
     else k_bmix<1><<<grid, kBlock, 0, s>>>(v, items, nitems, sdata, active);
     return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(256)
-k_bfinalize(const double *__restrict__ partial, const int *__restrict__ off, CgScalars *sc,
-            int which, int op, const int *__restrict__ active)
+k_bfinalize(const double *__restrict__ partial, const int *__restrict__ beg,
+            const int *__restrict__ end, CgScalars *sc, int which, int op,
+            const int *__restrict__ active)
 {
     const int sys = blockIdx.x;
     if (active && !active[sys]) return;
-    const int p0 = off[sys], p1 = off[sys + 1];
+    const int p0 = beg[sys], p1 = end[sys];
     double v = 0;
     for (int c = p0 + threadIdx.x; c < p1; c += blockDim.x)
         v = op == 3 ? ((partial[c] > v || partial[c] != partial[c]) ? partial[c] : v) : v + partial[c];
@@ -242,22 +396,27 @@ k_bfinalize(const double *__restrict__ partial, const int *__restrict__ off, CgS
     }
 }
 
-cudaError_t launch_bfinalize(const double *partial, const int *off, int nsys, CgScalars *sc,
-                             int which, int op, const int *active, cudaStream_t s)
+cudaError_t launch_bfinalize(const double *partial, const int *beg, const int *end, int nsys,
+                             CgScalars *sc, int which, int op, const int *active, cudaStream_t s)
 {
-    k_bfinalize<<<nsys, 256, 0, s>>>(partial, off, sc, which, op, active);
+    k_bfinalize<<<nsys, 256, 0, s>>>(partial, beg, end, sc, which, op, active);
     return cudaGetLastError();
 }
 
 #define TPMG_BINST(T)                                                                           \
     template cudaError_t launch_bsmooth<T>(const BOp<T> *, const BItem *, int, bool, double,      \
                                            const int *, int, int, int, cudaStream_t);             \
+    template cudaError_t launch_bsmooth_dot<T>(const BOp<T> *, const BItem *, int, double,        \
+                                               const int *, int, int, int, double *, cudaStream_t); \
     template cudaError_t launch_bcells<T>(int, const BOp<T> *, const BItem *, int, const int *,   \
                                           int, cudaStream_t);                                     \
     template cudaError_t launch_bstencil_red<T>(int, const BOp<T> *, const BItem *, int,          \
                                                 double *, const int *, int, cudaStream_t);        \
     template cudaError_t launch_bvec<T>(int, const BVec<T> *, const BItem *, int,                 \
-                                        const CgScalars *, double *, const int *, int, cudaStream_t);
+                                        const CgScalars *, double *, const int *, int, cudaStream_t); \
+    template cudaError_t launch_bdir_apply<T>(bool, const BOp<T> *, const BItem *, int,           \
+                                              const CgScalars *, double *, const int *, int,      \
+                                              cudaStream_t);
 
 TPMG_BINST(double)
 TPMG_BINST(float)

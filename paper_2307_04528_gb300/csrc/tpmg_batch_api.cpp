@@ -30,15 +30,20 @@ using namespace tpmg;
 
 namespace {
 
-enum { BK_SMOOTH0 = 0, BK_SMOOTH = 1, BK_RESID = 2, BK_RESTRICT = 3, BK_PROLONG = 4 };
+enum { BK_SMOOTH0 = 0, BK_SMOOTH = 1, BK_RESID = 2, BK_RESTRICT = 3, BK_PROLONG = 4,
+       BK_SMOOTH_DOT = 5, BK_KINDS = 6 };
 
 template <typename T>
 struct StepHost {
     int kind;
     std::vector<BOp<T>> ops;
-    std::vector<BItem> items;  // built for the tuned tile width
+    std::vector<BItem> items;  // work list of the small operators (tuned tile width)
+    std::vector<int> big;      // operators launched on their own (large levels)
+    std::vector<int> base;     // first partial sum of each big operator
+    std::vector<int> off;      // per-system partial-sum ranges: begin [0, n), end [n, 2n)
     BOp<T> *ops_dev = nullptr;
     BItem *items_dev = nullptr;
+    int *off_dev = nullptr;
 };
 
 template <typename T>
@@ -54,8 +59,10 @@ struct VecPlan {            // one fine-level vector operation over all systems
 template <typename T>
 struct RedPlan {            // fine-level stencil with per-system reduction
     std::vector<BOp<T>> ops;
-    std::vector<BItem> items;
-    std::vector<int> off;
+    std::vector<BItem> items;  // column tiles of the small systems
+    std::vector<int> big;      // systems launched on their own (large levels)
+    std::vector<int> base;     // first partial sum of each big system
+    std::vector<int> off;      // per-system partial-sum ranges: begin [0, n), end [n, 2n)
     BOp<T> *ops_dev = nullptr;
     BItem *items_dev = nullptr;
     int *off_dev = nullptr;
@@ -64,10 +71,21 @@ struct RedPlan {            // fine-level stencil with per-system reduction
 template <typename T>
 struct PrecPlan {
     std::vector<StepHost<T>> vsteps;   // batched V-cycle: cg.r -> cg.z of every system
-    VecPlan<T> dot_rz, dot_bb, update[2], dir[2], dir0, add, rmax;
+    VecPlan<T> dot_rz, dot_bb, update[2], dir[2], dir0, add, rmax, rcopy, xmax;
     RedPlan<T> resid;                  // r = b - H x (+ |r|^2), fixed b and x
     RedPlan<T> apply[2];               // Ad = H d (+ d.Ad), d = d0 / d1
+    RedPlan<T> dirapply0, dirapply[2]; // d = z (+ beta d_old) and Ad = H d (+ d.Ad)
     VGraph graph;
+};
+
+// FP64 residual -> scaled FP32 right-hand side, one descriptor per system.
+struct ResidPlan {
+    std::vector<BResid32> ops;
+    std::vector<BItem> items;
+    std::vector<int> off;
+    BResid32 *ops_dev = nullptr;
+    BItem *items_dev = nullptr;
+    int *off_dev = nullptr;
 };
 
 struct Bump {
@@ -105,14 +123,24 @@ struct mg_batch {
     PrecPlan<double> p64;
     PrecPlan<float> p32;
     // FP64 <-> FP32 transfers of the mixed solve (x: the caller's, set per call)
-    std::vector<BMix> mix;
+    std::vector<BMix> mix, mixb;       // mixb: cast of the caller's b (zero initial guess)
     std::vector<BItem> mix_items;
-    BMix *mix_dev = nullptr;
+    BMix *mix_dev = nullptr, *mixb_dev = nullptr;
     BItem *mix_items_dev = nullptr;
+    ResidPlan resid32;
     cudaStream_t cap_stream = nullptr;
 };
 
 namespace {
+
+size_t vec_chunk(const mg_batch *B)
+{
+    size_t total = 0;
+    for (const mg_grid &g : B->grids) total += (size_t)g.nlon * g.nlat * g.nz;
+    size_t c = (total + kVecItems - 1) / kVecItems;
+    c = (c + kBlock - 1) / kBlock * kBlock;
+    return c < (size_t)kVecChunkMin ? (size_t)kVecChunkMin : c;
+}
 
 template <typename T>
 PrecPlan<T> &plan_of(mg_batch *B);
@@ -128,6 +156,22 @@ struct SysOp {
     int kind;
     BOp<T> op;
 };
+
+// Layers per work item of the cell-type steps: the residual walks whole
+// columns where a level has enough of them (as the single-system path), and
+// the transfers take up to 16 layers per thread on large levels.
+template <typename T>
+int layers_per_item(int kind, const LevelDev<T> &L, const LinkDev &K)
+{
+    const long long ncol = (long long)L.nlon * L.nlat;
+    if (kind == BK_RESID) return ncol >= 32768 ? L.nz : 1;
+    if (kind != BK_RESTRICT && kind != BK_PROLONG) return L.nz;
+    const long long cols = kind == BK_RESTRICT ? (long long)(L.nlon / 2) * K.nlat_c
+                                               : (long long)(L.nlon / 2) * L.nlat;
+    if (cols >= 65536) return std::min(L.nz, 16);
+    if (cols >= 16384) return std::min(L.nz, 4);
+    return 1;
+}
 
 // The V-cycle of handle H as phases: phase l (down, 0 <= l < L) and phase
 // 2 Lmax - 2 - l (up), exactly in the order vcycle_level issues them.
@@ -148,6 +192,7 @@ void gen_level(mg_handle *H, int sys, int l, int Lmax, const T *b, T *out, T *sc
         op.x = x;
         op.y = y;
         op.sys = sys;
+        op.kz = layers_per_item(kind, L, K);
         per[sys].push_back({kind, op});
     };
     const LinkDev nolink{};
@@ -178,12 +223,17 @@ void gen_level(mg_handle *H, int sys, int l, int Lmax, const T *b, T *out, T *sc
                  phases, nsys);
     push(up, BK_PROLONG, Vec<T>::u(c), nullptr, cur, D, v.linkdev);
     for (int it = 0; it < H->p.nu2; ++it) {
-        push(up, BK_SMOOTH, b, cur, oth, D, nolink);
+        // the last sweep of the finest level also forms <r, z> of the CG
+        const int kind = (l == 0 && it + 1 == H->p.nu2) ? BK_SMOOTH_DOT : BK_SMOOTH;
+        push(up, kind, b, cur, oth, D, nolink);
         std::swap(cur, oth);
     }
 }
 
 int cdiv(long long a, int b) { return (int)((a + b - 1) / b); }
+
+// Elements per vector work item for the batch (fixed by the sizes alone).
+size_t vec_chunk(const mg_batch *B);
 
 // Tiles of a participant for its step kind (block = column tile width of smoothers).
 template <typename T>
@@ -193,29 +243,63 @@ int tiles_of(int kind, const BOp<T> &op, int block, int *nblk)
     switch (kind) {
     case BK_SMOOTH0:
     case BK_SMOOTH:
+    case BK_SMOOTH_DOT:
         *nblk = cdiv(ncol, block);
         return *nblk;
     case BK_RESID:
         *nblk = cdiv(ncol, kBlock);
-        return *nblk * op.L.nz;
+        return *nblk * cdiv(op.L.nz, op.kz);
     case BK_RESTRICT:
         *nblk = cdiv((long long)(op.L.nlon / 2) * op.K.nlat_c, kBlock);
-        return *nblk * op.L.nz;
+        return *nblk * cdiv(op.L.nz, op.kz);
     default:
         *nblk = cdiv((long long)(op.L.nlon / 2) * op.L.nlat, kBlock);
-        return *nblk * op.L.nz;
+        return *nblk * cdiv(op.L.nz, op.kz);
     }
 }
 
+// Levels with at least this many columns run the single-system kernels, one
+// launch per operator (their own grid fills the GPU, and their kernel
+// parameters live in the constant bank instead of registers); the smaller
+// ones share the persistent work-list launch.
+constexpr long long kBigColumns = 1LL << 18;
+
 template <typename T>
-void build_items(StepHost<T> &st, int block)
+bool is_big(const BOp<T> &op)
+{
+    return (long long)op.L.nlon * op.L.nlat >= kBigColumns;
+}
+
+// Work list of the small operators, the big ones, and the partial-sum ranges:
+// items first (partial[item]), then each big operator's blocks.
+template <typename T>
+void build_items(StepHost<T> &st, int block, int nsys)
 {
     st.items.clear();
+    st.big.clear();
+    st.base.clear();
+    st.off.assign(2 * nsys, 0);
     for (int i = 0; i < (int)st.ops.size(); ++i) {
         int nblk = 0;
         const int nt = tiles_of<T>(st.kind, st.ops[i], block, &nblk);
         st.ops[i].nblk = nblk;
+        if (is_big(st.ops[i])) {
+            st.big.push_back(i);
+            continue;
+        }
+        const int s0 = (int)st.items.size();
         for (int t = 0; t < nt; ++t) st.items.push_back({i, t});
+        st.off[st.ops[i].sys] = s0;
+        st.off[nsys + st.ops[i].sys] = (int)st.items.size();
+    }
+    int next = (int)st.items.size();
+    for (int i : st.big) {
+        const BOp<T> &op = st.ops[i];
+        const int grid = cdiv((long long)op.L.nlon * op.L.nlat, kBlock);
+        st.base.push_back(next);
+        st.off[op.sys] = next;
+        st.off[nsys + op.sys] = next + grid;
+        next += grid;
     }
 }
 
@@ -237,7 +321,7 @@ void build_program(mg_batch *B)
         size_t slots = 0;
         for (auto &lst : ph.second) slots = std::max(slots, lst.size());
         for (size_t q = 0; q < slots; ++q) {
-            for (int kind = 0; kind < 5; ++kind) {
+            for (int kind = 0; kind < BK_KINDS; ++kind) {
                 StepHost<T> st;
                 st.kind = kind;
                 for (auto &lst : ph.second)
@@ -246,7 +330,7 @@ void build_program(mg_batch *B)
             }
         }
     }
-    for (auto &st : P.vsteps) build_items(st, B->smooth_block);
+    for (auto &st : P.vsteps) build_items(st, B->smooth_block, B->n);
 }
 
 // Vector plan: one descriptor per system, items = chunks, grouped by system.
@@ -265,8 +349,9 @@ void vec_plan(mg_batch *B, VecPlan<T> &V, T *(*a)(mg_handle *), T *(*b)(mg_handl
         e.c = c ? c(H) : nullptr;
         e.d = d ? d(H) : nullptr;
         e.n = H->lev[0].n;
+        e.chunk = vec_chunk(B);
         e.sys = s;
-        e.nchunk = cdiv((long long)e.n, kVecChunk);
+        e.nchunk = (int)((e.n + e.chunk - 1) / e.chunk);
         V.v.push_back(e);
         for (int t = 0; t < e.nchunk; ++t) V.items.push_back({s, t});
         V.off.push_back((int)V.items.size());
@@ -275,23 +360,39 @@ void vec_plan(mg_batch *B, VecPlan<T> &V, T *(*a)(mg_handle *), T *(*b)(mg_handl
 
 template <typename T>
 void red_plan(mg_batch *B, RedPlan<T> &R, const T *(*a)(mg_handle *), const T *(*x)(mg_handle *),
-              T *(*y)(mg_handle *))
+              T *(*y)(mg_handle *), T *(*w)(mg_handle *) = nullptr, bool split = false)
 {
     R.ops.clear();
     R.items.clear();
-    R.off.assign(1, 0);
+    R.big.clear();
+    R.base.clear();
+    R.off.assign(2 * B->n, 0);
     for (int s = 0; s < B->n; ++s) {
         mg_handle *H = B->h[s];
         BOp<T> op{};
         op.L = dev<T>(H->lev[0]);
         op.a = a ? a(H) : nullptr;
-        op.x = x(H);
+        op.x = x ? x(H) : nullptr;
         op.y = y(H);
+        op.w = w ? w(H) : nullptr;
+        op.kz = op.L.nz;
         op.sys = s;
         op.nblk = cdiv((long long)op.L.nlon * op.L.nlat, kBlock);
         R.ops.push_back(op);
+        if (split && is_big(op)) {
+            R.big.push_back(s);
+            continue;
+        }
+        R.off[s] = (int)R.items.size();
         for (int t = 0; t < op.nblk; ++t) R.items.push_back({s, t});
-        R.off.push_back((int)R.items.size());
+        R.off[B->n + s] = (int)R.items.size();
+    }
+    int next = (int)R.items.size();
+    for (int s : R.big) {
+        R.base.push_back(next);
+        R.off[s] = next;
+        R.off[B->n + s] = next + R.ops[s].nblk;
+        next += R.ops[s].nblk;
     }
 }
 
@@ -336,6 +437,36 @@ void build_vector_plans(mg_batch *B)
                 Ad);
     red_plan<T>(B, P.apply[1], nullptr, [](mg_handle *H) -> const T * { return Vec<T>::cg(H).d1; },
                 Ad);
+    vec_plan<T>(B, P.rcopy, r, bx, nullptr, nullptr);  // r = b (inner solves start at x = 0)
+    vec_plan<T>(B, P.xmax, xx, nullptr, nullptr, nullptr);
+    // direction update + apply: d0 = z; d1 = z + beta d0; d0 = z + beta d1
+    auto zc = [](mg_handle *H) -> const T * { return Vec<T>::cg(H).z; };
+    auto d0c = [](mg_handle *H) -> const T * { return Vec<T>::cg(H).d0; };
+    auto d1c = [](mg_handle *H) -> const T * { return Vec<T>::cg(H).d1; };
+    red_plan<T>(B, P.dirapply0, zc, nullptr, d0, Ad, true);
+    red_plan<T>(B, P.dirapply[0], zc, d0c, d1, Ad, true);
+    red_plan<T>(B, P.dirapply[1], zc, d1c, d0, Ad, true);
+}
+
+void resid_plan(mg_batch *B)
+{
+    ResidPlan &R = B->resid32;
+    R.ops.clear();
+    R.items.clear();
+    R.off.assign(1, 0);
+    for (int s = 0; s < B->n; ++s) {
+        mg_handle *H = B->h[s];
+        BResid32 op{};
+        op.L = dev<double>(H->lev[0]);
+        op.b = (const double *)H->batch_b;
+        op.x = (const double *)H->batch_x;
+        op.r32 = H->lev[0].b32;
+        op.sys = s;
+        op.nblk = cdiv((long long)op.L.nlon * op.L.nlat, kBlock);
+        R.ops.push_back(op);
+        for (int t = 0; t < op.nblk; ++t) R.items.push_back({s, t});
+        R.off.push_back((int)R.items.size());
+    }
 }
 
 }  // namespace
@@ -354,6 +485,7 @@ void carve_step(Bump &b, StepHost<T> &st, size_t item_cap)
 {
     st.ops_dev = b.take<BOp<T>>(st.ops.size());
     st.items_dev = b.take<BItem>(item_cap);
+    st.off_dev = b.take<int>(st.off.size());
 }
 
 template <typename T>
@@ -393,11 +525,12 @@ void carve_plan(Bump &b, PrecPlan<T> &P, size_t *max_items)
         *max_items = std::max(*max_items, cap);
     }
     for (VecPlan<T> *V : {&P.dot_rz, &P.dot_bb, &P.update[0], &P.update[1], &P.dir[0], &P.dir[1],
-                          &P.dir0, &P.add, &P.rmax}) {
+                          &P.dir0, &P.add, &P.rmax, &P.rcopy, &P.xmax}) {
         carve_vec(b, *V);
         *max_items = std::max(*max_items, V->items.size());
     }
-    for (RedPlan<T> *R : {&P.resid, &P.apply[0], &P.apply[1]}) {
+    for (RedPlan<T> *R : {&P.resid, &P.apply[0], &P.apply[1], &P.dirapply0, &P.dirapply[0],
+                          &P.dirapply[1]}) {
         carve_red(b, *R);
         *max_items = std::max(*max_items, R->items.size());
     }
@@ -416,6 +549,7 @@ int upload_step(StepHost<T> &st, cudaStream_t s)
 {
     CHK(up(st.ops, st.ops_dev, s));
     CHK(up(st.items, st.items_dev, s));
+    CHK(up(st.off, st.off_dev, s));
     return MG_OK;
 }
 
@@ -442,9 +576,11 @@ int upload_plan(PrecPlan<T> &P, cudaStream_t s)
 {
     for (auto &st : P.vsteps) CHK(upload_step(st, s));
     for (VecPlan<T> *V : {&P.dot_rz, &P.dot_bb, &P.update[0], &P.update[1], &P.dir[0], &P.dir[1],
-                          &P.dir0, &P.add, &P.rmax})
+                          &P.dir0, &P.add, &P.rmax, &P.rcopy, &P.xmax})
         CHK(upload_vec(*V, s));
-    for (RedPlan<T> *R : {&P.resid, &P.apply[0], &P.apply[1]}) CHK(upload_red(*R, s));
+    for (RedPlan<T> *R : {&P.resid, &P.apply[0], &P.apply[1], &P.dirapply0, &P.dirapply[0],
+                          &P.dirapply[1]})
+        CHK(upload_red(*R, s));
     return MG_OK;
 }
 
@@ -485,15 +621,23 @@ static int batch_layout(mg_batch *B, void *base, size_t *total)
             m.r32 = H->lev[0].b32;
             m.e32 = H->cg32.x;
             m.n = H->lev[0].n;
+            m.chunk = vec_chunk(B);
             m.sys = i;
-            m.nchunk = cdiv((long long)m.n, kVecChunk);
+            m.nchunk = (int)((m.n + m.chunk - 1) / m.chunk);
             B->mix.push_back(m);
             for (int t = 0; t < m.nchunk; ++t) B->mix_items.push_back({i, t});
         }
+        B->mixb = B->mix;
         B->mix_dev = b.take<BMix>(B->mix.size());
+        B->mixb_dev = b.take<BMix>(B->mixb.size());
         B->mix_items_dev = b.take<BItem>(B->mix_items.size());
+        resid_plan(B);
+        ResidPlan &R = B->resid32;
+        R.ops_dev = b.take<BResid32>(R.ops.size());
+        R.items_dev = b.take<BItem>(R.items.size());
+        R.off_dev = b.take<int>(R.off.size());
     }
-    size_t max_items = 0;
+    size_t max_items = B->p.mixed ? B->resid32.items.size() : 0;
     carve_plan<double>(b, B->p64, &max_items);
     if (B->p.mixed) carve_plan<float>(b, B->p32, &max_items);
     B->partial_cap = max_items;
@@ -541,14 +685,42 @@ static int run_vstep(mg_batch *B, StepHost<T> &st, cudaStream_t s)
                               B->active, grid, B->smooth_block, B->nzmax, s);
         break;
     }
+    case BK_SMOOTH_DOT: {
+        const int grid = std::min(ni, B->smooth_grid);
+        e = launch_bsmooth_dot<T>(st.ops_dev, st.items_dev, ni, B->p.omega, B->active, grid,
+                                  B->smooth_block, B->nzmax, B->partial, s);
+        break;
+    }
     default: {
-        const int grid = std::min(ni, B->cell_grid);
+        // as many blocks as the GPU holds (the launcher clamps to occupancy)
+        const int grid = ni;
         const int kind = st.kind == BK_RESID ? 0 : (st.kind == BK_RESTRICT ? 1 : 2);
         e = launch_bcells<T>(kind, st.ops_dev, st.items_dev, ni, B->active, grid, s);
     }
     }
     if (e != cudaSuccess) return fail(MG_ERR_CUDA, "batched step: %s", cudaGetErrorString(e));
-    g_launches.fetch_add(1, std::memory_order_relaxed);
+    g_launches.fetch_add(ni > 0 ? 1 : 0, std::memory_order_relaxed);
+    for (size_t q = 0; q < st.big.size(); ++q) {
+        const BOp<T> &op = st.ops[st.big[q]];
+        const int *flag = B->active + op.sys;
+        switch (st.kind) {
+        case BK_SMOOTH0: e = launch_smooth<T>(op.L, op.a, nullptr, op.y, B->p.omega, s, flag); break;
+        case BK_SMOOTH: e = launch_smooth<T>(op.L, op.a, op.x, op.y, B->p.omega, s, flag); break;
+        case BK_SMOOTH_DOT:
+            launch_smooth_dot<T>(op.L, op.a, op.x, op.y, B->p.omega, B->partial + st.base[q], s,
+                                 flag);
+            e = cudaGetLastError();
+            break;
+        case BK_RESID:
+            launch_stencil<T>(op.L, 1, op.a, op.x, op.y, nullptr, s, flag);
+            e = cudaGetLastError();
+            break;
+        case BK_RESTRICT: e = launch_restrict<T>(op.L, op.K, op.a, op.y, s, flag); break;
+        default: e = launch_prolong_add<T>(op.L, op.K, op.a, op.y, s, flag); break;
+        }
+        if (e != cudaSuccess) return fail(MG_ERR_CUDA, "batched step: %s", cudaGetErrorString(e));
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
     return MG_OK;
 }
 
@@ -590,15 +762,18 @@ template <typename T>
 static int vec_op(mg_batch *B, int op, VecPlan<T> &V, cudaStream_t s)
 {
     const int ni = (int)V.items.size();
-    CU(launch_bvec<T>(op, V.v_dev, V.items_dev, ni, B->sc, B->partial, B->active,
-                      std::min(ni, B->vec_grid), s));
+    CU(launch_bvec<T>(op, V.v_dev, V.items_dev, ni, B->sc, B->partial, B->active, ni, s));
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return MG_OK;
 }
 
-static int finalize(mg_batch *B, const int *off, int which, int op, cudaStream_t s)
+// Per-system sums of the partials: contiguous ranges off[s] .. off[s+1], or
+// with end != nullptr explicit ranges off[s] .. end[s].
+static int finalize(mg_batch *B, const int *off, int which, int op, cudaStream_t s,
+                    const int *end = nullptr)
 {
-    CU(launch_bfinalize(B->partial, off, B->n, B->sc, which, op, B->active, s));
+    CU(launch_bfinalize(B->partial, off, end ? end : off + 1, B->n, B->sc, which, op, B->active,
+                        s));
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return MG_OK;
 }
@@ -607,8 +782,7 @@ template <typename T>
 static int red_op(mg_batch *B, int mode, RedPlan<T> &R, cudaStream_t s)
 {
     const int ni = (int)R.items.size();
-    CU(launch_bstencil_red<T>(mode, R.ops_dev, R.items_dev, ni, B->partial, B->active,
-                              std::min(ni, B->cell_grid), s));
+    CU(launch_bstencil_red<T>(mode, R.ops_dev, R.items_dev, ni, B->partial, B->active, ni, s));
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return MG_OK;
 }
@@ -631,13 +805,95 @@ static int read_slot(mg_batch *B, int which, std::vector<double> &out, cudaStrea
 
 static bool bad(double v) { return !(v == v) || std::isinf(v); }
 
+template <typename T>
+static int dir_apply_op(mg_batch *B, bool first, RedPlan<T> &R, cudaStream_t s)
+{
+    const int ni = (int)R.items.size();
+    if (ni > 0) {
+        CU(launch_bdir_apply<T>(first, R.ops_dev, R.items_dev, ni, B->sc, B->partial, B->active,
+                                ni, s));
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    for (size_t q = 0; q < R.big.size(); ++q) {
+        const BOp<T> &op = R.ops[R.big[q]];
+        launch_dir_apply<T>(op.L, op.a, first ? nullptr : op.x, B->sc + op.sys, op.y, op.w,
+                            B->partial + R.base[q], s, B->active + op.sys);
+        CU(cudaGetLastError());
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    return MG_OK;
+}
+
+// The CG iterations proper for the systems flagged in cgact (r holds their
+// residual): z = V r, then direction, apply, update until each system's
+// recursive residual meets tol, reaches maxit or grows by 1e6.  FP32 forms
+// the direction inside the apply (bandwidth-bound); FP64 (ALU-bound) keeps
+// the separate direction update.
+template <typename T>
+static int cg_iterations(mg_batch *B, std::vector<int> &cgact, const std::vector<double> &bb,
+                         const std::vector<double> &rr0, const std::vector<double> &tol,
+                         int maxit, std::vector<int> &its, std::vector<double> &rr,
+                         cudaStream_t s)
+{
+    PrecPlan<T> &P = plan_of<T>(B);
+    const int n = B->n;
+    constexpr bool fuse_direction = sizeof(T) == 4;
+    // <r, z> comes from the last sweep of the batched V-cycle when it has one
+    const StepHost<T> *dotstep = nullptr;
+    for (const auto &st : P.vsteps)
+        if (st.kind == BK_SMOOTH_DOT) dotstep = &st;
+    auto rz = [&](int which, int op) -> int {
+        if (dotstep) return finalize(B, dotstep->off_dev, which, op, s, dotstep->off_dev + n);
+        CHK(vec_op<T>(B, BV_DOT, P.dot_rz, s));
+        return finalize(B, P.dot_rz.off_dev, which, op, s);
+    };
+    CHK(set_active(B, cgact, s));
+    CHK(vcycle_batch<T>(B, s));
+    CHK(rz(S_RZ, 0));
+    int par = -1;  // current direction: none yet, d0 (0) or d1 (1)
+    while (true) {
+        if (fuse_direction) {
+            RedPlan<T> &R = par < 0 ? P.dirapply0 : P.dirapply[par];
+            CHK(dir_apply_op<T>(B, par < 0, R, s));
+            CHK(finalize(B, R.off_dev, S_DAD, 1, s, R.off_dev + n));
+        } else {
+            if (par < 0) CHK(vec_op<T>(B, BV_DIR0, P.dir0, s));
+            else CHK(vec_op<T>(B, BV_DIR, P.dir[par], s));
+            RedPlan<T> &R = P.apply[par < 0 ? 0 : par ^ 1];
+            CHK(red_op<T>(B, 0, R, s));
+            CHK(finalize(B, R.off_dev, S_DAD, 1, s, R.off_dev + n));
+        }
+        par = par < 0 ? 0 : par ^ 1;
+        CHK(vec_op<T>(B, BV_UPDATE, P.update[par], s));
+        CHK(finalize(B, P.update[par].off_dev, S_RR, 0, s));
+        CHK(read_slot(B, S_RR, rr, s));
+        int running = 0;
+        for (int i = 0; i < n; ++i) {
+            if (!cgact[i]) continue;
+            ++its[i];
+            const double bn = std::sqrt(bb[i]);
+            if (bad(rr[i]) || std::sqrt(rr[i]) <= tol[i] * bn || its[i] >= maxit ||
+                rr[i] > 1e6 * rr0[i])
+                cgact[i] = 0;
+            else
+                ++running;
+        }
+        if (!running) return MG_OK;
+        CHK(set_active(B, cgact, s));
+        CHK(vcycle_batch<T>(B, s));
+        CHK(rz(S_RZNEW, 2));
+    }
+}
+
 // V-cycle-preconditioned CG for every system in `want` (1 = solve), in lock
 // step; each system stops on its own tolerance.  b/x: bx_of / xx_of.
-// status[s], its[s], rel[s] per system.
+// status[s], its[s], rel[s] per system.  inner: x = 0 on entry, so r = b, and
+// the recursive residual decides (the FP32 solve of a refinement step);
+// otherwise every exit is confirmed on the true residual (restarting CG).
 template <typename T>
-static int batch_cg(mg_batch *B, const std::vector<int> &want, double tol, int maxit,
-                    std::vector<int> &status, std::vector<int> &its, std::vector<double> &rel,
-                    cudaStream_t s)
+static int batch_cg(mg_batch *B, const std::vector<int> &want, const std::vector<double> &tol,
+                    int maxit, std::vector<int> &status, std::vector<int> &its,
+                    std::vector<double> &rel, cudaStream_t s, bool inner = false)
 {
     PrecPlan<T> &P = plan_of<T>(B);
     const int n = B->n;
@@ -655,11 +911,33 @@ static int batch_cg(mg_batch *B, const std::vector<int> &want, double tol, int m
             status[i] = MG_ERR_NONFINITE;
             act[i] = 0;
         }
+    if (inner) {
+        CHK(set_active(B, act, s));
+        CHK(vec_op<T>(B, BV_DIR0, P.rcopy, s));
+        int left = 0;
+        for (int i = 0; i < n; ++i) {
+            if (!act[i]) continue;
+            rr0[i] = bb[i];
+            if (bb[i] == 0.0) act[i] = 0;  // x = 0 solves it
+            else ++left;
+        }
+        std::vector<int> cgact = act;
+        if (left) CHK(cg_iterations<T>(B, cgact, bb, rr0, tol, maxit, its, rr, s));
+        for (int i = 0; i < n; ++i) {
+            if (!act[i]) continue;
+            const double bn = std::sqrt(bb[i]);
+            rel[i] = std::sqrt(rr[i]) / bn;
+            status[i] = bad(rr[i]) ? MG_ERR_NONFINITE
+                                   : (std::sqrt(rr[i]) <= tol[i] * bn ? MG_OK
+                                                                      : MG_ERR_NOT_CONVERGED);
+        }
+        return MG_OK;
+    }
     for (int restart = 0; restart < 4; ++restart) {
         // true residual of every system still wanted
         CHK(set_active(B, act, s));
         CHK(red_op<T>(B, 1, P.resid, s));
-        CHK(finalize(B, P.resid.off_dev, S_RR, 0, s));
+        CHK(finalize(B, P.resid.off_dev, S_RR, 0, s, P.resid.off_dev + n));
         CHK(read_slot(B, S_RR, rr, s));
         int left = 0;
         for (int i = 0; i < n; ++i) {
@@ -669,7 +947,7 @@ static int batch_cg(mg_batch *B, const std::vector<int> &want, double tol, int m
             if (bad(rr[i])) {
                 status[i] = MG_ERR_NONFINITE;
                 act[i] = 0;
-            } else if (std::sqrt(rr[i]) <= tol * bn) {
+            } else if (std::sqrt(rr[i]) <= tol[i] * bn) {
                 status[i] = MG_OK;
                 act[i] = 0;
             } else if (its[i] >= maxit) {
@@ -682,37 +960,7 @@ static int batch_cg(mg_batch *B, const std::vector<int> &want, double tol, int m
         }
         if (!left) break;
         std::vector<int> cgact = act;
-        CHK(set_active(B, cgact, s));
-        CHK(vcycle_batch<T>(B, s));
-        CHK(vec_op<T>(B, BV_DOT, P.dot_rz, s));
-        CHK(finalize(B, P.dot_rz.off_dev, S_RZ, 0, s));
-        CHK(vec_op<T>(B, BV_DIR0, P.dir0, s));
-        int par = 0;  // current direction: d0 (par 0) or d1 (par 1)
-        while (true) {
-            CHK(red_op<T>(B, 0, P.apply[par], s));
-            CHK(finalize(B, P.apply[par].off_dev, S_DAD, 1, s));
-            CHK(vec_op<T>(B, BV_UPDATE, P.update[par], s));
-            CHK(finalize(B, P.update[par].off_dev, S_RR, 0, s));
-            CHK(read_slot(B, S_RR, rr, s));
-            int running = 0;
-            for (int i = 0; i < n; ++i) {
-                if (!cgact[i]) continue;
-                ++its[i];
-                const double bn = std::sqrt(bb[i]);
-                if (bad(rr[i]) || std::sqrt(rr[i]) <= tol * bn || its[i] >= maxit ||
-                    rr[i] > 1e6 * rr0[i])
-                    cgact[i] = 0;  // leave the CG loop; checked on the true residual
-                else
-                    ++running;
-            }
-            if (!running) break;
-            CHK(set_active(B, cgact, s));
-            CHK(vcycle_batch<T>(B, s));
-            CHK(vec_op<T>(B, BV_DOT, P.dot_rz, s));
-            CHK(finalize(B, P.dot_rz.off_dev, S_RZNEW, 2, s));
-            CHK(vec_op<T>(B, BV_DIR, P.dir[par], s));
-            par ^= 1;
-        }
+        CHK(cg_iterations<T>(B, cgact, bb, rr0, tol, maxit, its, rr, s));
     }
     for (int i = 0; i < n; ++i)
         if (act[i]) status[i] = MG_ERR_NOT_CONVERGED;
@@ -724,7 +972,7 @@ static int refresh_bx_plans(mg_batch *B, cudaStream_t s)
 {
     PrecPlan<T> &P = plan_of<T>(B);
     build_vector_plans<T>(B);
-    for (VecPlan<T> *V : {&P.dot_bb, &P.update[0], &P.update[1], &P.add})
+    for (VecPlan<T> *V : {&P.dot_bb, &P.update[0], &P.update[1], &P.add, &P.rcopy, &P.xmax})
         CHK(up(V->v, V->v_dev, s));
     CHK(up(P.resid.ops, P.resid.ops_dev, s));
     return MG_OK;
@@ -760,16 +1008,15 @@ static int autotune(mg_batch *B, cudaStream_t s)
     };
     // the fine-level non-zero-guess smoother step (the largest one)
     StepHost<T> *sm = nullptr;
-    StepHost<T> *cell = nullptr;
-    for (auto &st : P.vsteps) {
-        if (st.kind == BK_SMOOTH && (!sm || st.items.size() > sm->items.size())) sm = &st;
-        if (st.kind == BK_RESID && (!cell || st.items.size() > cell->items.size())) cell = &st;
-    }
+    for (auto &st : P.vsteps)
+        if ((st.kind == BK_SMOOTH || st.kind == BK_SMOOTH_DOT) &&
+            (!sm || st.items.size() > sm->items.size()))
+            sm = &st;
     double best = 1e30;
     int best_b = kBlock, best_g = sms * 4;
     for (int block : {64, 128}) {
         if (sm) {
-            build_items(*sm, block);
+            build_items(*sm, block, B->n);
             CHK(upload_step(*sm, s));
         }
         for (int per_sm : {2, 4, 6, 8, 12}) {
@@ -787,18 +1034,10 @@ static int autotune(mg_batch *B, cudaStream_t s)
     }
     B->smooth_block = best_b;
     B->smooth_grid = best_g;
-    best = 1e30;
-    int best_c = sms * 8;
-    for (int per_sm : {4, 8, 16, 32}) {
-        B->cell_grid = sms * per_sm;
-        if (!cell) break;
-        const double ms = time_it([&] { run_vstep<T>(B, *cell, s); });
-        if (ms < best) {
-            best = ms;
-            best_c = B->cell_grid;
-        }
-    }
-    B->cell_grid = best_c;
+    // cell-type steps and vector operations run on resident persistent grids
+    // (sized by occupancy in their launchers); reported for reference
+    B->cell_grid = sms * 8;
+
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CU(cudaGetLastError());
@@ -810,7 +1049,7 @@ static int rebuild_items(mg_batch *B, cudaStream_t s)
 {
     PrecPlan<T> &P = plan_of<T>(B);
     for (auto &st : P.vsteps) {
-        build_items(st, B->smooth_block);
+        build_items(st, B->smooth_block, B->n);
         CHK(upload_step(st, s));
     }
     return MG_OK;
@@ -933,31 +1172,109 @@ extern "C" int mg_batch_solve(mg_batch *B, const double *const *b, double *const
     std::vector<double> rel;
     if (!mixed) {
         std::vector<int> want(n, 1);
-        CHK(batch_cg<double>(B, want, tol, B->p.maxit, st, its, rel, s));
+        CHK(batch_cg<double>(B, want, std::vector<double>(n, tol), B->p.maxit, st, its, rel, s));
         for (int i = 0; i < n; ++i) batch_stats(stats, i, its[i], 0, rel[i]);
     } else {
         // FP64 refinement in lock step; the inner FP32 solves run batched.
+        // Each step writes the FP64 residual directly as the FP32 right-hand
+        // side r / s_i with s_i a power of two near the expected ||r_i||
+        // (exact scaling), corrected when the measured norm is outside
+        // [s_i 2^-10, s_i 2^10]; a zero initial guess makes the first
+        // residual b itself.
         PrecPlan<double> &P = B->p64;
-        std::vector<int> act(n, 1), outer(n, 0);
-        std::vector<double> bb, rr, mx, relv(n, 0.0), rr0(n, -1.0), sd(2 * n, 0.0);
-        for (int i = 0; i < n; ++i) B->mix[i].x = x[i];
+        ResidPlan &R = B->resid32;
+        std::vector<int> act(n, 1), outer(n, 0), xzero(n, 0);
+        std::vector<double> bb, rr, xm, relv(n, 0.0), rr0(n, -1.0), sd(2 * n, 0.0), pred(n);
+        for (int i = 0; i < n; ++i) {
+            B->mix[i].x = x[i];
+            B->mixb[i].r = b[i];
+        }
         CHK(up(B->mix, B->mix_dev, s));
+        CHK(up(B->mixb, B->mixb_dev, s));
         CHK(up(B->mix_items, B->mix_items_dev, s));
+        resid_plan(B);
+        CHK(up(R.ops, R.ops_dev, s));
+        CHK(up(R.items, R.items_dev, s));
+        CHK(up(R.off, R.off_dev, s));
         const int nmix = (int)B->mix_items.size();
+        const int nres = (int)R.items.size();
         CHK(set_active(B, act, s));
         CHK(vec_op<double>(B, BV_DOT, P.dot_bb, s));
         CHK(finalize(B, P.dot_bb.off_dev, S_RR, 0, s));
         CHK(read_slot(B, S_RR, bb, s));
-        for (int i = 0; i < n; ++i)
-            if (bad(bb[i])) {
+        CHK(vec_op<double>(B, BV_MAXABS, P.xmax, s));
+        CHK(finalize(B, P.xmax.off_dev, S_MAX, 3, s));
+        CHK(read_slot(B, S_MAX, xm, s));
+        for (int i = 0; i < n; ++i) {
+            pred[i] = std::sqrt(bb[i]);
+            xzero[i] = xm[i] == 0.0;
+            if (bad(bb[i]) || bad(xm[i])) {
                 st[i] = MG_ERR_NONFINITE;
                 act[i] = 0;
             }
+        }
+        auto scale_of = [](double v) {
+            int ex = 0;
+            std::frexp(v > 0 ? v : 1.0, &ex);
+            return std::ldexp(1.0, ex);
+        };
+        // FP64 residual -> FP32 right-hand side of the systems in `which`
+        auto residual_cast = [&](const std::vector<int> &which) -> int {
+            bool narrow = true;
+            for (int i = 0; i < n; ++i)
+                if (which[i] && !(sd[i] >= 0x1p-100 && sd[i] <= 0x1p60)) narrow = false;
+            CHK(set_active(B, which, s));
+            CU(launch_bresid_cast(narrow, R.ops_dev, R.items_dev, nres, B->sdata, B->partial,
+                                  B->active, nres, s));
+            g_launches.fetch_add(1, std::memory_order_relaxed);
+            return MG_OK;
+        };
         while (true) {
-            CHK(set_active(B, act, s));
-            CHK(red_op<double>(B, 1, P.resid, s));
-            CHK(finalize(B, P.resid.off_dev, S_RR, 0, s));
-            CHK(read_slot(B, S_RR, rr, s));
+            std::vector<int> from_b(n, 0), stencil(n, 0);
+            int nb = 0, ns = 0;
+            for (int i = 0; i < n; ++i) {
+                if (!act[i]) continue;
+                const double sc = scale_of(pred[i]);
+                sd[i] = 1.0 / sc;                    // cast factor
+                sd[n + i] = B->h[i]->scale32 * sc;   // update factor
+                if (xzero[i] && outer[i] == 0) from_b[i] = 1, ++nb;
+                else stencil[i] = 1, ++ns;
+            }
+            CHK(up(sd, B->sdata, s));
+            rr.assign(n, 0.0);
+            if (nb) {
+                CHK(set_active(B, from_b, s));
+                CU(launch_bmix(0, B->mixb_dev, B->mix_items_dev, nmix, B->sdata, B->active, nmix,
+                               s));
+                g_launches.fetch_add(1, std::memory_order_relaxed);
+                for (int i = 0; i < n; ++i)
+                    if (from_b[i]) rr[i] = bb[i];
+            }
+            if (ns) {
+                CHK(residual_cast(stencil));
+                CHK(finalize(B, R.off_dev, S_RR, 0, s));
+                std::vector<double> rs;
+                CHK(read_slot(B, S_RR, rs, s));
+                std::vector<int> redo(n, 0);
+                int nredo = 0;
+                for (int i = 0; i < n; ++i) {
+                    if (!stencil[i]) continue;
+                    rr[i] = rs[i];
+                    const double rn = std::sqrt(rs[i]), sc = 1.0 / sd[i];
+                    if (!bad(rs[i]) && rn > 0 &&
+                        (rn > std::ldexp(sc, 10) || rn < std::ldexp(sc, -10))) {
+                        const double sc2 = scale_of(rn);
+                        sd[i] = 1.0 / sc2;
+                        sd[n + i] = B->h[i]->scale32 * sc2;
+                        redo[i] = 1;
+                        ++nredo;
+                    }
+                }
+                if (nredo) {
+                    CHK(up(sd, B->sdata, s));
+                    CHK(residual_cast(redo));
+                }
+            }
             int left = 0;
             for (int i = 0; i < n; ++i) {
                 if (!act[i]) continue;
@@ -971,41 +1288,27 @@ extern "C" int mg_batch_solve(mg_batch *B, const double *const *b, double *const
                 else ++left;
             }
             if (!left) break;
-            CHK(set_active(B, act, s));
-            // per-system power-of-two scale of the residual (exact)
-            CHK(vec_op<double>(B, BV_MAXABS, P.rmax, s));
-            CHK(finalize(B, P.rmax.off_dev, S_MAX, 3, s));
-            CHK(read_slot(B, S_MAX, mx, s));
-            for (int i = 0; i < n; ++i) {
-                int ex = 0;
-                std::frexp(act[i] ? mx[i] : 1.0, &ex);
-                const double sc = std::ldexp(1.0, ex);
-                sd[i] = 1.0 / sc;                    // cast factor
-                sd[n + i] = B->h[i]->scale32 * sc;   // update factor
-            }
-            CHK(up(sd, B->sdata, s));
-            CU(launch_bmix(0, B->mix_dev, B->mix_items_dev, nmix, B->sdata, B->active,
-                           std::min(nmix, B->vec_grid), s));
             for (int i = 0; i < n; ++i)
                 if (act[i])
                     CU(cudaMemsetAsync(B->h[i]->cg32.x, 0, B->h[i]->lev[0].n * sizeof(float), s));
             std::vector<int> ist, iits;
             std::vector<double> irel;
-            // one inner tolerance for the batch: the loosest any system can use
-            double itol = 0.5;
+            // each system's inner tolerance (the rule of the single-system solve)
+            std::vector<double> itol(n, 0.5);
             for (int i = 0; i < n; ++i)
-                if (act[i]) itol = std::min(itol, inner_tolerance(B->p.inner_tol, tol, relv[i]));
-            CHK(batch_cg<float>(B, act, itol, B->p.inner_maxit, ist, iits, irel, s));
+                if (act[i]) itol[i] = inner_tolerance(B->p.inner_tol, tol, relv[i]);
+            CHK(batch_cg<float>(B, act, itol, B->p.inner_maxit, ist, iits, irel, s, true));
             for (int i = 0; i < n; ++i) {
                 if (!act[i]) continue;
                 if (ist[i] == MG_ERR_NONFINITE) { st[i] = MG_ERR_NONFINITE; act[i] = 0; continue; }
                 its_in[i] += iits[i];
                 ++outer[i];
+                pred[i] = std::sqrt(rr[i]) * std::max(irel[i], 1e-6);
             }
             CHK(set_active(B, act, s));
-            CU(launch_bmix(1, B->mix_dev, B->mix_items_dev, nmix, B->sdata + n, B->active,
-                           std::min(nmix, B->vec_grid), s));
-            g_launches.fetch_add(2, std::memory_order_relaxed);
+            CU(launch_bmix(1, B->mix_dev, B->mix_items_dev, nmix, B->sdata + n, B->active, nmix,
+                           s));
+            g_launches.fetch_add(1, std::memory_order_relaxed);
         }
         for (int i = 0; i < n; ++i) batch_stats(stats, i, outer[i], its_in[i], relv[i]);
     }

@@ -136,6 +136,95 @@ __device__ __forceinline__ T stencil_column(const LevelDev<T> &L, const T *__res
     return acc;
 }
 
+// Column loop of q = H d_new with the conjugate-gradient direction update
+// fused in: d_new = z + beta d_old (BZ: d_new = z) is formed on the fly at
+// the cell and its four horizontal neighbours, written for the cell, and
+// returned sum_k d_new q of the column (the CG inner product <d, H d>).  The
+// values equal those of a separate direction update followed by the apply.
+template <typename T>
+struct DirLoads {
+    T zc, dc, ze, de, zw, dw, zn, dn, zs, ds, tz, h, txc, txw, tyn, tys;
+};
+
+template <typename T, bool BZ>
+__device__ __forceinline__ void dir_load(DirLoads<T> &s, const LevelDev<T> &L,
+                                         const T *__restrict__ z, const T *__restrict__ dold,
+                                         size_t o, int col, int ie, int iw, int nlon, bool hasN,
+                                         bool hasS)
+{
+    s.zc = __ldg(z + o + col);
+    s.ze = __ldg(z + o + ie);
+    s.zw = __ldg(z + o + iw);
+    s.zn = hasN ? __ldg(z + o + col + nlon) : T(0);
+    s.zs = hasS ? __ldg(z + o + col - nlon) : T(0);
+    if (!BZ) {
+        s.dc = __ldg(dold + o + col);
+        s.de = __ldg(dold + o + ie);
+        s.dw = __ldg(dold + o + iw);
+        s.dn = hasN ? __ldg(dold + o + col + nlon) : T(0);
+        s.ds = hasS ? __ldg(dold + o + col - nlon) : T(0);
+    }
+    s.tz = __ldg(L.tz + o + col);
+    s.h = __ldg(L.h + o + col);
+    s.txc = __ldg(L.tx + o + col);
+    s.txw = __ldg(L.tx + o + iw);
+    s.tyn = hasN ? __ldg(L.ty + o + col) : T(0);
+    s.tys = hasS ? __ldg(L.ty + o + col - nlon) : T(0);
+}
+
+template <typename T, bool BZ>
+__device__ __forceinline__ T dir_apply_column(const LevelDev<T> &L, const T *__restrict__ z,
+                                              const T *__restrict__ dold, T beta,
+                                              T *__restrict__ dnew, T *__restrict__ q, int col)
+{
+    constexpr int kDepth = sizeof(T) == 8 ? 2 : 3;
+    const int nlon = L.nlon, nlat = L.nlat, nz = L.nz;
+    const int ncol = nlon * nlat;
+    T acc = 0;
+    if (col >= ncol) return acc;
+    const int j = col / nlon, i = col - j * nlon;
+    const int ie = (i + 1 == nlon) ? col - i : col + 1;
+    const int iw = (i == 0) ? col + nlon - 1 : col - 1;
+    const bool hasN = j + 1 < nlat, hasS = j > 0;
+    const size_t plane = (size_t)ncol;
+    auto dv = [&](T zv, T dvv) { return BZ ? zv : fma(beta, dvv, zv); };
+    DirLoads<T> st[kDepth];
+#pragma unroll
+    for (int d = 0; d < kDepth; ++d)
+        if (d < nz)
+            dir_load<T, BZ>(st[d], L, z, dold, (size_t)d * plane, col, ie, iw, nlon, hasN, hasS);
+    T xdn = 0, tdn = 0;
+    for (int k0 = 0; k0 < nz; k0 += kDepth) {
+#pragma unroll
+        for (int d = 0; d < kDepth; ++d) {
+            const int k = k0 + d;
+            if (k < nz) {
+                const DirLoads<T> &c = st[d];
+                const DirLoads<T> &nx = st[(d + 1) % kDepth];
+                const T xc = dv(c.zc, c.dc);
+                const T xup = (k + 1 < nz) ? dv(nx.zc, nx.dc) : T(0);
+                T v = c.h * xc;
+                v = fma(c.txc, xc - dv(c.ze, c.de), v);
+                v = fma(c.txw, xc - dv(c.zw, c.dw), v);
+                if (hasN) v = fma(c.tyn, xc - dv(c.zn, c.dn), v);
+                if (hasS) v = fma(c.tys, xc - dv(c.zs, c.ds), v);
+                v = fma(c.tz, xc - xup, v);
+                v = fma(tdn, xc - xdn, v);
+                const size_t o = (size_t)k * plane + col;
+                dnew[o] = xc;
+                q[o] = v;
+                acc = fma(v, xc, acc);
+                xdn = xc;
+                tdn = c.tz;
+                if (k + kDepth < nz)
+                    dir_load<T, BZ>(st[d], L, z, dold, (size_t)(k + kDepth) * plane, col, ie, iw,
+                                    nlon, hasN, hasS);
+            }
+        }
+    }
+    return acc;
+}
+
 // One cell of the stencil (cell-parallel form).
 template <typename T, int MODE>
 __device__ __forceinline__ void stencil_cell(const LevelDev<T> &L, const T *__restrict__ b,
@@ -219,7 +308,9 @@ __device__ __forceinline__ void smooth_load(SmoothLoads<T> &s, const LevelDev<T>
 // (nz * blockDim values of T per stored array).  DOT: also accumulate
 // sum_k b_k u_out,k of the column into *dacc (the CG inner product <r, z>
 // when the sweep is the last one of a V-cycle applied to r).
-template <typename T, bool ZERO, bool PRE, bool DOT = false>
+// BACK > 0 overrides the depth of the backward pipeline (the batched kernels,
+// which hold their work-item descriptors in registers as well).
+template <typename T, bool ZERO, bool PRE, bool DOT = false, int BACK = 0>
 __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__restrict__ b,
                                               const T *__restrict__ uin, T *__restrict__ uout,
                                               T omega, int col, unsigned char *smraw,
@@ -284,7 +375,7 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
     const T om1 = T(1) - omega;
     T xk = yprev;
     // backward sweep: prefetch u_in (and the precomputed q/p) kBack layers ahead
-    constexpr int kBack = SmoothDepth<T, ZERO>::back;
+    constexpr int kBack = BACK > 0 ? BACK : SmoothDepth<T, ZERO>::back;
     T up[kBack], dqp[kBack], bp[kBack];
 #pragma unroll
     for (int d = 0; d < kBack; ++d) {

@@ -42,25 +42,35 @@ constexpr int kBlock = 128;          // threads per block, one column per thread
 constexpr int kReduceSlots = 65536;  // per-block partial sums kept in the workspace
 
 // ---- launchers (tpmg_kernels.cu); all asynchronous on `s` -----------------
+// flag (device int, may be null): when it reads 0 the launch does nothing
+// (a converged system of a batch).
+//
 // y = H x (mode 0) or y = b - H x (mode 1).  If `partial` != null each block
 // writes sum(y*y) (mode 1) or sum(x*y) (mode 0) to partial[block]; returns
 // the number of blocks written (0 if partial == null).
 template <typename T>
 int launch_stencil(const LevelDev<T> &L, int mode, const T *b, const T *x, T *y,
-                   double *partial, cudaStream_t s);
+                   double *partial, cudaStream_t s, const int *flag = nullptr);
+
+// d_new = z + beta d_old (beta read from sc; d_old == nullptr: d_new = z) and
+// q = H d_new in one pass, with per-block partial sums of <d_new, q>; returns
+// the number of partial sums.
+template <typename T>
+int launch_dir_apply(const LevelDev<T> &L, const T *z, const T *d_old, const CgScalars *sc,
+                     T *d_new, T *q, double *partial, cudaStream_t s, const int *flag = nullptr);
 
 // One smoother sweep of Eq. (1) in the arrangement
 //   u_out = (1 - omega) u_in + omega H_z^{-1} (b - dH u_in)
 // (u_in == nullptr: zero initial guess).
 template <typename T>
 cudaError_t launch_smooth(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out,
-                          double omega, cudaStream_t s);
+                          double omega, cudaStream_t s, const int *flag = nullptr);
 
 // The same sweep (non-zero guess) writing the block sums of <b, u_out> to
 // partial[block]; returns the number of blocks.
 template <typename T>
 int launch_smooth_dot(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out, double omega,
-                      double *partial, cudaStream_t s);
+                      double *partial, cudaStream_t s, const int *flag = nullptr);
 
 // Raise the dynamic shared-memory limit of the smoother kernels (once per
 // process and device, before any stream capture).
@@ -73,11 +83,11 @@ size_t smooth_smem_bytes(int nz, size_t value_bytes);
 
 template <typename T>
 cudaError_t launch_restrict(const LevelDev<T> &F, const LinkDev &K, const T *r, T *bc,
-                            cudaStream_t s);
+                            cudaStream_t s, const int *flag = nullptr);
 
 template <typename T>
 cudaError_t launch_prolong_add(const LevelDev<T> &F, const LinkDev &K, const T *ec, T *u,
-                               cudaStream_t s);
+                               cudaStream_t s, const int *flag = nullptr);
 
 // Sum `n` partials in a fixed order into slots[which]; then (op) update
 // the CG scalars: 0 plain store, 1 alpha = rz / dAd, 2 beta = rz_new / rz
@@ -144,8 +154,18 @@ struct BOp {
     const T *a;      // right-hand side / source
     const T *x;      // second input (smoother u_in, nullptr = zero guess; stencil x)
     T *y;            // output
+    T *w;            // second output (direction update + apply: H d)
     int sys;         // system index (activity flag, per-system reductions)
-    int nblk;        // thread blocks per layer (cell tiles) or per level (column tiles)
+    int nblk;        // thread blocks per layer range (column tiles)
+    int kz;          // layers per work item (residual, transfers); nz: whole columns
+};
+
+// FP64 residual of one system handed to its FP32 inner solve (scaled).
+struct BResid32 {
+    LevelDev<double> L;
+    const double *b, *x;
+    float *r32;
+    int sys, nblk;
 };
 
 // A work item: participant `op`, tile `tile` (a column block, or
@@ -158,7 +178,7 @@ struct BItem {
 template <typename T>
 struct BVec {
     T *a, *b, *c, *d;
-    size_t n;
+    size_t n, chunk;  // length; elements per work item
     int sys, nchunk;
 };
 
@@ -168,11 +188,15 @@ struct BMix {
     const double *r;    // FP64 residual (cast)
     float *r32;         // FP32 right-hand side of the inner solve (cast)
     const float *e32;   // FP32 correction (update)
-    size_t n;
+    size_t n, chunk;    // length; elements per work item
     int sys, nchunk;
 };
 
-constexpr int kVecChunk = kBlock * 16;  // elements per vector work item
+// Elements per vector work item: the batch's total length split into about
+// kVecItems items (enough per resident block to balance the load), at least
+// kVecChunkMin, a multiple of kBlock.
+constexpr int kVecChunkMin = kBlock * 16;
+constexpr int kVecItems = 16384;
 
 enum { BV_DOT = 0, BV_UPDATE = 1, BV_DIR = 2, BV_DIR0 = 3, BV_ADD = 4, BV_MAXABS = 5 };
 
@@ -180,7 +204,8 @@ template <typename T>
 cudaError_t launch_bsmooth(const BOp<T> *ops, const BItem *items, int nitems, bool zero,
                            double omega, const int *active, int grid, int block, int nzmax,
                            cudaStream_t s);
-// kind: 0 residual y = a - H x (cells), 1 restriction (cells), 2 prolongation (cell pairs)
+// kind: 0 residual y = a - H x, 1 restriction, 2 prolongation (cell pairs); an item is a
+// column tile over op.kz layers (op.kz == nz: column walk of the residual)
 template <typename T>
 cudaError_t launch_bcells(int kind, const BOp<T> *ops, const BItem *items, int nitems,
                           const int *active, int grid, cudaStream_t s);
@@ -189,6 +214,18 @@ cudaError_t launch_bcells(int kind, const BOp<T> *ops, const BItem *items, int n
 template <typename T>
 cudaError_t launch_bstencil_red(int mode, const BOp<T> *ops, const BItem *items, int nitems,
                                 double *partial, const int *active, int grid, cudaStream_t s);
+// Direction update + apply for every system (item = column tile, one partial
+// per item): op.y = op.a + beta_sys op.x (bz: op.y = op.a), op.w = H op.y,
+// partial = sum op.y * op.w.
+template <typename T>
+cudaError_t launch_bdir_apply(bool bz, const BOp<T> *ops, const BItem *items, int nitems,
+                              const CgScalars *sc, double *partial, const int *active, int grid,
+                              cudaStream_t s);
+// r32 = (float)((b - H x) * sdata[sys]) in FP64 with the partial sums of
+// |b - H x|^2 (item = column tile); narrow: the scaling after the rounding.
+cudaError_t launch_bresid_cast(bool narrow, const BResid32 *ops, const BItem *items, int nitems,
+                               const double *sdata, double *partial, const int *active, int grid,
+                               cudaStream_t s);
 // Vector kernels over per-system chunks; per-item partials where the op reduces.
 template <typename T>
 cudaError_t launch_bvec(int op, const BVec<T> *v, const BItem *items, int nitems,
@@ -197,10 +234,16 @@ cudaError_t launch_bvec(int op, const BVec<T> *v, const BItem *items, int nitems
 // mode 0: r32 = (float)(r * sdata[sys]); mode 1: x += sdata[sys] * (double)e32
 cudaError_t launch_bmix(int mode, const BMix *v, const BItem *items, int nitems,
                         const double *sdata, const int *active, int grid, cudaStream_t s);
-// Per-system fixed-order sum of partial[off[s] .. off[s+1]) into sc[s] (ops
+// Per-system fixed-order sum of partial[beg[s] .. end[s]) into sc[s] (ops
 // as launch_finalize; op 3 = max); inactive systems are skipped.
-cudaError_t launch_bfinalize(const double *partial, const int *off, int nsys, CgScalars *sc,
-                             int which, int op, const int *active, cudaStream_t s);
+cudaError_t launch_bfinalize(const double *partial, const int *beg, const int *end, int nsys,
+                             CgScalars *sc, int which, int op, const int *active, cudaStream_t s);
+// The last sweep of the batched V-cycle with <b, u_out> fused: one partial
+// sum per item (block_store_at), as launch_bsmooth otherwise.
+template <typename T>
+cudaError_t launch_bsmooth_dot(const BOp<T> *ops, const BItem *items, int nitems, double omega,
+                               const int *active, int grid, int block, int nzmax,
+                               double *partial, cudaStream_t s);
 cudaError_t bsmooth_prepare();
 
 // Set the thread-local message mg_last_error() returns.

@@ -30,10 +30,39 @@ static int g_sms = 152;
 template <typename T, int MODE, bool RED>
 __global__ void __launch_bounds__(kBlock)
 k_stencil(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ y,
-          double *__restrict__ partial)
+          double *__restrict__ partial, const int *__restrict__ flag)
 {
+    if (flag && !*flag) return;
     const T acc = stencil_column<T, MODE, RED>(L, b, x, y, blockIdx.x * blockDim.x + threadIdx.x);
     if (RED) block_store<0>((double)acc, partial);
+}
+
+// d_new = z + beta d_old and q = H d_new in one pass (beta from the CG
+// scalars; BZ: first direction d_new = z), with the block sums of <d_new, q>.
+template <typename T, bool BZ>
+__global__ void __launch_bounds__(kBlock)
+k_dir_apply(LevelDev<T> L, const T *__restrict__ z, const T *__restrict__ dold,
+            const CgScalars *__restrict__ sc, T *__restrict__ dnew, T *__restrict__ q,
+            double *__restrict__ partial, const int *__restrict__ flag)
+{
+    if (flag && !*flag) return;
+    const T beta = BZ ? T(0) : (T)sc->beta;
+    const T acc = dir_apply_column<T, BZ>(L, z, dold, beta, dnew, q,
+                                          blockIdx.x * blockDim.x + threadIdx.x);
+    block_store<0>((double)acc, partial);
+}
+
+template <typename T>
+int launch_dir_apply(const LevelDev<T> &L, const T *z, const T *d_old, const CgScalars *sc,
+                     T *d_new, T *q, double *partial, cudaStream_t s, const int *flag)
+{
+    const int ncol = L.nlon * L.nlat;
+    const int grid = (ncol + kBlock - 1) / kBlock;
+    if (d_old == nullptr)
+        k_dir_apply<T, true><<<grid, kBlock, 0, s>>>(L, z, d_old, sc, d_new, q, partial, flag);
+    else
+        k_dir_apply<T, false><<<grid, kBlock, 0, s>>>(L, z, d_old, sc, d_new, q, partial, flag);
+    return grid;
 }
 
 // r32 = (float)((b - H x) * inv_scale) with the FP64 residual and the block
@@ -67,8 +96,10 @@ int launch_residual_cast(const LevelDev<double> &L, const double *b, const doubl
 // for levels with too few columns to fill the GPU with column loops.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kBlock)
-k_stencil_cells(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ y)
+k_stencil_cells(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ y,
+                const int *__restrict__ flag)
 {
+    if (flag && !*flag) return;
     stencil_cell<T, MODE>(L, b, x, y, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
 }
 
@@ -77,23 +108,23 @@ constexpr int kCellParallelColumns = 32768;
 
 template <typename T>
 int launch_stencil(const LevelDev<T> &L, int mode, const T *b, const T *x, T *y, double *partial,
-                   cudaStream_t s)
+                   cudaStream_t s, const int *flag)
 {
     const int ncol = L.nlon * L.nlat;
     const int grid = (ncol + kBlock - 1) / kBlock;
     if (!partial && ncol < kCellParallelColumns) {
         const dim3 g2(grid, L.nz);
-        if (mode) k_stencil_cells<T, 1><<<g2, kBlock, 0, s>>>(L, b, x, y);
-        else k_stencil_cells<T, 0><<<g2, kBlock, 0, s>>>(L, b, x, y);
+        if (mode) k_stencil_cells<T, 1><<<g2, kBlock, 0, s>>>(L, b, x, y, flag);
+        else k_stencil_cells<T, 0><<<g2, kBlock, 0, s>>>(L, b, x, y, flag);
         return 0;
     }
     if (partial) {
-        if (mode) k_stencil<T, 1, true><<<grid, kBlock, 0, s>>>(L, b, x, y, partial);
-        else k_stencil<T, 0, true><<<grid, kBlock, 0, s>>>(L, b, x, y, partial);
+        if (mode) k_stencil<T, 1, true><<<grid, kBlock, 0, s>>>(L, b, x, y, partial, flag);
+        else k_stencil<T, 0, true><<<grid, kBlock, 0, s>>>(L, b, x, y, partial, flag);
         return grid;
     }
-    if (mode) k_stencil<T, 1, false><<<grid, kBlock, 0, s>>>(L, b, x, y, nullptr);
-    else k_stencil<T, 0, false><<<grid, kBlock, 0, s>>>(L, b, x, y, nullptr);
+    if (mode) k_stencil<T, 1, false><<<grid, kBlock, 0, s>>>(L, b, x, y, nullptr, flag);
+    else k_stencil<T, 0, false><<<grid, kBlock, 0, s>>>(L, b, x, y, nullptr, flag);
     return 0;
 }
 
@@ -116,8 +147,9 @@ int launch_stencil(const LevelDev<T> &L, int mode, const T *b, const T *x, T *y,
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_smooth(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ uin, T *__restrict__ uout,
-         T omega)
+         T omega, const int *__restrict__ flag)
 {
+    if (flag && !*flag) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     smooth_column<T, false, true>(L, b, uin, uout, omega, blockIdx.x * blockDim.x + threadIdx.x,
                                   smraw);
@@ -125,8 +157,10 @@ k_smooth(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ uin, T *_
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
-k_smooth0(LevelDev<T> L, const T *__restrict__ b, T *__restrict__ uout, T omega)
+k_smooth0(LevelDev<T> L, const T *__restrict__ b, T *__restrict__ uout, T omega,
+          const int *__restrict__ flag)
 {
+    if (flag && !*flag) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     smooth_staged<T, true>(L, b, nullptr, uout, omega, blockIdx.x * blockDim.x + threadIdx.x,
                            smraw);
@@ -137,8 +171,10 @@ k_smooth0(LevelDev<T> L, const T *__restrict__ b, T *__restrict__ uout, T omega)
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_smooth_dot(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ uin,
-             T *__restrict__ uout, T omega, double *__restrict__ partial)
+             T *__restrict__ uout, T omega, double *__restrict__ partial,
+             const int *__restrict__ flag)
 {
+    if (flag && !*flag) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     T acc = 0;
     smooth_column<T, false, true, true>(L, b, uin, uout, omega,
@@ -148,27 +184,27 @@ k_smooth_dot(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ uin,
 
 template <typename T>
 int launch_smooth_dot(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out, double omega,
-                      double *partial, cudaStream_t s)
+                      double *partial, cudaStream_t s, const int *flag)
 {
     const size_t smem = (size_t)L.nz * kBlock * sizeof(T);
     const int ncol = L.nlon * L.nlat;
     const int grid = (ncol + kBlock - 1) / kBlock;
-    k_smooth_dot<T><<<grid, kBlock, smem, s>>>(L, b, u_in, u_out, (T)omega, partial);
+    k_smooth_dot<T><<<grid, kBlock, smem, s>>>(L, b, u_in, u_out, (T)omega, partial, flag);
     return grid;
 }
 
 template <typename T>
 cudaError_t launch_smooth(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out, double omega,
-                          cudaStream_t s)
+                          cudaStream_t s, const int *flag)
 {
     const int ncol = L.nlon * L.nlat;
     const int grid = (ncol + kBlock - 1) / kBlock;
     if (u_in == nullptr) {
         const size_t smem = ring_smem_bytes<T, true>(L.nz, kBlock);
-        k_smooth0<T><<<grid, kBlock, smem, s>>>(L, b, u_out, (T)omega);
+        k_smooth0<T><<<grid, kBlock, smem, s>>>(L, b, u_out, (T)omega, flag);
     } else {
         const size_t smem = (size_t)L.nz * kBlock * sizeof(T);
-        k_smooth<T><<<grid, kBlock, smem, s>>>(L, b, u_in, u_out, (T)omega);
+        k_smooth<T><<<grid, kBlock, smem, s>>>(L, b, u_in, u_out, (T)omega, flag);
     }
     return cudaGetLastError();
 }
@@ -222,8 +258,10 @@ size_t smooth_smem_bytes(int nz, size_t value_bytes)
 // 2I, 2I+1, 2I+2 (mod nlon) with weights 1/4, 3/4, 3/4, 1/4.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
-k_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ r, T *__restrict__ bc, int kz)
+k_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ r, T *__restrict__ bc, int kz,
+           const int *__restrict__ flag)
 {
+    if (flag && !*flag) return;
     const int k0 = blockIdx.y * kz;
     restrict_layers<T>(F, K, r, bc, blockIdx.x * blockDim.x + threadIdx.x, k0,
                        min(F.nz, k0 + kz));
@@ -243,12 +281,12 @@ static int layers_per_thread(size_t columns, int nz)
 
 template <typename T>
 cudaError_t launch_restrict(const LevelDev<T> &F, const LinkDev &K, const T *r, T *bc,
-                            cudaStream_t s)
+                            cudaStream_t s, const int *flag)
 {
     const int ncol_c = (F.nlon / 2) * K.nlat_c;
     const int kz = layers_per_thread(ncol_c, F.nz);
     const dim3 grid((ncol_c + kBlock - 1) / kBlock, (F.nz + kz - 1) / kz);
-    k_restrict<T><<<grid, kBlock, 0, s>>>(F, K, r, bc, kz);
+    k_restrict<T><<<grid, kBlock, 0, s>>>(F, K, r, bc, kz, flag);
     return cudaGetLastError();
 }
 
@@ -259,20 +297,22 @@ cudaError_t launch_restrict(const LevelDev<T> &F, const LinkDev &K, const T *r, 
 // row serve both.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
-k_prolong_add(LevelDev<T> F, LinkDev K, const T *__restrict__ ec, T *__restrict__ u, int kz)
+k_prolong_add(LevelDev<T> F, LinkDev K, const T *__restrict__ ec, T *__restrict__ u, int kz,
+              const int *__restrict__ flag)
 {
+    if (flag && !*flag) return;
     const int k0 = blockIdx.y * kz;
     prolong_layers<T>(F, K, ec, u, blockIdx.x * blockDim.x + threadIdx.x, k0, min(F.nz, k0 + kz));
 }
 
 template <typename T>
 cudaError_t launch_prolong_add(const LevelDev<T> &F, const LinkDev &K, const T *ec, T *u,
-                               cudaStream_t s)
+                               cudaStream_t s, const int *flag)
 {
     const int npair = (F.nlon / 2) * F.nlat;
     const int kz = layers_per_thread(npair, F.nz);
     const dim3 grid((npair + kBlock - 1) / kBlock, (F.nz + kz - 1) / kz);
-    k_prolong_add<T><<<grid, kBlock, 0, s>>>(F, K, ec, u, kz);
+    k_prolong_add<T><<<grid, kBlock, 0, s>>>(F, K, ec, u, kz, flag);
     return cudaGetLastError();
 }
 
@@ -612,22 +652,24 @@ cudaError_t launch_coeff_grad(int nlon, int nlat, int nz, const double *lam, con
 // ------------------------------------------------------------------ instantiations
 #define TPMG_INST(T)                                                                              \
     template int launch_stencil<T>(const LevelDev<T> &, int, const T *, const T *, T *, double *, \
-                                   cudaStream_t);                                                 \
+                                   cudaStream_t, const int *);                                    \
     template cudaError_t launch_smooth<T>(const LevelDev<T> &, const T *, const T *, T *, double,  \
-                                          cudaStream_t);                                          \
+                                          cudaStream_t, const int *);                             \
     template int launch_smooth_dot<T>(const LevelDev<T> &, const T *, const T *, T *, double,      \
-                                      double *, cudaStream_t);                                    \
+                                      double *, cudaStream_t, const int *);                       \
     template cudaError_t launch_restrict<T>(const LevelDev<T> &, const LinkDev &, const T *, T *,  \
-                                            cudaStream_t);                                        \
+                                            cudaStream_t, const int *);                           \
     template cudaError_t launch_prolong_add<T>(const LevelDev<T> &, const LinkDev &, const T *,    \
-                                               T *, cudaStream_t);                                \
+                                               T *, cudaStream_t, const int *);                   \
     template int launch_dot<T>(const T *, const T *, size_t, double *, cudaStream_t);             \
     template int launch_maxabs<T>(const T *, size_t, double *, cudaStream_t);                     \
     template int launch_cg_update<T>(T *, T *, const T *, const T *, size_t, const CgScalars *,    \
                                      double *, cudaStream_t);                                     \
     template cudaError_t launch_cg_direction<T>(const T *, const T *, T *, size_t,                \
                                                 const CgScalars *, bool, cudaStream_t);           \
-    template cudaError_t launch_add<T>(T *, const T *, size_t, cudaStream_t);
+    template cudaError_t launch_add<T>(T *, const T *, size_t, cudaStream_t);                    \
+    template int launch_dir_apply<T>(const LevelDev<T> &, const T *, const T *, const CgScalars *, \
+                                     T *, T *, double *, cudaStream_t, const int *);
 
 TPMG_INST(double)
 TPMG_INST(float)

@@ -42,7 +42,8 @@ def test_default_params(lib):
     from paper_2307_04528_gb300 import _lib as L
     p = L.default_params()
     assert (p.levels, p.nu1, p.nu2, p.coarse_iters, p.method, p.mixed) == (0, 1, 1, 8, 0, 0)
-    assert p.omega == 0.8 and p.alpha_c == 0.6 and p.maxit == 200 and p.inner_tol == 3e-3
+    assert p.omega == 0.85 and p.alpha_c == 0.6 and p.maxit == 200 and p.inner_tol == 5e-4
+    assert p.inner_maxit == 12
 
 
 def _bytes(lib, nlon, nlat, nz, **kw):

@@ -63,3 +63,25 @@ def test_batched_repeat_is_deterministic(batch):
     xb, _ = B.solve(bs, tol=1e-8, mixed=True)
     for a, b in zip(xa, xb):
         assert torch.equal(a, b)
+
+
+def test_batched_large_members_column_paths():
+    """Members large enough for the column-walk residual (>= 32768 columns),
+    the multi-layer transfers and the single-system kernels of large levels
+    (768 x 384 = 294,912 columns), next to a small one: the batched mixed
+    solve meets the tolerance on the oracle's own FP64 residual and agrees
+    with the single-system mixed solve of each member."""
+    from paper_2307_04528_gb300.solver import MGBatch
+    shapes = [(256, 192, 12), (768, 384, 4), (64, 32, 16)]
+    probs = [problem(*shp, sigma=0.1, seed=300 + i) for i, shp in enumerate(shapes)]
+    systems = [tuple(dev(P[k]) for k in ("tx", "ty", "tz", "h")) for P in probs]
+    B = MGBatch(systems, mixed=1)
+    bs = [dev(P["b"]) for P in probs]
+    xs, infos = B.solve(bs, tol=1e-10, mixed=True)
+    for i, P in enumerate(probs):
+        assert infos[i]["status"] == 0 and infos[i]["rel_res"] <= 1e-10
+        lev, _ = oracle_levels(P)
+        rel = O.norm2(O.residual(lev[0], P["b"], host(xs[i]))) / O.norm2(P["b"])
+        assert rel <= 1e-10 and abs(rel - infos[i]["rel_res"]) <= 1e-12
+        xi, _ = B.handle(i).solve_mixed(bs[i], tol=1e-10)
+        assert rel_2(host(xs[i]), host(xi)) <= 1e-8
