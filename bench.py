@@ -183,8 +183,8 @@ KERNEL_WORDS = {
 
 
 # DRAM bytes per fine cell of one k_smooth_dot<float> launch (ncu capture at
-# 512x384x70: 447.8 MB read + 37.3 MB written for 13,762,560 cells)
-SMOOTH_DOT_DRAM_BYTES_PER_CELL = (447.782144e6 + 37.335040e6) / (512 * 384 * 70)
+# 512x384x70: 397.3 MB read + 34.8 MB written for 13,762,560 cells)
+SMOOTH_DOT_DRAM_BYTES_PER_CELL = (397.266944e6 + 34.799616e6) / (512 * 384 * 70)
 
 
 def kernel_table(H, L, N):

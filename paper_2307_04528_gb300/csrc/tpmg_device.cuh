@@ -280,12 +280,63 @@ struct SmoothLoads {
     T b, tz, m, h, txc, txw, tyn, tys, ue, uw, un, us;
 };
 
-template <typename T, bool ZERO, bool PRE>
+// L2 eviction-priority hints (ld.global.nc.L2::cache_hint with a
+// createpolicy policy): the sweep with the fused inner product reads b again
+// in its backward pass, so b is loaded evict_last and the read-once
+// coefficient streams evict_first.
+struct L2Hints {
+    unsigned long long keep, stream;
+};
+
+__device__ __forceinline__ L2Hints make_l2_hints()
+{
+    L2Hints h;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(h.keep));
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(h.stream));
+    return h;
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_hint(const T *p, unsigned long long pol);
+
+template <>
+__device__ __forceinline__ float ld_hint<float>(const float *p, unsigned long long pol)
+{
+    float v;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+template <>
+__device__ __forceinline__ double ld_hint<double>(const double *p, unsigned long long pol)
+{
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+// HINT: loads with the L2 policies above (b kept, coefficients streamed);
+// only for sweeps on a non-zero guess with precomputed factors.
+template <typename T, bool ZERO, bool PRE, bool HINT = false>
 __device__ __forceinline__ void smooth_load(SmoothLoads<T> &s, const LevelDev<T> &L,
                                             const T *__restrict__ b, const T *__restrict__ uin,
                                             size_t o, int col, int ie, int iw, int nlon, bool hasN,
-                                            bool hasS)
+                                            bool hasS, L2Hints hp = L2Hints{})
 {
+    if (HINT) {
+        s.b = ld_hint(b + o + col, hp.keep);
+        s.tz = ld_hint(L.tz + o + col, hp.stream);
+        s.m = ld_hint(L.m + o + col, hp.stream);
+        s.txc = ld_hint(L.tx + o + col, hp.stream);
+        s.txw = __ldg(L.tx + o + iw);
+        s.tyn = hasN ? ld_hint(L.ty + o + col, hp.stream) : T(0);
+        s.tys = hasS ? __ldg(L.ty + o + col - nlon) : T(0);
+        s.ue = __ldg(uin + o + ie);
+        s.uw = __ldg(uin + o + iw);
+        s.un = hasN ? __ldg(uin + o + col + nlon) : T(0);
+        s.us = hasS ? __ldg(uin + o + col - nlon) : T(0);
+        return;
+    }
     s.b = __ldg(b + o + col);
     s.tz = __ldg(L.tz + o + col);
     if (PRE) s.m = __ldg(L.m + o + col);
@@ -316,7 +367,11 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
                                               T omega, int col, unsigned char *smraw,
                                               T *dacc = nullptr)
 {
-    constexpr int kDepth = SmoothDepth<T, ZERO>::value;
+    // the fused-inner-product sweep of the single-system path (BACK == 0)
+    // runs with the L2 hints and a deeper FP32 forward pipeline
+    constexpr bool HINT = DOT && PRE && !ZERO && BACK == 0;
+    constexpr int kDepth = (HINT && sizeof(T) == 4) ? 8 : SmoothDepth<T, ZERO>::value;
+    const L2Hints hp = HINT ? make_l2_hints() : L2Hints{};
     const int nlon = L.nlon, nlat = L.nlat, nz = L.nz;
     const int bd = blockDim.x, tid = threadIdx.x;
     T *ys = reinterpret_cast<T *>(smraw);
@@ -333,8 +388,8 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
 #pragma unroll
     for (int d = 0; d < kDepth; ++d)
         if (d < nz)
-            smooth_load<T, ZERO, PRE>(st[d], L, b, uin, (size_t)d * plane, col, ie, iw, nlon,
-                                      hasN, hasS);
+            smooth_load<T, ZERO, PRE, HINT>(st[d], L, b, uin, (size_t)d * plane, col, ie, iw,
+                                            nlon, hasN, hasS, hp);
 
     T yprev = 0, tdn = 0, dprev = 0;
     for (int k0 = 0; k0 < nz; k0 += kDepth) {
@@ -366,8 +421,8 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
                 yprev = y;
                 tdn = tup;
                 if (k + kDepth < nz)
-                    smooth_load<T, ZERO, PRE>(c, L, b, uin, (size_t)(k + kDepth) * plane, col, ie,
-                                              iw, nlon, hasN, hasS);
+                    smooth_load<T, ZERO, PRE, HINT>(c, L, b, uin, (size_t)(k + kDepth) * plane,
+                                                    col, ie, iw, nlon, hasN, hasS, hp);
             }
         }
     }
@@ -383,7 +438,7 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
         if (k >= 0) {
             const size_t o = (size_t)k * plane + col;
             up[d] = ZERO ? T(0) : __ldg(uin + o);
-            dqp[d] = PRE ? __ldg(L.dq + o) : T(0);
+            dqp[d] = PRE ? (HINT ? ld_hint(L.dq + o, hp.stream) : __ldg(L.dq + o)) : T(0);
             bp[d] = DOT ? __ldg(b + o) : T(0);
         }
     }
@@ -404,7 +459,7 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
                 if (kn >= 0) {
                     const size_t on = (size_t)kn * plane + col;
                     if (!ZERO) up[d] = __ldg(uin + on);
-                    if (PRE) dqp[d] = __ldg(L.dq + on);
+                    if (PRE) dqp[d] = HINT ? ld_hint(L.dq + on, hp.stream) : __ldg(L.dq + on);
                     if (DOT) bp[d] = __ldg(b + on);
                 }
             }
