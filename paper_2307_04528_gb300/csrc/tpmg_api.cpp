@@ -21,6 +21,8 @@
 
 using namespace tpmg;
 
+static_assert(kMaxLayers == MG_MAX_NZ, "device layer bound must match the C ABI");
+
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_last_error;
 
@@ -543,6 +545,11 @@ template <typename T>
 static int smooth_from_zero(mg_handle *H, int l, const LevelDev<T> &D, const T *b, T *out,
                             T *scratch, int sweeps, double omega, cudaStream_t s)
 {
+    if (coarse_solve_fits(D.nlon, D.nlat, sizeof(T))) {  // all sweeps in one launch
+        KRUN(K_SMOOTH0, l, prec_of<T>(),
+             launch_coarse_solve<T>(D, b, out, scratch, omega, sweeps, s));
+        return MG_OK;
+    }
     T *cur = (sweeps % 2 == 1) ? out : scratch;
     T *oth = (cur == out) ? scratch : out;
     KRUN(K_SMOOTH0, l, prec_of<T>(), launch_smooth<T>(D, b, nullptr, cur, omega, s));

@@ -467,6 +467,123 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
     }
 }
 
+// ------------------------------------------------------------------ warp sweep
+// One column of the sweep of Eq. (1) solved by a whole warp, for the small
+// coarse levels, where one thread per column leaves the GPU waiting on the
+// 2 nz dependent steps of the column recurrences.  Lane l owns layers
+// [l C, l C + C), C = ceil(nz / 32).  Both recurrences are first-order and
+// linear, so they run as warp scans of affine maps:
+//   forward   y_k = (v_k + t_{k-1} y_{k-1}) / p_k  = (t_{k-1}/p_k) y_{k-1} + v_k/p_k
+//   backward  x_k = y_k + (1 - q_k/p_k) x_{k+1}      (x_nz = 0)
+// Each lane composes the maps of its layers, a Kogge-Stone scan across the
+// lanes gives each lane the value entering its layers, and the lane then
+// re-runs its own layers with the serial formulas of smooth_column.  The
+// values differ from the serial sweep only by rounding.  u_in is read with
+// ordinary (coherent) loads, so a block may read what its own earlier sweep
+// wrote after a block barrier.  All 32 lanes must call it with the same
+// col < ncol.
+constexpr int kWarpLayers = (kMaxLayers + 31) / 32;  // layers per lane at most
+
+template <typename T, bool ZERO>
+__device__ __forceinline__ void smooth_warp_column(const LevelDev<T> &L, const T *__restrict__ b,
+                                                   const T *uin, T *uout, T omega, int col,
+                                                   int lane)
+{
+    const int nlon = L.nlon, nlat = L.nlat, nz = L.nz;
+    const int j = col / nlon, i = col - j * nlon;
+    const int ie = (i + 1 == nlon) ? col - i : col + 1;
+    const int iw = (i == 0) ? col + nlon - 1 : col - 1;
+    const bool hasN = j + 1 < nlat, hasS = j > 0;
+    const size_t plane = (size_t)nlon * nlat;
+    const int C = (nz + 31) / 32;
+    const int k0 = lane * C;
+    T v[kWarpLayers], tz[kWarpLayers], m[kWarpLayers], dq[kWarpLayers], u0[kWarpLayers];
+#pragma unroll
+    for (int c = 0; c < kWarpLayers; ++c) {
+        const int k = k0 + c;
+        v[c] = tz[c] = m[c] = dq[c] = u0[c] = T(0);
+        if (c < C && k < nz) {
+            const size_t o = (size_t)k * plane;
+            T vv = __ldg(b + o + col);
+            if (!ZERO) {
+                vv = fma(__ldg(L.tx + o + col), uin[o + ie], vv);
+                vv = fma(__ldg(L.tx + o + iw), uin[o + iw], vv);
+                if (hasN) vv = fma(__ldg(L.ty + o + col), uin[o + col + nlon], vv);
+                if (hasS) vv = fma(__ldg(L.ty + o + col - nlon), uin[o + col - nlon], vv);
+                u0[c] = uin[o + col];
+            }
+            v[c] = vv;
+            tz[c] = __ldg(L.tz + o + col);
+            m[c] = __ldg(L.m + o + col);
+            dq[c] = __ldg(L.dq + o + col);
+        }
+    }
+    const T tprev = (k0 >= 1 && k0 - 1 < nz) ? __ldg(L.tz + (size_t)(k0 - 1) * plane + col) : T(0);
+
+    // forward: this lane's map y_out = A y_in + Cy, then an inclusive scan
+    T A = 1, Cy = 0, tp = tprev;
+#pragma unroll
+    for (int c = 0; c < kWarpLayers; ++c) {
+        if (c < C && k0 + c < nz) {
+            const T a = tp * m[c];
+            Cy = fma(a, Cy, v[c] * m[c]);
+            A = a * A;
+            tp = tz[c];
+        }
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T A2 = __shfl_up_sync(0xffffffffu, A, off);
+        const T C2 = __shfl_up_sync(0xffffffffu, Cy, off);
+        if (lane >= off) {
+            Cy = fma(A, C2, Cy);
+            A = A * A2;
+        }
+    }
+    T y = __shfl_up_sync(0xffffffffu, Cy, 1);
+    if (lane == 0) y = T(0);
+    tp = tprev;
+#pragma unroll
+    for (int c = 0; c < kWarpLayers; ++c) {
+        if (c < C && k0 + c < nz) {
+            y = fma(tp, y, v[c]) * m[c];
+            v[c] = y;  // v now holds y
+            tp = tz[c];
+        }
+    }
+
+    // backward: x_bottom = E x_above + F over this lane's layers, suffix scan
+    T E = 1, F = 0;
+#pragma unroll
+    for (int c = kWarpLayers - 1; c >= 0; --c) {
+        if (c < C && k0 + c < nz) {
+            const T e = T(1) - dq[c];
+            F = fma(e, F, v[c]);
+            E = e * E;
+        }
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T E2 = __shfl_down_sync(0xffffffffu, E, off);
+        const T F2 = __shfl_down_sync(0xffffffffu, F, off);
+        if (lane + off < 32) {
+            F = fma(E, F2, F);
+            E = E * E2;
+        }
+    }
+    T x = __shfl_down_sync(0xffffffffu, F, 1);
+    if (lane == 31) x = T(0);
+    const T om1 = T(1) - omega;
+#pragma unroll
+    for (int c = kWarpLayers - 1; c >= 0; --c) {
+        const int k = k0 + c;
+        if (c < C && k < nz) {
+            x = x + fma(-dq[c], x, v[c]);
+            uout[(size_t)k * plane + col] = ZERO ? omega * x : fma(om1, u0[c], omega * x);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ staged sweep
 // Asynchronous global->shared copies (cp.async, 4 or 8 bytes per thread).
 // Each thread stages and later reads only its own slots, so completion of

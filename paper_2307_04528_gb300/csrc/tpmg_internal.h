@@ -39,6 +39,7 @@ struct CgScalars {
 };
 
 constexpr int kBlock = 128;          // threads per block, one column per thread
+constexpr int kMaxLayers = 192;      // MG_MAX_NZ of the C ABI (checked in tpmg_api.cpp)
 constexpr int kReduceSlots = 65536;  // per-block partial sums kept in the workspace
 
 // ---- launchers (tpmg_kernels.cu); all asynchronous on `s` -----------------
@@ -65,6 +66,14 @@ int launch_dir_apply(const LevelDev<T> &L, const T *z, const T *d_old, const CgS
 template <typename T>
 cudaError_t launch_smooth(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out,
                           double omega, cudaStream_t s, const int *flag = nullptr);
+
+// The coarsest-level solve: `sweeps` sweeps from a zero guess in one
+// one-block launch (result in out; scratch: a second level vector), for
+// coarsest levels where coarse_solve_fits(nlon, nlat, sizeof value).
+bool coarse_solve_fits(int nlon, int nlat, size_t value_bytes);
+template <typename T>
+cudaError_t launch_coarse_solve(const LevelDev<T> &L, const T *b, T *out, T *scratch, double omega,
+                                int sweeps, cudaStream_t s);
 
 // The same sweep (non-zero guess) writing the block sums of <b, u_out> to
 // partial[block]; returns the number of blocks.

@@ -193,12 +193,82 @@ int launch_smooth_dot(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out,
     return grid;
 }
 
+// One warp per column (smooth_warp_column), for levels small enough that
+// the serial column recurrences would dominate.
+template <typename T, bool ZERO>
+__global__ void __launch_bounds__(kBlock)
+k_smooth_warp(LevelDev<T> L, const T *__restrict__ b, const T *uin, T *uout, T omega,
+              const int *__restrict__ flag)
+{
+    if (flag && !*flag) return;
+    const int col = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (col >= L.nlon * L.nlat) return;  // whole warps
+    smooth_warp_column<T, ZERO>(L, b, uin, uout, omega, col, threadIdx.x & 31);
+}
+
+// The coarsest-level solve (Section 2.3's simple iteration: `sweeps`
+// block-Jacobi sweeps from a zero guess) as one block: the warps share the
+// columns, a block barrier separates the sweeps, and the sweeps alternate
+// between out and scratch so that the last one lands in out.
+constexpr int kCoarseSolveThreads = 512;  // 16 warps (registers of the FP64 sweep)
+
+template <typename T>
+__global__ void __launch_bounds__(kCoarseSolveThreads)
+k_coarse_solve(LevelDev<T> L, const T *__restrict__ b, T *out, T *scratch, T omega, int sweeps,
+               const int *__restrict__ flag)
+{
+    if (flag && !*flag) return;
+    const int ncol = L.nlon * L.nlat;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T *cur = (sweeps % 2 == 1) ? out : scratch;
+    T *oth = (cur == out) ? scratch : out;
+    for (int c = warp; c < ncol; c += nw) smooth_warp_column<T, true>(L, b, nullptr, cur, omega, c, lane);
+    for (int it = 1; it < sweeps; ++it) {
+        __syncthreads();  // the previous sweep is visible to the whole block
+        for (int c = warp; c < ncol; c += nw)
+            smooth_warp_column<T, false>(L, b, cur, oth, omega, c, lane);
+        T *t = cur;
+        cur = oth;
+        oth = t;
+    }
+}
+
+// FP32 levels with at most this many cells take the warp sweep (larger
+// ones do not fit L2, where the warp's strided column loads cost sectors).
+constexpr size_t kWarpSweepCells = (size_t)1 << 17;
+// Coarsest levels with at most this many columns take the one-block solve.
+constexpr int kCoarseSolveColumns = 2048;
+
+// FP32 only: the scans cost about twice the FP64 operations of the serial
+// sweep, and the FP64 sweeps are bound by FP64 arithmetic.
+bool coarse_solve_fits(int nlon, int nlat, size_t value_bytes)
+{
+    return value_bytes == 4 && nlon * nlat <= kCoarseSolveColumns;
+}
+
+template <typename T>
+cudaError_t launch_coarse_solve(const LevelDev<T> &L, const T *b, T *out, T *scratch, double omega,
+                                int sweeps, cudaStream_t s)
+{
+    k_coarse_solve<T><<<1, kCoarseSolveThreads, 0, s>>>(L, b, out, scratch, (T)omega, sweeps,
+                                                         nullptr);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_smooth(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out, double omega,
                           cudaStream_t s, const int *flag)
 {
     const int ncol = L.nlon * L.nlat;
     const int grid = (ncol + kBlock - 1) / kBlock;
+    if (sizeof(T) == 4 && (size_t)ncol * L.nz <= kWarpSweepCells) {
+        const int wgrid = (int)(((size_t)ncol * 32 + kBlock - 1) / kBlock);
+        if (u_in == nullptr)
+            k_smooth_warp<T, true><<<wgrid, kBlock, 0, s>>>(L, b, nullptr, u_out, (T)omega, flag);
+        else
+            k_smooth_warp<T, false><<<wgrid, kBlock, 0, s>>>(L, b, u_in, u_out, (T)omega, flag);
+        return cudaGetLastError();
+    }
     if (u_in == nullptr) {
         const size_t smem = ring_smem_bytes<T, true>(L.nz, kBlock);
         k_smooth0<T><<<grid, kBlock, smem, s>>>(L, b, u_out, (T)omega, flag);
@@ -668,6 +738,8 @@ cudaError_t launch_coeff_grad(int nlon, int nlat, int nz, const double *lam, con
     template cudaError_t launch_cg_direction<T>(const T *, const T *, T *, size_t,                \
                                                 const CgScalars *, bool, cudaStream_t);           \
     template cudaError_t launch_add<T>(T *, const T *, size_t, cudaStream_t);                    \
+    template cudaError_t launch_coarse_solve<T>(const LevelDev<T> &, const T *, T *, T *, double, \
+                                                int, cudaStream_t);                               \
     template int launch_dir_apply<T>(const LevelDev<T> &, const T *, const T *, const CgScalars *, \
                                      T *, T *, double *, cudaStream_t, const int *);
 
