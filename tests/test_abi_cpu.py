@@ -71,6 +71,7 @@ def test_workspace_sizing(lib):
                                       ((2, 32, 16), {}),         # nlon < 4
                                       ((64, 32, 0), {}),         # nz < 1
                                       ((64, 32, 300), {}),       # nz > MG_MAX_NZ
+                                      ((64, 32, 193), {}),       # nz = MG_MAX_NZ + 1
                                       ((48, 32, 4), {"levels": 6}),  # 48 not divisible by 32
                                       ((64, 32, 4), {"omega": 2.5}),
                                       ((64, 32, 4), {"nu1": 0})])
