@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_bsmooth(const BOp<T> *__restrict_
         if (ZERO)
             smooth_staged<T, true>(op.L, op.a, nullptr, op.y, omega, col, smraw);
         else
-            smooth_column<T, false, true>(op.L, op.a, op.x, op.y, omega, col, smraw);
+            smooth_column<T>(op.L, op.a, op.x, op.y, omega, col, smraw);
     }
 }
 
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_bsmooth_dot(const BOp<T> *__restr
         const BOp<T> &op = ops[item.op];
         if (active && !active[op.sys]) continue;
         T acc = 0;
-        smooth_column<T, false, true, true, 6>(op.L, op.a, op.x, op.y, omega,
+        smooth_column<T, true, 6>(op.L, op.a, op.x, op.y, omega,
                                                item.tile * blockDim.x + threadIdx.x, smraw, &acc);
         block_store_at<0>((double)acc, partial, it);
     }

@@ -71,7 +71,7 @@ struct RedPlan {            // fine-level stencil with per-system reduction
 template <typename T>
 struct PrecPlan {
     std::vector<StepHost<T>> vsteps;   // batched V-cycle: cg.r -> cg.z of every system
-    VecPlan<T> dot_rz, dot_bb, update[2], dir[2], dir0, add, rmax, rcopy, xmax;
+    VecPlan<T> dot_rz, dot_bb, update[2], dir[2], dir0, add, rcopy, xmax;
     RedPlan<T> resid;                  // r = b - H x (+ |r|^2), fixed b and x
     RedPlan<T> apply[2];               // Ad = H d (+ d.Ad), d = d0 / d1
     RedPlan<T> dirapply0, dirapply[2]; // d = z (+ beta d_old) and Ad = H d (+ d.Ad)
@@ -430,7 +430,6 @@ void build_vector_plans(mg_batch *B)
     vec_plan<T>(B, P.dir[1], d0, z, d1, nullptr);   // d0 = z + beta d1
     vec_plan<T>(B, P.dir0, d0, z, nullptr, nullptr);
     vec_plan<T>(B, P.add, xx, z, nullptr, nullptr);
-    vec_plan<T>(B, P.rmax, r, nullptr, nullptr, nullptr);
     red_plan<T>(B, P.resid, [](mg_handle *H) -> const T * { return bx_of<T>(H); },
                 [](mg_handle *H) -> const T * { return xx_of<T>(H); }, r);
     red_plan<T>(B, P.apply[0], nullptr, [](mg_handle *H) -> const T * { return Vec<T>::cg(H).d0; },
@@ -525,7 +524,7 @@ void carve_plan(Bump &b, PrecPlan<T> &P, size_t *max_items)
         *max_items = std::max(*max_items, cap);
     }
     for (VecPlan<T> *V : {&P.dot_rz, &P.dot_bb, &P.update[0], &P.update[1], &P.dir[0], &P.dir[1],
-                          &P.dir0, &P.add, &P.rmax, &P.rcopy, &P.xmax}) {
+                          &P.dir0, &P.add, &P.rcopy, &P.xmax}) {
         carve_vec(b, *V);
         *max_items = std::max(*max_items, V->items.size());
     }
@@ -576,7 +575,7 @@ int upload_plan(PrecPlan<T> &P, cudaStream_t s)
 {
     for (auto &st : P.vsteps) CHK(upload_step(st, s));
     for (VecPlan<T> *V : {&P.dot_rz, &P.dot_bb, &P.update[0], &P.update[1], &P.dir[0], &P.dir[1],
-                          &P.dir0, &P.add, &P.rmax, &P.rcopy, &P.xmax})
+                          &P.dir0, &P.add, &P.rcopy, &P.xmax})
         CHK(upload_vec(*V, s));
     for (RedPlan<T> *R : {&P.resid, &P.apply[0], &P.apply[1], &P.dirapply0, &P.dirapply[0],
                           &P.dirapply[1]})

@@ -254,30 +254,28 @@ __device__ __forceinline__ void stencil_cell(const LevelDev<T> &L, const T *__re
 // One sweep of Eq. (1), u_out = (1 - omega) u_in + omega H_z^{-1}(b - dH u_in),
 // with the column tridiagonal H_z (diagonal s_k + t_{k-1} + t_k, couplings
 // -t_k, s_k = h + the four horizontal couplings) solved by elimination with
-// pivots p_k = q_k + t_k:
-//   forward   y_k = (v_k + t_{k-1} y_{k-1}) / p_k
-//   backward  x_k = x_{k+1} + (y_k - (q_k / p_k) x_{k+1})
-// PRE: 1/p_k and q_k/p_k read from the setup factors; otherwise
-// q_k = s_k + t_{k-1} q_{k-1}/p_{k-1} is formed on the fly.  The forward
-// values y (and q/p on the fly) wait in shared memory for the backward sweep:
-// blockDim x nz values per array.
+// pivots p_k = q_k + t_k, on the setup factors m_k = 1/p_k and dq_k = q_k/p_k:
+//   forward   y_k = (v_k + t_{k-1} y_{k-1}) m_k,  v_k = b_k + sum_h T u_in,nb
+//   backward  x_k = x_{k+1} + (y_k - dq_k x_{k+1})
+// This is the sweep on a non-zero guess; sweeps from a zero guess are
+// smooth_staged (large levels) and smooth_warp_column (small FP32 levels).
+// The forward values y wait in shared memory for the backward sweep
+// (blockDim x nz values).
 //
-// Shared memory caps residency at ~3 blocks of 128 columns per SM, so the
+// Shared memory caps residency at a few blocks of 128 columns per SM, so the
 // loads of layers k+1..k+DEPTH are issued before layer k is computed (a
 // register pipeline) to keep enough bytes in flight to cover HBM latency:
-// deeper for the FP32 sweeps (few registers per layer, HBM-bound), shallow
-// for FP64 (FP64-ALU-bound, twice the registers per value).
-template <typename T, bool ZERO>
+// deeper for FP32 (few registers per layer, HBM-bound), shallow for FP64
+// (FP64-ALU-bound, twice the registers per value).
+template <typename T>
 struct SmoothDepth {
-    // forward sweep: layers of loads in flight per thread
-    static constexpr int value = sizeof(T) == 8 ? (ZERO ? 4 : 3) : (ZERO ? 16 : 6);
-    // backward sweep (one or two streams per layer): deeper
-    static constexpr int back = sizeof(T) == 8 ? 4 : (ZERO ? 16 : 12);
+    static constexpr int value = sizeof(T) == 8 ? 3 : 6;  // forward: layers in flight
+    static constexpr int back = sizeof(T) == 8 ? 4 : 12;  // backward (u_in, q/p, b)
 };
 
 template <typename T>
 struct SmoothLoads {
-    T b, tz, m, h, txc, txw, tyn, tys, ue, uw, un, us;
+    T b, tz, m, txc, txw, tyn, tys, ue, uw, un, us;
 };
 
 // L2 eviction-priority hints (ld.global.nc.L2::cache_hint with a
@@ -315,67 +313,54 @@ __device__ __forceinline__ double ld_hint<double>(const double *p, unsigned long
     return v;
 }
 
-// HINT: loads with the L2 policies above (b kept, coefficients streamed);
-// only for sweeps on a non-zero guess with precomputed factors.
-template <typename T, bool ZERO, bool PRE, bool HINT = false>
+// One layer's loads of the sweep.  HINT: b kept and the own-column
+// coefficients streamed in L2 (the policies above).
+template <typename T, bool HINT>
 __device__ __forceinline__ void smooth_load(SmoothLoads<T> &s, const LevelDev<T> &L,
                                             const T *__restrict__ b, const T *__restrict__ uin,
                                             size_t o, int col, int ie, int iw, int nlon, bool hasN,
-                                            bool hasS, L2Hints hp = L2Hints{})
+                                            bool hasS, L2Hints hp)
 {
     if (HINT) {
         s.b = ld_hint(b + o + col, hp.keep);
         s.tz = ld_hint(L.tz + o + col, hp.stream);
         s.m = ld_hint(L.m + o + col, hp.stream);
         s.txc = ld_hint(L.tx + o + col, hp.stream);
-        s.txw = __ldg(L.tx + o + iw);
         s.tyn = hasN ? ld_hint(L.ty + o + col, hp.stream) : T(0);
-        s.tys = hasS ? __ldg(L.ty + o + col - nlon) : T(0);
-        s.ue = __ldg(uin + o + ie);
-        s.uw = __ldg(uin + o + iw);
-        s.un = hasN ? __ldg(uin + o + col + nlon) : T(0);
-        s.us = hasS ? __ldg(uin + o + col - nlon) : T(0);
-        return;
-    }
-    s.b = __ldg(b + o + col);
-    s.tz = __ldg(L.tz + o + col);
-    if (PRE) s.m = __ldg(L.m + o + col);
-    if (!PRE) s.h = __ldg(L.h + o + col);
-    if (!ZERO || !PRE) {
+    } else {
+        s.b = __ldg(b + o + col);
+        s.tz = __ldg(L.tz + o + col);
+        s.m = __ldg(L.m + o + col);
         s.txc = __ldg(L.tx + o + col);
-        s.txw = __ldg(L.tx + o + iw);
         s.tyn = hasN ? __ldg(L.ty + o + col) : T(0);
-        s.tys = hasS ? __ldg(L.ty + o + col - nlon) : T(0);
     }
-    if (!ZERO) {
-        s.ue = __ldg(uin + o + ie);
-        s.uw = __ldg(uin + o + iw);
-        s.un = hasN ? __ldg(uin + o + col + nlon) : T(0);
-        s.us = hasS ? __ldg(uin + o + col - nlon) : T(0);
-    }
+    s.txw = __ldg(L.tx + o + iw);
+    s.tys = hasS ? __ldg(L.ty + o + col - nlon) : T(0);
+    s.ue = __ldg(uin + o + ie);
+    s.uw = __ldg(uin + o + iw);
+    s.un = hasN ? __ldg(uin + o + col + nlon) : T(0);
+    s.us = hasS ? __ldg(uin + o + col - nlon) : T(0);
 }
 
 // One column of the sweep.  smraw: this block's dynamic shared memory
-// (nz * blockDim values of T per stored array).  DOT: also accumulate
-// sum_k b_k u_out,k of the column into *dacc (the CG inner product <r, z>
-// when the sweep is the last one of a V-cycle applied to r).
-// BACK > 0 overrides the depth of the backward pipeline (the batched kernels,
-// which hold their work-item descriptors in registers as well).
-template <typename T, bool ZERO, bool PRE, bool DOT = false, int BACK = 0>
+// (nz * blockDim values of T).  DOT: also accumulate sum_k b_k u_out,k of
+// the column into *dacc (the CG inner product <r, z> when the sweep is the
+// last one of a V-cycle applied to r); the single-system DOT sweep (BACK ==
+// 0) loads with the L2 hints and an 8-layer FP32 forward pipeline.  BACK > 0
+// overrides the backward depth (the batched kernels, which hold their
+// work-item descriptors in registers as well).
+template <typename T, bool DOT = false, int BACK = 0>
 __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__restrict__ b,
                                               const T *__restrict__ uin, T *__restrict__ uout,
                                               T omega, int col, unsigned char *smraw,
                                               T *dacc = nullptr)
 {
-    // the fused-inner-product sweep of the single-system path (BACK == 0)
-    // runs with the L2 hints and a deeper FP32 forward pipeline
-    constexpr bool HINT = DOT && PRE && !ZERO && BACK == 0;
-    constexpr int kDepth = (HINT && sizeof(T) == 4) ? 8 : SmoothDepth<T, ZERO>::value;
+    constexpr bool HINT = DOT && BACK == 0;
+    constexpr int kDepth = (HINT && sizeof(T) == 4) ? 8 : SmoothDepth<T>::value;
     const L2Hints hp = HINT ? make_l2_hints() : L2Hints{};
     const int nlon = L.nlon, nlat = L.nlat, nz = L.nz;
     const int bd = blockDim.x, tid = threadIdx.x;
     T *ys = reinterpret_cast<T *>(smraw);
-    T *ds = ys + (size_t)nz * bd;
     const int ncol = nlon * nlat;
     if (col >= ncol) return;
     const int j = col / nlon, i = col - j * nlon;
@@ -388,10 +373,10 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
 #pragma unroll
     for (int d = 0; d < kDepth; ++d)
         if (d < nz)
-            smooth_load<T, ZERO, PRE, HINT>(st[d], L, b, uin, (size_t)d * plane, col, ie, iw,
-                                            nlon, hasN, hasS, hp);
+            smooth_load<T, HINT>(st[d], L, b, uin, (size_t)d * plane, col, ie, iw, nlon, hasN,
+                                 hasS, hp);
 
-    T yprev = 0, tdn = 0, dprev = 0;
+    T yprev = 0, tdn = 0;
     for (int k0 = 0; k0 < nz; k0 += kDepth) {
 #pragma unroll
         for (int d = 0; d < kDepth; ++d) {
@@ -399,46 +384,33 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
             if (k < nz) {
                 SmoothLoads<T> &c = st[d];
                 T v = c.b;
-                if (!ZERO) {
-                    v = fma(c.txc, c.ue, v);
-                    v = fma(c.txw, c.uw, v);
-                    v = fma(c.tyn, c.un, v);
-                    v = fma(c.tys, c.us, v);
-                }
-                const T tup = c.tz;
-                T y;
-                if (PRE) {
-                    y = fma(tdn, yprev, v) * c.m;
-                } else {
-                    const T s = c.h + c.txc + c.txw + c.tyn + c.tys;
-                    const T q = (k == 0) ? s : fma(tdn, dprev, s);
-                    const T inv = T(1) / (q + tup);
-                    y = fma(tdn, yprev, v) * inv;
-                    dprev = q * inv;
-                    ds[(size_t)k * bd + tid] = dprev;
-                }
+                v = fma(c.txc, c.ue, v);
+                v = fma(c.txw, c.uw, v);
+                v = fma(c.tyn, c.un, v);
+                v = fma(c.tys, c.us, v);
+                const T y = fma(tdn, yprev, v) * c.m;
                 ys[(size_t)k * bd + tid] = y;
                 yprev = y;
-                tdn = tup;
+                tdn = c.tz;
                 if (k + kDepth < nz)
-                    smooth_load<T, ZERO, PRE, HINT>(c, L, b, uin, (size_t)(k + kDepth) * plane,
-                                                    col, ie, iw, nlon, hasN, hasS, hp);
+                    smooth_load<T, HINT>(c, L, b, uin, (size_t)(k + kDepth) * plane, col, ie, iw,
+                                         nlon, hasN, hasS, hp);
             }
         }
     }
 
     const T om1 = T(1) - omega;
     T xk = yprev;
-    // backward sweep: prefetch u_in (and the precomputed q/p) kBack layers ahead
-    constexpr int kBack = BACK > 0 ? BACK : SmoothDepth<T, ZERO>::back;
+    // backward sweep: prefetch u_in, q/p (and b) kBack layers ahead
+    constexpr int kBack = BACK > 0 ? BACK : SmoothDepth<T>::back;
     T up[kBack], dqp[kBack], bp[kBack];
 #pragma unroll
     for (int d = 0; d < kBack; ++d) {
         const int k = nz - 1 - d;
         if (k >= 0) {
             const size_t o = (size_t)k * plane + col;
-            up[d] = ZERO ? T(0) : __ldg(uin + o);
-            dqp[d] = PRE ? (HINT ? ld_hint(L.dq + o, hp.stream) : __ldg(L.dq + o)) : T(0);
+            up[d] = __ldg(uin + o);
+            dqp[d] = HINT ? ld_hint(L.dq + o, hp.stream) : __ldg(L.dq + o);
             bp[d] = DOT ? __ldg(b + o) : T(0);
         }
     }
@@ -448,18 +420,15 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
             const int k = k0 - d;
             if (k >= 0) {
                 const size_t o = (size_t)k * plane + col;
-                if (k < nz - 1) {
-                    const T dqk = PRE ? dqp[d] : ds[(size_t)k * bd + tid];
-                    xk = xk + fma(-dqk, xk, ys[(size_t)k * bd + tid]);
-                }
-                const T uo = ZERO ? omega * xk : fma(om1, up[d], omega * xk);
+                if (k < nz - 1) xk = xk + fma(-dqp[d], xk, ys[(size_t)k * bd + tid]);
+                const T uo = fma(om1, up[d], omega * xk);
                 uout[o] = uo;
                 if (DOT) *dacc = fma(bp[d], uo, *dacc);
                 const int kn = k - kBack;
                 if (kn >= 0) {
                     const size_t on = (size_t)kn * plane + col;
-                    if (!ZERO) up[d] = __ldg(uin + on);
-                    if (PRE) dqp[d] = HINT ? ld_hint(L.dq + on, hp.stream) : __ldg(L.dq + on);
+                    up[d] = __ldg(uin + on);
+                    dqp[d] = HINT ? ld_hint(L.dq + on, hp.stream) : __ldg(L.dq + on);
                     if (DOT) bp[d] = __ldg(b + on);
                 }
             }

@@ -151,7 +151,7 @@ k_smooth(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ uin, T *_
 {
     if (flag && !*flag) return;
     extern __shared__ __align__(16) unsigned char smraw[];
-    smooth_column<T, false, true>(L, b, uin, uout, omega, blockIdx.x * blockDim.x + threadIdx.x,
+    smooth_column<T>(L, b, uin, uout, omega, blockIdx.x * blockDim.x + threadIdx.x,
                                   smraw);
 }
 
@@ -177,7 +177,7 @@ k_smooth_dot(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ uin,
     if (flag && !*flag) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     T acc = 0;
-    smooth_column<T, false, true, true>(L, b, uin, uout, omega,
+    smooth_column<T, true>(L, b, uin, uout, omega,
                                         blockIdx.x * blockDim.x + threadIdx.x, smraw, &acc);
     block_store<0>((double)acc, partial);
 }
