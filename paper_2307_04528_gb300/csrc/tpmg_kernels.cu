@@ -210,7 +210,7 @@ k_smooth_warp(LevelDev<T> L, const T *__restrict__ b, const T *uin, T *uout, T o
 // block-Jacobi sweeps from a zero guess) as one block: the warps share the
 // columns, a block barrier separates the sweeps, and the sweeps alternate
 // between out and scratch so that the last one lands in out.
-constexpr int kCoarseSolveThreads = 512;  // 16 warps (registers of the FP64 sweep)
+constexpr int kCoarseSolveThreads = 1024;  // 32 warps (FP32 only: ~56 registers per thread)
 
 template <typename T>
 __global__ void __launch_bounds__(kCoarseSolveThreads)

@@ -85,3 +85,13 @@ def test_batched_large_members_column_paths():
         assert rel <= 1e-10 and abs(rel - infos[i]["rel_res"]) <= 1e-12
         xi, _ = B.handle(i).solve_mixed(bs[i], tol=1e-10)
         assert rel_2(host(xs[i]), host(xi)) <= 1e-8
+    # the FP64 batched solve takes the same large-level dispatch
+    x64, inf64 = B.solve(bs, tol=1e-10, mixed=False)
+    for i, P in enumerate(probs):
+        assert inf64[i]["status"] == 0 and inf64[i]["rel_res"] <= 1e-10
+        lev, _ = oracle_levels(P)
+        rel = O.norm2(O.residual(lev[0], P["b"], host(x64[i]))) / O.norm2(P["b"])
+        assert rel <= 1e-10 and abs(rel - inf64[i]["rel_res"]) <= 1e-12
+        xi, inf1 = B.handle(i).solve(bs[i], tol=1e-10)
+        assert abs(inf1["iterations"] - inf64[i]["iterations"]) <= 1
+        assert rel_2(host(x64[i]), host(xi)) <= 1e-8
