@@ -387,9 +387,15 @@ cudaError_t launch_prolong_add(const LevelDev<T> &F, const LinkDev &K, const T *
 }
 
 // ------------------------------------------------------------------ vectors
+// Grid of the vector kernels: one wave of full occupancy (16 blocks of 128
+// threads per SM) striding over the vector, at least 8 elements per thread;
+// a grid-stride stream of this shape runs at the copy rate, where one block
+// per few elements spends its time starting blocks.
 static inline int red_grid(size_t n)
 {
     size_t g = (n + (size_t)kBlock * 8 - 1) / ((size_t)kBlock * 8);
+    const size_t wave = (size_t)g_sms * 16;
+    if (g > wave) g = wave;
     if (g < 1) g = 1;
     if (g > (size_t)kReduceSlots) g = kReduceSlots;
     return (int)g;
@@ -400,6 +406,7 @@ __global__ void __launch_bounds__(kBlock)
 k_dot(const T *__restrict__ a, const T *__restrict__ b, size_t n, double *partial)
 {
     T acc = 0;
+#pragma unroll 4
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
          c += (size_t)gridDim.x * blockDim.x)
         acc = fma(a[c], b[c], acc);
@@ -418,6 +425,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_maxabs(const T *__restrict__ a, size_t n, double *partial)
 {
     double m = 0;
+#pragma unroll 4
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
          c += (size_t)gridDim.x * blockDim.x) {
         const double v = fabs((double)a[c]);
@@ -441,6 +449,7 @@ k_cg_update(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ d, const
 {
     const T alpha = (T)sc->alpha;
     T acc = 0;
+#pragma unroll 4
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
          c += (size_t)gridDim.x * blockDim.x) {
         x[c] = fma(alpha, d[c], x[c]);
@@ -466,6 +475,7 @@ k_cg_direction(const T *__restrict__ z, const T *__restrict__ din, T *__restrict
                const CgScalars *sc)
 {
     const T beta = BZ ? T(0) : (T)sc->beta;
+#pragma unroll 4
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
          c += (size_t)gridDim.x * blockDim.x)
         dout[c] = BZ ? z[c] : fma(beta, din[c], z[c]);
@@ -475,7 +485,7 @@ template <typename T>
 cudaError_t launch_cg_direction(const T *z, const T *d_in, T *d_out, size_t n, const CgScalars *sc,
                                 bool beta_zero, cudaStream_t s)
 {
-    const int g = red_grid(n) * 2;
+    const int g = red_grid(n);
     if (beta_zero) k_cg_direction<T, true><<<g, kBlock, 0, s>>>(z, d_in, d_out, n, sc);
     else k_cg_direction<T, false><<<g, kBlock, 0, s>>>(z, d_in, d_out, n, sc);
     return cudaGetLastError();
@@ -484,6 +494,7 @@ cudaError_t launch_cg_direction(const T *z, const T *d_in, T *d_out, size_t n, c
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_add(T *__restrict__ x, const T *__restrict__ e, size_t n)
 {
+#pragma unroll 4
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
          c += (size_t)gridDim.x * blockDim.x)
         x[c] += e[c];
@@ -492,13 +503,14 @@ __global__ void __launch_bounds__(kBlock) k_add(T *__restrict__ x, const T *__re
 template <typename T>
 cudaError_t launch_add(T *x, const T *e, size_t n, cudaStream_t s)
 {
-    k_add<T><<<red_grid(n) * 2, kBlock, 0, s>>>(x, e, n);
+    k_add<T><<<red_grid(n), kBlock, 0, s>>>(x, e, n);
     return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(kBlock)
 k_cast_scaled(const double *__restrict__ r, float *__restrict__ r32, double inv, size_t n)
 {
+#pragma unroll 4
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
          c += (size_t)gridDim.x * blockDim.x)
         r32[c] = (float)(r[c] * inv);
@@ -507,13 +519,14 @@ k_cast_scaled(const double *__restrict__ r, float *__restrict__ r32, double inv,
 cudaError_t launch_cast_scaled(const double *r, float *r32, double inv_scale, size_t n,
                                cudaStream_t s)
 {
-    k_cast_scaled<<<red_grid(n) * 2, kBlock, 0, s>>>(r, r32, inv_scale, n);
+    k_cast_scaled<<<red_grid(n), kBlock, 0, s>>>(r, r32, inv_scale, n);
     return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(kBlock)
 k_update_mixed(double *__restrict__ x, const float *__restrict__ e, double scale, size_t n)
 {
+#pragma unroll 4
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
          c += (size_t)gridDim.x * blockDim.x)
         x[c] = fma(scale, (double)e[c], x[c]);
@@ -521,7 +534,7 @@ k_update_mixed(double *__restrict__ x, const float *__restrict__ e, double scale
 
 cudaError_t launch_update_mixed(double *x, const float *e, double scale, size_t n, cudaStream_t s)
 {
-    k_update_mixed<<<red_grid(n) * 2, kBlock, 0, s>>>(x, e, scale, n);
+    k_update_mixed<<<red_grid(n), kBlock, 0, s>>>(x, e, scale, n);
     return cudaGetLastError();
 }
 
@@ -682,7 +695,7 @@ k_to_float(const double *__restrict__ in, float *__restrict__ out, double scale,
 
 cudaError_t launch_to_float(const double *in, float *out, double scale, size_t n, cudaStream_t s)
 {
-    k_to_float<<<red_grid(n) * 2, kBlock, 0, s>>>(in, out, scale, n);
+    k_to_float<<<red_grid(n), kBlock, 0, s>>>(in, out, scale, n);
     return cudaGetLastError();
 }
 
