@@ -171,6 +171,16 @@ int mg_level_residual(mg_handle *h, int level, int prec, const void *b, const vo
 int mg_level_smooth(mg_handle *h, int level, int prec, const void *b, const void *u_in,
                     void *u_out, void *stream);
 
+/* out = `sweeps` sweeps of Eq. (1) on level l from the zero guess (b, out:
+ * the level's shape, distinct).  On the coarsest level with sweeps =
+ * coarse_iters this is the V-cycle's coarsest-level solve (Section 2.3: a
+ * simple iteration on the coarsest grid), run as one launch when the level
+ * is small enough; elsewhere one launch per sweep.  Uses the handle's level
+ * scratch vector: calls on one handle must not overlap.  MG_ERR_ARG for
+ * sweeps outside 1..1000 or aliased buffers. */
+int mg_level_relax(mg_handle *h, int level, int prec, int sweeps, const void *b, void *out,
+                   void *stream);
+
 /* The same sweep (u_in != NULL) also returning *dot = <b, u_out> (host
  * double; FP64 accumulation of per-column sums): the last sweep of a V-cycle
  * with the conjugate-gradient inner product <r, z> fused in.  Synchronises. */

@@ -344,6 +344,16 @@ static int device_max(mg_handle *H, const double *a, size_t n, double *out, cuda
 
 static int setup_impl(mg_handle *H, const mg_coeffs *co, void *ws, size_t ws_bytes, cudaStream_t s)
 {
+    // A coarse row gathers its own one or two fine rows and at most the
+    // nearer child of each neighbouring pair: the restriction kernels hold
+    // kMaxRestrictRows rows per coarse row.
+    for (int l = 0; l + 1 < H->L; ++l) {
+        const std::vector<int> &rp = H->lev[l].link.rptr;
+        for (size_t J = 0; J + 1 < rp.size(); ++J)
+            if (rp[J + 1] - rp[J] > kMaxRestrictRows)
+                return fail(MG_ERR_ARG, "level %d: coarse row %zu gathers %d fine rows (> %d)", l,
+                            J, rp[J + 1] - rp[J], kMaxRestrictRows);
+    }
     size_t need = carve(H, nullptr);
     if (!ws) return fail(MG_ERR_WORKSPACE, "null workspace");
     if ((uintptr_t)ws % 256) return fail(MG_ERR_WORKSPACE, "workspace not 256-byte aligned");
@@ -1025,6 +1035,26 @@ extern "C" int mg_level_prolong_add(mg_handle *H, int level, int prec, const voi
                                     void *stream)
 {
     return level_dispatch(H, level, prec, 4, ec, nullptr, u, stream);
+}
+
+extern "C" int mg_level_relax(mg_handle *H, int level, int prec, int sweeps, const void *b,
+                              void *out, void *stream)
+{
+    CHK(level_check(H, level, prec, false));
+    if (!b || !out || b == out) return fail(MG_ERR_ARG, "bad relaxation buffers");
+    if (sweeps < 1 || sweeps > 1000) return fail(MG_ERR_ARG, "sweeps outside 1..1000");
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelHost &v = H->lev[level];
+    if (prec == MG_PREC_FP64) {
+        if (out == Vec<double>::w(v) || b == Vec<double>::w(v))
+            return fail(MG_ERR_ARG, "buffer aliases the level scratch");
+        return smooth_from_zero<double>(H, level, dev<double>(v), (const double *)b,
+                                        (double *)out, Vec<double>::w(v), sweeps, H->p.omega, s);
+    }
+    if (out == Vec<float>::w(v) || b == Vec<float>::w(v))
+        return fail(MG_ERR_ARG, "buffer aliases the level scratch");
+    return smooth_from_zero<float>(H, level, dev<float>(v), (const float *)b, (float *)out,
+                                   Vec<float>::w(v), sweeps, H->p.omega, s);
 }
 
 extern "C" int mg_level_smooth_dot(mg_handle *H, int level, int prec, const void *b,

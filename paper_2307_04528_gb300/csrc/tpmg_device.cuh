@@ -453,42 +453,15 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
 // col < ncol.
 constexpr int kWarpLayers = (kMaxLayers + 31) / 32;  // layers per lane at most
 
-template <typename T, bool ZERO>
-__device__ __forceinline__ void smooth_warp_column(const LevelDev<T> &L, const T *__restrict__ b,
-                                                   const T *uin, T *uout, T omega, int col,
-                                                   int lane)
+// The two scans of the warp sweep over one lane's layers k0 .. k0 + C - 1:
+// v holds the right-hand sides v_k on entry and the column solution x_k of
+// H_z x = v on return; tprev = t_{k0-1} (0 for the first lane).
+template <typename T>
+__device__ __forceinline__ void warp_column_scan(T (&v)[kWarpLayers], const T (&tz)[kWarpLayers],
+                                                 const T (&m)[kWarpLayers],
+                                                 const T (&dq)[kWarpLayers], T tprev, int C,
+                                                 int k0, int nz, int lane)
 {
-    const int nlon = L.nlon, nlat = L.nlat, nz = L.nz;
-    const int j = col / nlon, i = col - j * nlon;
-    const int ie = (i + 1 == nlon) ? col - i : col + 1;
-    const int iw = (i == 0) ? col + nlon - 1 : col - 1;
-    const bool hasN = j + 1 < nlat, hasS = j > 0;
-    const size_t plane = (size_t)nlon * nlat;
-    const int C = (nz + 31) / 32;
-    const int k0 = lane * C;
-    T v[kWarpLayers], tz[kWarpLayers], m[kWarpLayers], dq[kWarpLayers], u0[kWarpLayers];
-#pragma unroll
-    for (int c = 0; c < kWarpLayers; ++c) {
-        const int k = k0 + c;
-        v[c] = tz[c] = m[c] = dq[c] = u0[c] = T(0);
-        if (c < C && k < nz) {
-            const size_t o = (size_t)k * plane;
-            T vv = __ldg(b + o + col);
-            if (!ZERO) {
-                vv = fma(__ldg(L.tx + o + col), uin[o + ie], vv);
-                vv = fma(__ldg(L.tx + o + iw), uin[o + iw], vv);
-                if (hasN) vv = fma(__ldg(L.ty + o + col), uin[o + col + nlon], vv);
-                if (hasS) vv = fma(__ldg(L.ty + o + col - nlon), uin[o + col - nlon], vv);
-                u0[c] = uin[o + col];
-            }
-            v[c] = vv;
-            tz[c] = __ldg(L.tz + o + col);
-            m[c] = __ldg(L.m + o + col);
-            dq[c] = __ldg(L.dq + o + col);
-        }
-    }
-    const T tprev = (k0 >= 1 && k0 - 1 < nz) ? __ldg(L.tz + (size_t)(k0 - 1) * plane + col) : T(0);
-
     // forward: this lane's map y_out = A y_in + Cy, then an inclusive scan
     T A = 1, Cy = 0, tp = tprev;
 #pragma unroll
@@ -542,14 +515,57 @@ __device__ __forceinline__ void smooth_warp_column(const LevelDev<T> &L, const T
     }
     T x = __shfl_down_sync(0xffffffffu, F, 1);
     if (lane == 31) x = T(0);
-    const T om1 = T(1) - omega;
 #pragma unroll
     for (int c = kWarpLayers - 1; c >= 0; --c) {
-        const int k = k0 + c;
-        if (c < C && k < nz) {
+        if (c < C && k0 + c < nz) {
             x = x + fma(-dq[c], x, v[c]);
-            uout[(size_t)k * plane + col] = ZERO ? omega * x : fma(om1, u0[c], omega * x);
+            v[c] = x;  // v now holds x
         }
+    }
+}
+
+template <typename T, bool ZERO>
+__device__ __forceinline__ void smooth_warp_column(const LevelDev<T> &L, const T *__restrict__ b,
+                                                   const T *uin, T *uout, T omega, int col,
+                                                   int lane)
+{
+    const int nlon = L.nlon, nlat = L.nlat, nz = L.nz;
+    const int j = col / nlon, i = col - j * nlon;
+    const int ie = (i + 1 == nlon) ? col - i : col + 1;
+    const int iw = (i == 0) ? col + nlon - 1 : col - 1;
+    const bool hasN = j + 1 < nlat, hasS = j > 0;
+    const size_t plane = (size_t)nlon * nlat;
+    const int C = (nz + 31) / 32;
+    const int k0 = lane * C;
+    T v[kWarpLayers], tz[kWarpLayers], m[kWarpLayers], dq[kWarpLayers], u0[kWarpLayers];
+#pragma unroll
+    for (int c = 0; c < kWarpLayers; ++c) {
+        const int k = k0 + c;
+        v[c] = tz[c] = m[c] = dq[c] = u0[c] = T(0);
+        if (c < C && k < nz) {
+            const size_t o = (size_t)k * plane;
+            T vv = __ldg(b + o + col);
+            if (!ZERO) {
+                vv = fma(__ldg(L.tx + o + col), uin[o + ie], vv);
+                vv = fma(__ldg(L.tx + o + iw), uin[o + iw], vv);
+                if (hasN) vv = fma(__ldg(L.ty + o + col), uin[o + col + nlon], vv);
+                if (hasS) vv = fma(__ldg(L.ty + o + col - nlon), uin[o + col - nlon], vv);
+                u0[c] = uin[o + col];
+            }
+            v[c] = vv;
+            tz[c] = __ldg(L.tz + o + col);
+            m[c] = __ldg(L.m + o + col);
+            dq[c] = __ldg(L.dq + o + col);
+        }
+    }
+    const T tprev = (k0 >= 1 && k0 - 1 < nz) ? __ldg(L.tz + (size_t)(k0 - 1) * plane + col) : T(0);
+    warp_column_scan<T>(v, tz, m, dq, tprev, C, k0, nz, lane);
+    const T om1 = T(1) - omega;
+#pragma unroll
+    for (int c = 0; c < kWarpLayers; ++c) {
+        const int k = k0 + c;
+        if (c < C && k < nz)
+            uout[(size_t)k * plane + col] = ZERO ? omega * v[c] : fma(om1, u0[c], omega * v[c]);
     }
 }
 
@@ -742,74 +758,17 @@ __device__ __forceinline__ void smooth_staged(const LevelDev<T> &L, const T *__r
 // Restriction R = P^T as a gather: coarse (I, J, k) sums, over the fine rows
 // listed for J with their latitude weights, the fine residuals at longitudes
 // 2I-1, 2I, 2I+1, 2I+2 (mod nlon) with weights 1/4, 3/4, 3/4, 1/4.
-// One coarse cell (col, k) of the restriction.
-template <typename T>
-__device__ __forceinline__ void restrict_cell(const LevelDev<T> &F, const LinkDev &K,
-                                              const T *__restrict__ r, T *__restrict__ bc, int col,
-                                              int k)
-{
-    const int nf = F.nlon, nc = nf / 2;
-    const int ncol_c = nc * K.nlat_c;
-    if (col >= ncol_c) return;
-    const int J = col / nc, I = col - J * nc;
-    const int i0 = 2 * I, i1 = 2 * I + 1;
-    const int im = (i0 == 0) ? nf - 1 : i0 - 1;
-    const int ip = (i1 + 1 == nf) ? 0 : i1 + 1;
-    const size_t plane_f = (size_t)nf * F.nlat, plane_c = (size_t)ncol_c;
-    const int p0 = __ldg(K.rptr + J), p1 = __ldg(K.rptr + J + 1);
-    const T q1 = T(0.25), q3 = T(0.75);
-    const T *rk = r + (size_t)k * plane_f;
-    T acc = 0;
-    for (int p = p0; p < p1; ++p) {
-        const T *row = rk + (size_t)__ldg(K.rrow + p) * nf;
-        const T w = (T)__ldg(K.rw + p);
-        acc = fma(w, fma(q1, __ldg(row + im) + __ldg(row + ip), q3 * (__ldg(row + i0) + __ldg(row + i1))),
-                  acc);
-    }
-    bc[(size_t)k * plane_c + col] = acc;
-}
-
 // Bilinear prolongation and correction: fine cell 2I adds
 // sum_a w_a (3/4 e[J_a, I] + 1/4 e[J_a, I-1]) and 2I+1 adds
 // sum_a w_a (3/4 e[J_a, I] + 1/4 e[J_a, I+1]) (periodic in longitude).
-// One pair of fine cells (t = j * nlon/2 + I, layer k) of the prolongation.
-template <typename T>
-__device__ __forceinline__ void prolong_pair(const LevelDev<T> &F, const LinkDev &K,
-                                             const T *__restrict__ ec, T *__restrict__ u, int t,
-                                             int k)
-{
-    const int nf = F.nlon, nc = nf / 2;
-    const int npair = nc * F.nlat;
-    if (t >= npair) return;
-    const int j = t / nc, I = t - j * nc;
-    const int Im = (I == 0) ? nc - 1 : I - 1;
-    const int Ip = (I + 1 == nc) ? 0 : I + 1;
-    const int Ja = __ldg(K.j0 + j), Jb = __ldg(K.j1 + j);
-    const size_t plane_c = (size_t)nc * K.nlat_c;
-    const T q1 = T(0.25), q3 = T(0.75);
-    const T *ek = ec + (size_t)k * plane_c;
-    const T *ea = ek + (size_t)Ja * nc;
-    const T wa = (T)__ldg(K.w0 + j);
-    const T ca = __ldg(ea + I);
-    T a0 = wa * fma(q3, ca, q1 * __ldg(ea + Im));
-    T a1 = wa * fma(q3, ca, q1 * __ldg(ea + Ip));
-    if (Jb >= 0) {
-        const T *eb = ek + (size_t)Jb * nc;
-        const T wb = (T)__ldg(K.w1 + j);
-        const T cb = __ldg(eb + I);
-        a0 = fma(wb, fma(q3, cb, q1 * __ldg(eb + Im)), a0);
-        a1 = fma(wb, fma(q3, cb, q1 * __ldg(eb + Ip)), a1);
-    }
-    T *uk = u + (size_t)k * nf * F.nlat + (size_t)j * nf + 2 * I;
-    uk[0] += a0;
-    uk[1] += a1;
-}
 
 // Layers k0 <= k < k1 of one coarse column of the restriction: the row
-// list of J (at most 4 fine rows for the semi-coarsening row maps) and the
+// list of J (at most kMaxRestrictRows fine rows, checked at setup) and the
 // longitude indices are read once, then every layer issues its loads
-// independently of the others.  Same arithmetic, same order as
-// restrict_cell.
+// independently of the others, one layer per loop trip (unrolling the
+// layer loop costs 8 registers and runs 20-25 % slower at 1536 x 1152 and
+// 768 x 726 columns).  The sum over the row list runs in its (ascending
+// fine-row) order.
 template <typename T>
 __device__ __forceinline__ void restrict_layers(const LevelDev<T> &F, const LinkDev &K,
                                                 const T *__restrict__ r, T *__restrict__ bc,
@@ -823,25 +782,21 @@ __device__ __forceinline__ void restrict_layers(const LevelDev<T> &F, const Link
     const int im = (i0 == 0) ? nf - 1 : i0 - 1;
     const int ip = (i1 + 1 == nf) ? 0 : i1 + 1;
     const int p0 = __ldg(K.rptr + J), cnt = __ldg(K.rptr + J + 1) - p0;
-    if (cnt > 4) {  // general row lists
-        for (int k = k0; k < k1; ++k) restrict_cell<T>(F, K, r, bc, col, k);
-        return;
-    }
     const size_t plane_f = (size_t)nf * F.nlat, plane_c = (size_t)ncol_c;
-    int off[4];
-    T w[4];
+    int off[kMaxRestrictRows];
+    T w[kMaxRestrictRows];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < kMaxRestrictRows; ++a) {
         off[a] = a < cnt ? __ldg(K.rrow + p0 + a) * nf : 0;
         w[a] = a < cnt ? (T)__ldg(K.rw + p0 + a) : T(0);
     }
     const T q1 = T(0.25), q3 = T(0.75);
-#pragma unroll 2
+#pragma unroll 1
     for (int k = k0; k < k1; ++k) {
         const T *rk = r + (size_t)k * plane_f;
         T acc = 0;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < kMaxRestrictRows; ++a) {
             if (a < cnt) {
                 const T *row = rk + off[a];
                 acc = fma(w[a],
@@ -854,8 +809,8 @@ __device__ __forceinline__ void restrict_layers(const LevelDev<T> &F, const Link
     }
 }
 
-// Layers k0 <= k < k1 of one pair of fine columns of the prolongation and
-// correction (row links read once); same arithmetic as prolong_pair.
+// Layers k0 <= k < k1 of one pair of fine columns (t = j * nlon/2 + I) of
+// the prolongation and correction, the row links read once.
 template <typename T>
 __device__ __forceinline__ void prolong_layers(const LevelDev<T> &F, const LinkDev &K,
                                                const T *__restrict__ ec, T *__restrict__ u, int t,

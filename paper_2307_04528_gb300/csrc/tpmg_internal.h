@@ -40,6 +40,7 @@ struct CgScalars {
 
 constexpr int kBlock = 128;          // threads per block, one column per thread
 constexpr int kMaxLayers = 192;      // MG_MAX_NZ of the C ABI (checked in tpmg_api.cpp)
+constexpr int kMaxRestrictRows = 4;  // fine rows per coarse row of the restriction (checked at setup)
 constexpr int kReduceSlots = 65536;  // per-block partial sums kept in the workspace
 
 // ---- launchers (tpmg_kernels.cu); all asynchronous on `s` -----------------

@@ -172,6 +172,14 @@ class MGHandle:
                                          _stream()))
         return out
 
+    def level_relax(self, level, b, sweeps, prec=L.MG_PREC_FP64):
+        """`sweeps` sweeps from the zero guess (on the coarsest level with
+        sweeps = coarse_iters: the V-cycle's coarsest-level solve)."""
+        out = torch.empty_like(b)
+        L.check(self.lib.mg_level_relax(self._hh, level, prec, int(sweeps), _ptr(b), _ptr(out),
+                                        _stream()))
+        return out
+
     def level_smooth_dot(self, level, b, u_in, prec=L.MG_PREC_FP64):
         """One sweep plus <b, u_out> (the V-cycle's last sweep with the CG
         inner product fused in)."""

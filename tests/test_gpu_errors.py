@@ -71,3 +71,9 @@ def test_workspace_and_argument_errors():
     H = handle_for(P, mixed=0)
     _raises(L.MG_ERR_ARG, lambda: H.solve_mixed(dev(P["b"])))
     _raises(L.MG_ERR_ARG, lambda: H.level_smooth(99, dev(P["b"])))
+    _raises(L.MG_ERR_ARG, lambda: H.level_relax(0, dev(P["b"]), 0))
+    _raises(L.MG_ERR_ARG, lambda: H.level_relax(0, dev(P["b"]), 1001))
+    _raises(L.MG_ERR_ARG, lambda: H.level_relax(0, dev(P["b"]), 2, prec=L.MG_PREC_FP32))
+    b = dev(P["b"])
+    assert lib.mg_level_relax(H._hh, 0, 0, 2, ctypes.c_void_p(b.data_ptr()),
+                              ctypes.c_void_p(b.data_ptr()), s) == L.MG_ERR_ARG

@@ -92,6 +92,57 @@ def test_smoother_with_fused_dot(case):
     assert abs(dot - O.dot(b, ref)) <= 1e-5 * O.norm2(b) * O.norm2(ref)
 
 
+def _sweeps_from_zero(ol, b, sweeps, omega):
+    ref = np.zeros_like(b)
+    for _ in range(sweeps):
+        O.smooth(ol, b, ref, omega)
+    return ref
+
+
+def test_relax_and_coarsest_solve(case):
+    """`coarse_iters` sweeps from zero on the coarsest level (the V-cycle's
+    coarsest-level solve: one launch, the level in shared memory in FP32) and
+    on the finest (one launch per sweep), FP64 1e-12 and FP32 2e-5 against
+    the oracle's sweeps repeated (FP32 rounding drift over 8 sweeps measured
+    at ~1e-6 on these shapes)."""
+    P, lev, p, H = case
+    l32 = O.float_levels(lev)
+    rng = np.random.default_rng(13)
+    for l in sorted({0, len(lev) - 1}):
+        b = rng.standard_normal(lev[l].shape)
+        got = host(H.level_relax(l, dev(b), p.coarse_iters))
+        assert rel_inf(got, _sweeps_from_zero(lev[l], b, p.coarse_iters, p.omega)) <= 1e-12
+        b32 = b.astype(np.float32)
+        got = host(H.level_relax(l, dev(b32, torch.float32), p.coarse_iters, prec=1))
+        want = _sweeps_from_zero(l32[l], b32, p.coarse_iters, np.float32(p.omega))
+        assert rel_inf(got, want) <= 2e-5
+    b = rng.standard_normal(lev[-1].shape)
+    one = host(H.level_relax(len(lev) - 1, dev(b), 1))
+    assert rel_inf(one, _sweeps_from_zero(lev[-1], b, 1, p.omega)) <= 1e-13
+    b32 = b.astype(np.float32)
+    for sweeps in (1, 3):
+        got = host(H.level_relax(len(lev) - 1, dev(b32, torch.float32), sweeps, prec=1))
+        want = _sweeps_from_zero(l32[-1], b32, sweeps, np.float32(p.omega))
+        assert rel_inf(got, want) <= 2e-5
+
+
+def test_coarsest_solve_beyond_shared_memory():
+    """A shallow hierarchy whose coarsest level (40 x 30 x 32 cells) exceeds
+    one block's shared memory: the FP32 coarsest-level solve runs from
+    global memory (one block, 32 warps); odd sweep counts end in out."""
+    P = problem(128, 64, 40, sigma=0.2, seed=232)
+    lev, p = oracle_levels(P, levels=3)
+    H = handle_for(P, levels=3)
+    assert H.num_levels == 3 and H.level_shape(2) == (40, 30, 32)
+    l32 = O.float_levels(lev)
+    rng = np.random.default_rng(14)
+    b32 = rng.standard_normal(lev[2].shape).astype(np.float32)
+    for sweeps in (p.coarse_iters, 3):
+        got = host(H.level_relax(2, dev(b32, torch.float32), sweeps, prec=1))
+        want = _sweeps_from_zero(l32[2], b32, sweeps, np.float32(p.omega))
+        assert rel_inf(got, want) <= 2e-5
+
+
 def test_transfers_fp64(case):
     P, lev, p, H = case
     rng = np.random.default_rng(3)

@@ -295,6 +295,23 @@ def test_row_maps_properties():
             assert np.all(alpha >= p.alpha_c)
 
 
+@pytest.mark.parametrize("alpha_c", [0.3, 0.5, 0.6, 0.9])
+def test_restriction_gathers_at_most_four_fine_rows(alpha_c):
+    """R = P^T in latitude: a coarse row collects its one or two children
+    and, from each neighbouring merged pair, only the child nearer to it (a
+    single child sits at its parent's centre and interpolates nowhere) --
+    at most 4 fine rows, the bound the GPU restriction is built for."""
+    P = make_problem(256, 192, 2, 0.1, 0)
+    lev, _ = levels_of(P, alpha_c=alpha_c)
+    for f in lev[:-1]:
+        j0, w0, j1, w1 = f.links()
+        gathered = np.bincount(j0, minlength=f.nlat_c) + np.bincount(j1[j1 >= 0],
+                                                                     minlength=f.nlat_c)
+        assert gathered.max() <= 4
+        single = np.bincount(f.row_of, minlength=f.nlat_c)[f.row_of] == 1
+        assert np.all(j1[single] == -1)      # a lone child interpolates nowhere
+
+
 def test_coarse_operator_conserves_volume_and_stays_spd():
     P = small(nlon=16, nlat=8, nz=3)
     lev, _ = levels_of(P, levels=3)
