@@ -173,7 +173,7 @@ KERNEL_WORDS = {
     # (kind, prec): (name, words per cell)
     (0, 1): ("smooth fp32 (+ <r, z>)", 8),            # u b tx ty tz m dq -> u
     (1, 1): ("smooth fp32 zero guess", 5),            # b tz m dq -> u
-    (2, 1): ("residual fp32", 7),                     # u b tx ty tz h -> r
+    (2, 1): ("residual + restriction fp32", 6),       # u b tx ty tz h -> b_c (+ coarse write)
     (3, 1): ("direction update + apply fp32", 8),     # z d tx ty tz h -> d q
     (0, 0): ("smooth fp64", 8),                       # u b tx ty tz m dq -> u
     (1, 0): ("smooth fp64 zero guess", 5),
@@ -189,10 +189,14 @@ SMOOTH_DOT_DRAM_BYTES_PER_CELL = (397.266944e6 + 34.799616e6) / (512 * 384 * 70)
 
 def kernel_table(H, L, N):
     rows = []
+    c = H.level_shape(1) if H.num_levels > 1 else (0, 0, 0)
+    coarse_ratio = c[0] * c[1] * c[2] / N  # level-1 cells per fine cell
     for (kind, prec), (name, words) in KERNEL_WORDS.items():
         n, ms = H.profile_read(kind, 0, prec)
         if n == 0:
             continue
+        if (kind, prec) == (2, 1):
+            words = words + coarse_ratio
         avg = ms / n
         nbytes = words * (4 if prec == 1 else 8) * N
         rows.append({"kernel": name, "launches": n, "avg_ms": round(avg, 4),

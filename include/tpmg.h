@@ -164,6 +164,15 @@ int mg_level_apply(mg_handle *h, int level, int prec, const void *x, void *y, vo
 int mg_level_residual(mg_handle *h, int level, int prec, const void *b, const void *u,
                       void *r, void *stream);
 
+/* bc = R_l (b - H_l u): the residual restricted to level l+1 in one pass,
+ * the residual itself never stored (the FP32 V-cycle's form; equal term for
+ * term to mg_level_residual followed by mg_level_restrict).  b, u: level l;
+ * bc: level l+1, aliasing neither.  Buffers not aligned to two values take
+ * the two passes through the handle's level-l residual vector (calls on one
+ * handle must not overlap).  MG_ERR_ARG on the coarsest level. */
+int mg_level_residual_restrict(mg_handle *h, int level, int prec, const void *b, const void *u,
+                               void *bc, void *stream);
+
 /* One smoother sweep of Eq. (1) on level l:
  *   u_out = u_in + omega H_z^{-1} (b - H u_in), evaluated as
  *   (1 - omega) u_in + omega H_z^{-1} (b - dH u_in).

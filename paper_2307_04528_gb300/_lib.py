@@ -87,6 +87,7 @@ def load() -> ctypes.CDLL:
         "mg_level_smooth": (I, [H, I, I, P, P, P, P]),
         "mg_level_smooth_dot": (I, [H, I, I, P, P, P, ctypes.POINTER(D), P]),
         "mg_level_relax": (I, [H, I, I, I, P, P, P]),
+        "mg_level_residual_restrict": (I, [H, I, I, P, P, P, P]),
         "mg_level_restrict": (I, [H, I, I, P, P, P]),
         "mg_level_prolong_add": (I, [H, I, I, P, P, P]),
         "mg_fp32_scale": (D, [H]),

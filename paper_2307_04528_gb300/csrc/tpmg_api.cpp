@@ -593,9 +593,15 @@ static int vcycle_level(mg_handle *H, int l, const T *b, T *out, T *scratch, T *
         KRUN(K_SMOOTH, l, P, launch_smooth<T>(D, b, cur, oth, om, s));
         std::swap(cur, oth);
     }
-    KRUN(K_RESID, l, P, launch_stencil<T>(D, 1, b, cur, rbuf, nullptr, s));
     LevelHost &c = H->lev[l + 1];
-    KRUN(K_RESTRICT, l, P, launch_restrict<T>(D, v.linkdev, rbuf, Vec<T>::b(c), s));
+    if (sizeof(T) == 4 && resid_restrict_fits(b, cur, sizeof(T))) {
+        // FP32: one pass, the residual never stored (the FP64 stencil is
+        // bound by FP64 arithmetic, which the fused pass would increase)
+        KRUN(K_RESID, l, P, launch_resid_restrict<T>(D, v.linkdev, b, cur, Vec<T>::b(c), s));
+    } else {
+        KRUN(K_RESID, l, P, launch_stencil<T>(D, 1, b, cur, rbuf, nullptr, s));
+        KRUN(K_RESTRICT, l, P, launch_restrict<T>(D, v.linkdev, rbuf, Vec<T>::b(c), s));
+    }
     CHK(vcycle_level<T>(H, l + 1, Vec<T>::b(c), Vec<T>::u(c), Vec<T>::w(c), Vec<T>::r(c), s));
     KRUN(K_PROLONG, l, P, launch_prolong_add<T>(D, v.linkdev, Vec<T>::u(c), cur, s));
     for (int it = 0; it < H->p.nu2; ++it) {
@@ -1035,6 +1041,34 @@ extern "C" int mg_level_prolong_add(mg_handle *H, int level, int prec, const voi
                                     void *stream)
 {
     return level_dispatch(H, level, prec, 4, ec, nullptr, u, stream);
+}
+
+extern "C" int mg_level_residual_restrict(mg_handle *H, int level, int prec, const void *b,
+                                          const void *u, void *bc, void *stream)
+{
+    CHK(level_check(H, level, prec, true));
+    if (!b || !u || !bc || bc == b || bc == u) return fail(MG_ERR_ARG, "bad buffers");
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelHost &v = H->lev[level];
+    const size_t vb = prec == MG_PREC_FP64 ? 8 : 4;
+    if (resid_restrict_fits(b, u, vb)) {
+        if (prec == MG_PREC_FP64)
+            KRUN(K_RESID, level, 0,
+                 launch_resid_restrict<double>(dev<double>(v), v.linkdev, (const double *)b,
+                                               (const double *)u, (double *)bc, s));
+        else
+            KRUN(K_RESID, level, 1,
+                 launch_resid_restrict<float>(dev<float>(v), v.linkdev, (const float *)b,
+                                              (const float *)u, (float *)bc, s));
+        return MG_OK;
+    }
+    // unaligned buffers: the two passes through the level's residual vector
+    if (prec == MG_PREC_FP64) {
+        CHK(level_op<double>(H, level, 1, b, u, Vec<double>::r(v), s));
+        return level_op<double>(H, level, 3, Vec<double>::r(v), nullptr, bc, s);
+    }
+    CHK(level_op<float>(H, level, 1, b, u, Vec<float>::r(v), s));
+    return level_op<float>(H, level, 3, Vec<float>::r(v), nullptr, bc, s);
 }
 
 extern "C" int mg_level_relax(mg_handle *H, int level, int prec, int sweeps, const void *b,

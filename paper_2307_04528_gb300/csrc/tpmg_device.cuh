@@ -848,4 +848,147 @@ __device__ __forceinline__ void prolong_layers(const LevelDev<T> &F, const LinkD
     }
 }
 
+// ------------------------------------------------------------------ residual + restriction
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+    using type = float2;
+};
+template <>
+struct Pair<double> {
+    using type = double2;
+};
+
+template <typename T>
+__device__ __forceinline__ typename Pair<T>::type ld_pair(const T *p)
+{
+    return __ldg(reinterpret_cast<const typename Pair<T>::type *>(p));
+}
+
+// Coarse rows per band and owned coarse columns per warp of the fused
+// residual + restriction.
+constexpr int kRRBand = 8;
+constexpr int kRROwned = 30;
+
+// b_c = R (b - H u) on one layer k, for a band of kRRBand coarse rows
+// [Jb, Je) and one coarse column per lane: lanes 1..30 of a warp own coarse
+// columns 30 w .. 30 w + 29 (w: the warp's index along longitude), lanes 0
+// and 31 carry the neighbouring columns (periodic).  A lane walks the fine
+// rows of the band's gather lists northward and, per row, forms
+//   * the residual of its fine columns 2I and 2I+1: the stencil of
+//     stencil_column with the same operations in the same order, the outer
+//     east/west values and the west face coupling taken from the adjacent
+//     lanes;
+//   * the longitude sum of the restriction, 1/4 r[2I-1] + 3/4 (r[2I] +
+//     r[2I+1]) + 1/4 r[2I+2], the outer residuals from the adjacent lanes;
+//   * its latitude contributions w0 (row j0) and w1 (row j1) of the
+//     prolongation links (R = P^T) to the at most three coarse rows still
+//     open, storing a coarse row once its last listed fine row has passed.
+// Each coarse value is the sum restrict_layers forms over the residual
+// stencil_column writes, term for term and in the same order, so the result
+// equals the two kernels' exactly; the residual never reaches memory.  The
+// fine rows shared by two bands are computed in both.  All 32 lanes of the
+// warp call it (whole warps past the last column return together); b, u and
+// the coefficient arrays aligned to two values.
+template <typename T>
+__device__ __forceinline__ void resid_restrict_band(const LevelDev<T> &F, const LinkDev &K,
+                                                    const T *__restrict__ b,
+                                                    const T *__restrict__ u, T *__restrict__ bc,
+                                                    int warp, int lane, int Jb, int k)
+{
+    using P2 = typename Pair<T>::type;
+    constexpr unsigned kAll = 0xffffffffu;
+    const int nf = F.nlon, nc = nf / 2, nlat = F.nlat, nz = F.nz, ncJ = K.nlat_c;
+    const int Iown = warp * kRROwned + lane - 1;
+    const bool owned = lane >= 1 && lane <= kRROwned && Iown < nc;
+    int I = Iown < 0 ? Iown + nc : (Iown >= nc ? Iown - nc : Iown);
+    if (I >= nc) I = nc - 1;  // past the east neighbour of the last column: unused
+    const int Je = min(ncJ, Jb + kRRBand);
+    const size_t plane = (size_t)nf * nlat, plane_c = (size_t)nc * ncJ;
+    const size_t o = (size_t)k * plane + 2 * I;
+    const bool up = k + 1 < nz, dn = k > 0;
+    const T *uk = u + o, *bk = b + o, *hk = F.h + o, *txk = F.tx + o, *tyk = F.ty + o;
+    const T *tzk = F.tz + o;
+    const T *uu = up ? uk + plane : uk, *ud = dn ? uk - plane : uk, *tzd = dn ? tzk - plane : tzk;
+    T *out = bc + (size_t)k * plane_c + (owned ? Iown : 0);
+    const int jfirst = __ldg(K.rrow + __ldg(K.rptr + Jb));
+    const int jlast = __ldg(K.rrow + __ldg(K.rptr + Je) - 1);
+    const T q1 = T(0.25), q3 = T(0.75);
+    int Jlo = Jb;                                          // lowest open coarse row
+    int lastlo = __ldg(K.rrow + __ldg(K.rptr + Jlo + 1) - 1);  // its last fine row
+    T a0 = 0, a1 = 0, a2 = 0;                              // rows Jlo, Jlo + 1, Jlo + 2
+    P2 zero;
+    zero.x = zero.y = T(0);
+    P2 Us = jfirst > 0 ? ld_pair(uk + (size_t)(jfirst - 1) * nf) : zero;
+    P2 Tys = jfirst > 0 ? ld_pair(tyk + (size_t)(jfirst - 1) * nf) : zero;
+    P2 Uc = ld_pair(uk + (size_t)jfirst * nf);
+#pragma unroll 1
+    for (int j = jfirst; j <= jlast; ++j) {
+        const bool hasN = j + 1 < nlat, hasS = j > 0;
+        const size_t oj = (size_t)j * nf;
+        const P2 Un = hasN ? ld_pair(uk + oj + nf) : zero;
+        const P2 B = ld_pair(bk + oj), Hh = ld_pair(hk + oj), TX = ld_pair(txk + oj);
+        const P2 TYN = hasN ? ld_pair(tyk + oj) : zero;
+        const P2 TZ = ld_pair(tzk + oj);
+        const P2 TZD = dn ? ld_pair(tzd + oj) : zero;
+        const P2 UU = up ? ld_pair(uu + oj) : zero;
+        const P2 UD = dn ? ld_pair(ud + oj) : zero;
+        const T uw = __shfl_up_sync(kAll, Uc.y, 1);    // u[2I-1]
+        const T ue = __shfl_down_sync(kAll, Uc.x, 1);  // u[2I+2]
+        const T txw = __shfl_up_sync(kAll, TX.y, 1);   // t_x[2I-1], west face of 2I
+        T v0 = Hh.x * Uc.x;
+        v0 = fma(TX.x, Uc.x - Uc.y, v0);
+        v0 = fma(txw, Uc.x - uw, v0);
+        if (hasN) v0 = fma(TYN.x, Uc.x - Un.x, v0);
+        if (hasS) v0 = fma(Tys.x, Uc.x - Us.x, v0);
+        v0 = fma(TZ.x, Uc.x - UU.x, v0);
+        v0 = fma(TZD.x, Uc.x - UD.x, v0);
+        T v1 = Hh.y * Uc.y;
+        v1 = fma(TX.y, Uc.y - ue, v1);
+        v1 = fma(TX.x, Uc.y - Uc.x, v1);
+        if (hasN) v1 = fma(TYN.y, Uc.y - Un.y, v1);
+        if (hasS) v1 = fma(Tys.y, Uc.y - Us.y, v1);
+        v1 = fma(TZ.y, Uc.y - UU.y, v1);
+        v1 = fma(TZD.y, Uc.y - UD.y, v1);
+        const T r0 = B.x - v0, r1 = B.y - v1;
+        const T rw = __shfl_up_sync(kAll, r1, 1);    // r[2I-1]
+        const T re = __shfl_down_sync(kAll, r0, 1);  // r[2I+2]
+        const T sv = fma(q1, rw + re, q3 * (r0 + r1));
+        while (j > lastlo) {  // Jlo has all its rows
+            if (owned) out[(size_t)Jlo * nc] = a0;
+            a0 = a1;
+            a1 = a2;
+            a2 = T(0);
+            ++Jlo;
+            lastlo = Jlo < Je ? __ldg(K.rrow + __ldg(K.rptr + Jlo + 1) - 1) : 0x7fffffff;
+        }
+        const int J0 = __ldg(K.j0 + j), J1 = __ldg(K.j1 + j);
+        if (J0 >= Jb && J0 < Je) {
+            const T w = (T)__ldg(K.w0 + j);
+            const int d = J0 - Jlo;
+            if (d == 0) a0 = fma(w, sv, a0);
+            else if (d == 1) a1 = fma(w, sv, a1);
+            else a2 = fma(w, sv, a2);
+        }
+        if (J1 >= Jb && J1 < Je) {
+            const T w = (T)__ldg(K.w1 + j);
+            const int d = J1 - Jlo;
+            if (d == 0) a0 = fma(w, sv, a0);
+            else if (d == 1) a1 = fma(w, sv, a1);
+            else a2 = fma(w, sv, a2);
+        }
+        Us = Uc;
+        Uc = Un;
+        Tys = TYN;
+    }
+    while (Jlo < Je) {
+        if (owned) out[(size_t)Jlo * nc] = a0;
+        a0 = a1;
+        a1 = a2;
+        a2 = T(0);
+        ++Jlo;
+    }
+}
+
 }  // namespace tpmg

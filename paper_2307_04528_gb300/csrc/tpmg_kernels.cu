@@ -435,6 +435,36 @@ k_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ r, T *__restrict__ bc
                        min(F.nz, k0 + kz));
 }
 
+// Residual and restriction fused (resid_restrict_band): grid x = warps of
+// kRROwned coarse columns, y = bands of kRRBand coarse rows, z = layers.
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_resid_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ b, const T *__restrict__ u,
+                 T *__restrict__ bc, const int *__restrict__ flag)
+{
+    if (flag && !*flag) return;
+    const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (warp * kRROwned >= F.nlon / 2) return;  // whole warps
+    resid_restrict_band<T>(F, K, b, u, bc, warp, threadIdx.x & 31, blockIdx.y * kRRBand,
+                           blockIdx.z);
+}
+
+bool resid_restrict_fits(const void *b, const void *u, size_t value_bytes)
+{
+    return (uintptr_t)b % (2 * value_bytes) == 0 && (uintptr_t)u % (2 * value_bytes) == 0;
+}
+
+template <typename T>
+cudaError_t launch_resid_restrict(const LevelDev<T> &F, const LinkDev &K, const T *b, const T *u,
+                                  T *bc, cudaStream_t s, const int *flag)
+{
+    const int nc = F.nlon / 2;
+    const int warps = (nc + kRROwned - 1) / kRROwned;
+    const dim3 grid((warps * 32 + kBlock - 1) / kBlock, (K.nlat_c + kRRBand - 1) / kRRBand, F.nz);
+    k_resid_restrict<T><<<grid, kBlock, 0, s>>>(F, K, b, u, bc, flag);
+    return cudaGetLastError();
+}
+
 // Layers per thread of the cell-parallel transfers: enough column-layer
 // blocks for two waves of 16 blocks on every SM, and at most 16 layers.
 
@@ -838,6 +868,8 @@ cudaError_t launch_coeff_grad(int nlon, int nlat, int nz, const double *lam, con
                                           cudaStream_t, const int *);                             \
     template int launch_smooth_dot<T>(const LevelDev<T> &, const T *, const T *, T *, double,      \
                                       double *, cudaStream_t, const int *);                       \
+    template cudaError_t launch_resid_restrict<T>(const LevelDev<T> &, const LinkDev &, const T *, \
+                                                  const T *, T *, cudaStream_t, const int *);     \
     template cudaError_t launch_restrict<T>(const LevelDev<T> &, const LinkDev &, const T *, T *,  \
                                             cudaStream_t, const int *);                           \
     template cudaError_t launch_prolong_add<T>(const LevelDev<T> &, const LinkDev &, const T *,    \

@@ -172,6 +172,14 @@ class MGHandle:
                                          _stream()))
         return out
 
+    def level_residual_restrict(self, level, b, u, prec=L.MG_PREC_FP64):
+        """R (b - H u) on level -> level + 1 in one pass."""
+        shp = self.level_shape(level + 1)
+        bc = torch.empty(shp, dtype=b.dtype, device=b.device)
+        L.check(self.lib.mg_level_residual_restrict(self._hh, level, prec, _ptr(b), _ptr(u),
+                                                    _ptr(bc), _stream()))
+        return bc
+
     def level_relax(self, level, b, sweeps, prec=L.MG_PREC_FP64):
         """`sweeps` sweeps from the zero guess (on the coarsest level with
         sweeps = coarse_iters: the V-cycle's coarsest-level solve)."""

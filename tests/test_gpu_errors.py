@@ -77,3 +77,11 @@ def test_workspace_and_argument_errors():
     b = dev(P["b"])
     assert lib.mg_level_relax(H._hh, 0, 0, 2, ctypes.c_void_p(b.data_ptr()),
                               ctypes.c_void_p(b.data_ptr()), s) == L.MG_ERR_ARG
+    last = H.num_levels - 1
+    u, bc = torch.zeros_like(b), torch.zeros_like(b)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    assert lib.mg_level_residual_restrict(H._hh, last, 0, ptr(b), ptr(u), ptr(bc), s) == L.MG_ERR_ARG
+    assert lib.mg_level_residual_restrict(H._hh, 0, 0, ptr(b), ptr(u), ptr(u), s) == L.MG_ERR_ARG
+    assert lib.mg_level_residual_restrict(H._hh, 0, 0, ctypes.c_void_p(b.data_ptr()),
+                                          ctypes.c_void_p(b.data_ptr()),
+                                          ctypes.c_void_p(b.data_ptr()), s) == L.MG_ERR_ARG

@@ -89,6 +89,11 @@ def test_fine_level_kernels_fp32(full):
     ref = x.copy()
     O.prolong_add(f, e, ref)
     assert rel_inf(host(H.level_prolong_add(0, f32(e), f32(x), prec=1)), ref) <= 2e-5
+    # the V-cycle's fused residual + restriction
+    got = H.level_residual_restrict(0, f32(b), f32(x), prec=1)
+    assert rel_inf(host(got), O.restrict(f, O.residual(f, b, x))) <= 2e-5
+    two = H.level_restrict(0, H.level_residual(0, f32(b), f32(x), prec=1), prec=1)
+    assert torch.equal(got, two)
 
 
 def test_vcycle_fp64(full):

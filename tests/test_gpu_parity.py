@@ -143,6 +143,33 @@ def test_coarsest_solve_beyond_shared_memory():
         assert rel_inf(got, want) <= 2e-5
 
 
+def test_residual_restrict_fused(case):
+    """R (b - H u) in one pass on every level: against the oracle's residual
+    then restriction (FP64 1e-13, FP32 2e-5), and equal to the library's own
+    two passes exactly (the same operations in the same order).  A buffer
+    one value off alignment takes the two-pass path."""
+    P, lev, p, H = case
+    l32 = O.float_levels(lev)
+    rng = np.random.default_rng(15)
+    for l in range(len(lev) - 1):
+        b = rng.standard_normal(lev[l].shape)
+        u = rng.standard_normal(lev[l].shape)
+        got = host(H.level_residual_restrict(l, dev(b), dev(u)))
+        assert rel_inf(got, O.restrict(lev[l], O.residual(lev[l], b, u))) <= 1e-13
+        b32, u32 = dev(b, torch.float32), dev(u, torch.float32)
+        got = H.level_residual_restrict(l, b32, u32, prec=1)
+        want = O.restrict(l32[l], O.residual(l32[l], host(b32), host(u32)))
+        assert rel_inf(host(got), want) <= 2e-5
+        two = H.level_restrict(l, H.level_residual(l, b32, u32, prec=1), prec=1)
+        assert torch.equal(got, two)
+    buf = torch.empty(lev[0].size + 1, dtype=torch.float32, device="cuda")
+    b_odd = buf[1:].view(lev[0].shape)
+    b_odd.copy_(dev(rng.standard_normal(lev[0].shape), torch.float32))
+    u32 = dev(rng.standard_normal(lev[0].shape), torch.float32)
+    got = H.level_residual_restrict(0, b_odd, u32, prec=1)
+    assert torch.equal(got, H.level_restrict(0, H.level_residual(0, b_odd, u32, prec=1), prec=1))
+
+
 def test_transfers_fp64(case):
     P, lev, p, H = case
     rng = np.random.default_rng(3)
