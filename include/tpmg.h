@@ -73,7 +73,7 @@ typedef struct {
     int levels;        /* 0: coarsen down to the coarsest level (nlon >= 4 there);
                           4 is the shallow hierarchy of Section 2.3 */
     int nu1, nu2;      /* pre/post smoothing sweeps (V(1,1) default) */
-    int coarse_iters;  /* block-Jacobi sweeps on the coarsest level (8) */
+    int coarse_iters;  /* block-Jacobi sweeps on the coarsest level (12) */
     int method;        /* MG_METHOD_CG (V-cycle-preconditioned CG, default) or
                           MG_METHOD_STATIONARY (x <- x + V(b - H x), Section 2) */
     int mixed;         /* 1: also build the FP32 hierarchy for mg_solve_mixed */

@@ -69,7 +69,8 @@ class MGParams:
     nu1: int = 1               # pre-smoothing sweeps, V(1,1)
     nu2: int = 1               # post-smoothing sweeps
     omega: float = 0.85        # Eq. (1) relaxation factor (value not printed; tuned)
-    coarse_iters: int = 8      # Section 2.3's "simple iterative method": block-Jacobi sweeps
+    coarse_iters: int = 12     # Section 2.3's simple coarsest-grid iteration: block-Jacobi sweeps
+    #                            (count not printed; measured)
     alpha_c: float = 0.6       # Section 2.2 anisotropy threshold (value not printed; tuned)
     method: str = "cg"         # outer iteration: "cg" (V-cycle-preconditioned CG) or "stationary"
     maxit: int = 200

@@ -290,7 +290,7 @@ extern "C" void mg_default_params(mg_params *p)
     p->levels = 0;
     p->nu1 = 1;
     p->nu2 = 1;
-    p->coarse_iters = 8;
+    p->coarse_iters = 12;
     p->method = MG_METHOD_CG;
     p->mixed = 0;
     p->maxit = 200;

@@ -101,6 +101,27 @@ cudaError_t launch_bsmooth_dot(const BOp<T> *ops, const BItem *items, int nitems
     return cudaGetLastError();
 }
 
+// One system's coarsest-level solve per block (coarse_solve_sh).
+template <typename T>
+__global__ void __launch_bounds__(kCoarseSolveThreads)
+k_bcoarse_solve(const BOp<T> *__restrict__ ops, T omega, int sweeps,
+                const int *__restrict__ active)
+{
+    const BOp<T> &op = ops[blockIdx.x];
+    if (active && !active[op.sys]) return;
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    coarse_solve_sh<T>(op.L, op.a, op.y, omega, sweeps, reinterpret_cast<T *>(sh_raw));
+}
+
+template <typename T>
+cudaError_t launch_bcoarse_solve(const BOp<T> *ops, int nops, double omega, int sweeps,
+                                 const int *active, size_t smem, cudaStream_t s)
+{
+    if (nops <= 0) return cudaSuccess;
+    k_bcoarse_solve<T><<<nops, kCoarseSolveThreads, smem, s>>>(ops, (T)omega, sweeps, active);
+    return cudaGetLastError();
+}
+
 cudaError_t bsmooth_prepare()
 {
     cudaError_t e;
@@ -111,7 +132,8 @@ cudaError_t bsmooth_prepare()
         return e;
     const void *kernels[] = {(const void *)k_bsmooth<double, true>, (const void *)k_bsmooth<double, false>,
                              (const void *)k_bsmooth<float, true>, (const void *)k_bsmooth<float, false>,
-                             (const void *)k_bsmooth_dot<double>, (const void *)k_bsmooth_dot<float>};
+                             (const void *)k_bsmooth_dot<double>, (const void *)k_bsmooth_dot<float>,
+                             (const void *)k_bcoarse_solve<double>, (const void *)k_bcoarse_solve<float>};
     for (const void *k : kernels)
         if ((e = set_dynamic_smem_limit(k, lim)) != cudaSuccess) return e;
     return cudaSuccess;
@@ -404,6 +426,8 @@ cudaError_t launch_bfinalize(const double *partial, const int *beg, const int *e
 }
 
 #define TPMG_BINST(T)                                                                           \
+    template cudaError_t launch_bcoarse_solve<T>(const BOp<T> *, int, double, int, const int *,  \
+                                                 size_t, cudaStream_t);                          \
     template cudaError_t launch_bsmooth<T>(const BOp<T> *, const BItem *, int, bool, double,      \
                                            const int *, int, int, int, cudaStream_t);             \
     template cudaError_t launch_bsmooth_dot<T>(const BOp<T> *, const BItem *, int, double,        \

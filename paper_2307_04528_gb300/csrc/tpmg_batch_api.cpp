@@ -31,7 +31,7 @@ using namespace tpmg;
 namespace {
 
 enum { BK_SMOOTH0 = 0, BK_SMOOTH = 1, BK_RESID = 2, BK_RESTRICT = 3, BK_PROLONG = 4,
-       BK_SMOOTH_DOT = 5, BK_KINDS = 6 };
+       BK_SMOOTH_DOT = 5, BK_RESID_RESTRICT = 6, BK_COARSE = 7, BK_KINDS = 8 };
 
 template <typename T>
 struct StepHost {
@@ -157,6 +157,12 @@ struct SysOp {
     BOp<T> op;
 };
 
+// Levels with at least this many columns run the single-system kernels, one
+// launch per operator (their own grid fills the GPU, and their kernel
+// parameters live in the constant bank instead of registers); the smaller
+// ones share the persistent work-list launch.
+constexpr long long kBigColumns = 1LL << 18;
+
 // Layers per work item of the cell-type steps: the residual walks whole
 // columns where a level has enough of them (as the single-system path), and
 // the transfers take up to 16 layers per thread on large levels.
@@ -199,6 +205,11 @@ void gen_level(mg_handle *H, int sys, int l, int Lmax, const T *b, T *out, T *sc
     const int down = l, up = 2 * Lmax - 2 - l;
     if (l == H->L - 1) {
         const int sweeps = H->p.coarse_iters;
+        if (sizeof(T) == 4 && coarse_sh_fits(D.nlon * D.nlat, D.nz, sizeof(T))) {
+            // all sweeps in one block per system, the level in shared memory
+            push(down, BK_COARSE, b, nullptr, out, D, nolink);
+            return;
+        }
         T *cur = (sweeps % 2 == 1) ? out : scratch;
         T *oth = (cur == out) ? scratch : out;
         push(down, BK_SMOOTH0, b, nullptr, cur, D, nolink);
@@ -217,8 +228,14 @@ void gen_level(mg_handle *H, int sys, int l, int Lmax, const T *b, T *out, T *sc
         std::swap(cur, oth);
     }
     LevelHost &c = H->lev[l + 1];
-    push(down, BK_RESID, b, cur, rbuf, D, nolink);
-    push(down, BK_RESTRICT, rbuf, nullptr, Vec<T>::b(c), D, v.linkdev);
+    if (sizeof(T) == 4 && (long long)D.nlon * D.nlat >= kBigColumns &&
+        resid_restrict_fits(b, cur, sizeof(T))) {
+        // a large FP32 level: the single-system fused pass
+        push(down, BK_RESID_RESTRICT, b, cur, Vec<T>::b(c), D, v.linkdev);
+    } else {
+        push(down, BK_RESID, b, cur, rbuf, D, nolink);
+        push(down, BK_RESTRICT, rbuf, nullptr, Vec<T>::b(c), D, v.linkdev);
+    }
     gen_level<T>(H, sys, l + 1, Lmax, Vec<T>::b(c), Vec<T>::u(c), Vec<T>::w(c), Vec<T>::r(c),
                  phases, nsys);
     push(up, BK_PROLONG, Vec<T>::u(c), nullptr, cur, D, v.linkdev);
@@ -252,17 +269,16 @@ int tiles_of(int kind, const BOp<T> &op, int block, int *nblk)
     case BK_RESTRICT:
         *nblk = cdiv((long long)(op.L.nlon / 2) * op.K.nlat_c, kBlock);
         return *nblk * cdiv(op.L.nz, op.kz);
+    case BK_RESID_RESTRICT:  // large levels only, launched on their own
+    case BK_COARSE:          // one block per system, launched on its own
+        *nblk = 0;
+        return 0;
     default:
         *nblk = cdiv((long long)(op.L.nlon / 2) * op.L.nlat, kBlock);
         return *nblk * cdiv(op.L.nz, op.kz);
     }
 }
 
-// Levels with at least this many columns run the single-system kernels, one
-// launch per operator (their own grid fills the GPU, and their kernel
-// parameters live in the constant bank instead of registers); the smaller
-// ones share the persistent work-list launch.
-constexpr long long kBigColumns = 1LL << 18;
 
 template <typename T>
 bool is_big(const BOp<T> &op)
@@ -690,6 +706,17 @@ static int run_vstep(mg_batch *B, StepHost<T> &st, cudaStream_t s)
                                   B->smooth_block, B->nzmax, B->partial, s);
         break;
     }
+    case BK_RESID_RESTRICT:  // large levels only: no work-list items
+        break;
+    case BK_COARSE: {
+        size_t smem = 0;
+        for (const BOp<T> &op : st.ops)
+            smem = std::max(smem, coarse_sh_bytes(op.L.nlon * op.L.nlat, op.L.nz, sizeof(T)));
+        e = launch_bcoarse_solve<T>(st.ops_dev, (int)st.ops.size(), B->p.omega,
+                                    B->p.coarse_iters, B->active, smem, s);
+        if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+        break;
+    }
     default: {
         // as many blocks as the GPU holds (the launcher clamps to occupancy)
         const int grid = ni;
@@ -715,6 +742,9 @@ static int run_vstep(mg_batch *B, StepHost<T> &st, cudaStream_t s)
             e = cudaGetLastError();
             break;
         case BK_RESTRICT: e = launch_restrict<T>(op.L, op.K, op.a, op.y, s, flag); break;
+        case BK_RESID_RESTRICT:
+            e = launch_resid_restrict<T>(op.L, op.K, op.a, op.x, op.y, s, flag);
+            break;
         default: e = launch_prolong_add<T>(op.L, op.K, op.a, op.y, s, flag); break;
         }
         if (e != cudaSuccess) return fail(MG_ERR_CUDA, "batched step: %s", cudaGetErrorString(e));

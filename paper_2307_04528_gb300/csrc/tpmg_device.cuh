@@ -569,6 +569,87 @@ __device__ __forceinline__ void smooth_warp_column(const LevelDev<T> &L, const T
     }
 }
 
+// The coarsest-level solve (sweeps of Eq. (1) from zero) by one block with
+// the whole level in shared memory: b, t_z, 1/p, q/p,
+// t_x, t_y and the two sweep vectors, each stored as [column][layer], so a
+// lane's own layers are consecutive words (bank-conflict free for an odd
+// layers-per-lane count).  The level is staged once from its [layer][column]
+// arrays and the result written back once; the sweeps in between touch no
+// global memory.  Same arithmetic, same order as the sweeps from global
+// memory (smooth_warp_column).  Called by every thread of the block; sh:
+// kCoarseShArrays * ncol * nz values of dynamic shared memory.
+constexpr int kCoarseShArrays = 8;
+
+template <typename T>
+__device__ __forceinline__ void coarse_solve_sh(const LevelDev<T> &L, const T *__restrict__ b,
+                                                T *__restrict__ out, T omega, int sweeps, T *sh)
+{
+    const int nlon = L.nlon, nlat = L.nlat, nz = L.nz;
+    const int ncol = nlon * nlat, n = ncol * nz;
+    T *sb = sh, *stz = sh + n, *sm = sh + 2 * n, *sdq = sh + 3 * n, *stx = sh + 4 * n,
+      *sty = sh + 5 * n;
+    T *cur = sh + 6 * n, *oth = sh + 7 * n;
+    for (int g = threadIdx.x; g < n; g += blockDim.x) {
+        const int k = g / ncol, c = g - k * ncol, o = c * nz + k;
+        sb[o] = __ldg(b + g);
+        stz[o] = __ldg(L.tz + g);
+        sm[o] = __ldg(L.m + g);
+        sdq[o] = __ldg(L.dq + g);
+        stx[o] = __ldg(L.tx + g);
+        sty[o] = __ldg(L.ty + g);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int C = (nz + 31) / 32, k0 = lane * C;
+    const T om1 = T(1) - omega;
+    for (int it = 0; it < sweeps; ++it) {
+        for (int col = warp; col < ncol; col += nw) {
+            const int j = col / nlon, i = col - j * nlon;
+            const int ie = (i + 1 == nlon) ? col - i : col + 1;
+            const int iw = (i == 0) ? col + nlon - 1 : col - 1;
+            const bool hasN = j + 1 < nlat, hasS = j > 0;
+            const int oc = col * nz, oe = ie * nz, ow = iw * nz;
+            const int on = (col + nlon) * nz, os = (col - nlon) * nz;
+            T v[kWarpLayers], tz[kWarpLayers], m[kWarpLayers], dq[kWarpLayers], u0[kWarpLayers];
+#pragma unroll
+            for (int c = 0; c < kWarpLayers; ++c) {
+                const int k = k0 + c;
+                v[c] = tz[c] = m[c] = dq[c] = u0[c] = T(0);
+                if (c < C && k < nz) {
+                    T vv = sb[oc + k];
+                    if (it > 0) {
+                        vv = fma(stx[oc + k], cur[oe + k], vv);
+                        vv = fma(stx[ow + k], cur[ow + k], vv);
+                        if (hasN) vv = fma(sty[oc + k], cur[on + k], vv);
+                        if (hasS) vv = fma(sty[os + k], cur[os + k], vv);
+                        u0[c] = cur[oc + k];
+                    }
+                    v[c] = vv;
+                    tz[c] = stz[oc + k];
+                    m[c] = sm[oc + k];
+                    dq[c] = sdq[oc + k];
+                }
+            }
+            const T tprev = (k0 >= 1 && k0 - 1 < nz) ? stz[oc + k0 - 1] : T(0);
+            warp_column_scan<T>(v, tz, m, dq, tprev, C, k0, nz, lane);
+#pragma unroll
+            for (int c = 0; c < kWarpLayers; ++c) {
+                const int k = k0 + c;
+                if (c < C && k < nz)
+                    oth[oc + k] = it == 0 ? omega * v[c] : fma(om1, u0[c], omega * v[c]);
+            }
+        }
+        __syncthreads();  // the sweep is complete before the next one reads it
+        T *t = cur;
+        cur = oth;
+        oth = t;
+    }
+    for (int g = threadIdx.x; g < n; g += blockDim.x) {
+        const int k = g / ncol, c = g - k * ncol;
+        out[g] = cur[c * nz + k];
+    }
+}
+
 // ------------------------------------------------------------------ staged sweep
 // Asynchronous global->shared copies (cp.async, 4 or 8 bytes per thread).
 // Each thread stages and later reads only its own slots, so completion of

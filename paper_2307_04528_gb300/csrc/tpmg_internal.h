@@ -41,6 +41,7 @@ struct CgScalars {
 constexpr int kBlock = 128;          // threads per block, one column per thread
 constexpr int kMaxLayers = 192;      // MG_MAX_NZ of the C ABI (checked in tpmg_api.cpp)
 constexpr int kMaxRestrictRows = 4;  // fine rows per coarse row of the restriction (checked at setup)
+constexpr int kCoarseSolveThreads = 1024;  // one-block coarsest-level solve: 32 warps (FP32 only)
 constexpr int kReduceSlots = 65536;  // per-block partial sums kept in the workspace
 
 // ---- launchers (tpmg_kernels.cu); all asynchronous on `s` -----------------
@@ -261,6 +262,15 @@ cudaError_t launch_bsmooth_dot(const BOp<T> *ops, const BItem *items, int nitems
                                const int *active, int grid, int block, int nzmax,
                                double *partial, cudaStream_t s);
 cudaError_t bsmooth_prepare();
+// The coarsest-level solve of several systems, one block each with its level
+// in shared memory (coarse_solve_sh); op.a = b, op.y = out.  smem: the
+// largest coarse_sh_bytes of the ops.
+template <typename T>
+cudaError_t launch_bcoarse_solve(const BOp<T> *ops, int nops, double omega, int sweeps,
+                                 const int *active, size_t smem, cudaStream_t s);
+// Shared memory of the one-block coarsest-level solve, and whether it fits.
+size_t coarse_sh_bytes(int ncol, int nz, size_t value_bytes);
+bool coarse_sh_fits(int ncol, int nz, size_t value_bytes);
 
 // Set the thread-local message mg_last_error() returns.
 void set_last_error(const char *msg);

@@ -210,7 +210,6 @@ k_smooth_warp(LevelDev<T> L, const T *__restrict__ b, const T *uin, T *uout, T o
 // block-Jacobi sweeps from a zero guess) as one block: the warps share the
 // columns, a block barrier separates the sweeps, and the sweeps alternate
 // between out and scratch so that the last one lands in out.
-constexpr int kCoarseSolveThreads = 1024;  // 32 warps (FP32 only: ~56 registers per thread)
 
 template <typename T>
 __global__ void __launch_bounds__(kCoarseSolveThreads)
@@ -233,14 +232,7 @@ k_coarse_solve(LevelDev<T> L, const T *__restrict__ b, T *out, T *scratch, T ome
     }
 }
 
-// The same solve with the whole level in shared memory: b, t_z, 1/p, q/p,
-// t_x, t_y and the two sweep vectors, each stored as [column][layer], so a
-// lane's own layers are consecutive words (bank-conflict free for an odd
-// layers-per-lane count).  The level is staged once from its [layer][column]
-// arrays and the result written back once; the sweeps in between touch no
-// global memory.  Same arithmetic, same order as k_coarse_solve.
-constexpr int kCoarseShArrays = 8;
-
+// The same solve with the whole level in shared memory (coarse_solve_sh).
 template <typename T>
 __global__ void __launch_bounds__(kCoarseSolveThreads)
 k_coarse_solve_sh(LevelDev<T> L, const T *__restrict__ b, T *__restrict__ out, T omega, int sweeps,
@@ -248,79 +240,20 @@ k_coarse_solve_sh(LevelDev<T> L, const T *__restrict__ b, T *__restrict__ out, T
 {
     if (flag && !*flag) return;
     extern __shared__ __align__(16) unsigned char sh_raw[];
-    T *sh = reinterpret_cast<T *>(sh_raw);
-    const int nlon = L.nlon, nlat = L.nlat, nz = L.nz;
-    const int ncol = nlon * nlat, n = ncol * nz;
-    T *sb = sh, *stz = sh + n, *sm = sh + 2 * n, *sdq = sh + 3 * n, *stx = sh + 4 * n,
-      *sty = sh + 5 * n;
-    T *cur = sh + 6 * n, *oth = sh + 7 * n;
-    for (int g = threadIdx.x; g < n; g += blockDim.x) {
-        const int k = g / ncol, c = g - k * ncol, o = c * nz + k;
-        sb[o] = __ldg(b + g);
-        stz[o] = __ldg(L.tz + g);
-        sm[o] = __ldg(L.m + g);
-        sdq[o] = __ldg(L.dq + g);
-        stx[o] = __ldg(L.tx + g);
-        sty[o] = __ldg(L.ty + g);
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int C = (nz + 31) / 32, k0 = lane * C;
-    const T om1 = T(1) - omega;
-    for (int it = 0; it < sweeps; ++it) {
-        for (int col = warp; col < ncol; col += nw) {
-            const int j = col / nlon, i = col - j * nlon;
-            const int ie = (i + 1 == nlon) ? col - i : col + 1;
-            const int iw = (i == 0) ? col + nlon - 1 : col - 1;
-            const bool hasN = j + 1 < nlat, hasS = j > 0;
-            const int oc = col * nz, oe = ie * nz, ow = iw * nz;
-            const int on = (col + nlon) * nz, os = (col - nlon) * nz;
-            T v[kWarpLayers], tz[kWarpLayers], m[kWarpLayers], dq[kWarpLayers], u0[kWarpLayers];
-#pragma unroll
-            for (int c = 0; c < kWarpLayers; ++c) {
-                const int k = k0 + c;
-                v[c] = tz[c] = m[c] = dq[c] = u0[c] = T(0);
-                if (c < C && k < nz) {
-                    T vv = sb[oc + k];
-                    if (it > 0) {
-                        vv = fma(stx[oc + k], cur[oe + k], vv);
-                        vv = fma(stx[ow + k], cur[ow + k], vv);
-                        if (hasN) vv = fma(sty[oc + k], cur[on + k], vv);
-                        if (hasS) vv = fma(sty[os + k], cur[os + k], vv);
-                        u0[c] = cur[oc + k];
-                    }
-                    v[c] = vv;
-                    tz[c] = stz[oc + k];
-                    m[c] = sm[oc + k];
-                    dq[c] = sdq[oc + k];
-                }
-            }
-            const T tprev = (k0 >= 1 && k0 - 1 < nz) ? stz[oc + k0 - 1] : T(0);
-            warp_column_scan<T>(v, tz, m, dq, tprev, C, k0, nz, lane);
-#pragma unroll
-            for (int c = 0; c < kWarpLayers; ++c) {
-                const int k = k0 + c;
-                if (c < C && k < nz)
-                    oth[oc + k] = it == 0 ? omega * v[c] : fma(om1, u0[c], omega * v[c]);
-            }
-        }
-        __syncthreads();  // the sweep is complete before the next one reads it
-        T *t = cur;
-        cur = oth;
-        oth = t;
-    }
-    for (int g = threadIdx.x; g < n; g += blockDim.x) {
-        const int k = g / ncol, c = g - k * ncol;
-        out[g] = cur[c * nz + k];
-    }
+    coarse_solve_sh<T>(L, b, out, omega, sweeps, reinterpret_cast<T *>(sh_raw));
 }
 
 // Opt-in shared memory per block (set by smooth_prepare).
 static int g_smem_optin = 48 * 1024;
 
-static size_t coarse_sh_bytes(int ncol, int nz, size_t value_bytes)
+size_t coarse_sh_bytes(int ncol, int nz, size_t value_bytes)
 {
     return (size_t)kCoarseShArrays * ncol * nz * value_bytes;
+}
+
+bool coarse_sh_fits(int ncol, int nz, size_t value_bytes)
+{
+    return coarse_sh_bytes(ncol, nz, value_bytes) <= (size_t)g_smem_optin;
 }
 
 // FP32 levels with at most this many cells take the warp sweep (larger
@@ -341,7 +274,7 @@ cudaError_t launch_coarse_solve(const LevelDev<T> &L, const T *b, T *out, T *scr
                                 int sweeps, cudaStream_t s)
 {
     const size_t sh = coarse_sh_bytes(L.nlon * L.nlat, L.nz, sizeof(T));
-    if (sweeps >= 1 && sh <= (size_t)g_smem_optin)
+    if (sweeps >= 1 && coarse_sh_fits(L.nlon * L.nlat, L.nz, sizeof(T)))
         k_coarse_solve_sh<T><<<1, kCoarseSolveThreads, sh, s>>>(L, b, out, (T)omega, sweeps,
                                                                 nullptr);
     else

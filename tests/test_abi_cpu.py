@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_default_params(lib):
     from paper_2307_04528_gb300 import _lib as L
     p = L.default_params()
-    assert (p.levels, p.nu1, p.nu2, p.coarse_iters, p.method, p.mixed) == (0, 1, 1, 8, 0, 0)
+    assert (p.levels, p.nu1, p.nu2, p.coarse_iters, p.method, p.mixed) == (0, 1, 1, 12, 0, 0)
     assert p.omega == 0.85 and p.alpha_c == 0.6 and p.maxit == 200 and p.inner_tol == 5e-4
     assert p.inner_maxit == 12
 

@@ -103,7 +103,7 @@ def test_relax_and_coarsest_solve(case):
     """`coarse_iters` sweeps from zero on the coarsest level (the V-cycle's
     coarsest-level solve: one launch, the level in shared memory in FP32) and
     on the finest (one launch per sweep), FP64 1e-12 and FP32 2e-5 against
-    the oracle's sweeps repeated (FP32 rounding drift over 8 sweeps measured
+    the oracle's sweeps repeated (FP32 rounding drift over 12 sweeps measured
     at ~1e-6 on these shapes)."""
     P, lev, p, H = case
     l32 = O.float_levels(lev)

@@ -12,6 +12,7 @@ import subprocess
 
 import pytest
 
+import test_golden_paper as golden
 import test_oracle_pins as pins
 from oracle import build as obuild
 from oracle import tpmg as O
@@ -58,6 +59,29 @@ PINS = [
     pins.test_convergence_factor_on_small_workload,
     pins.test_gradient_matches_dense_lu_and_finite_differences,
 ]
+
+
+def _golden_condition_number():
+    golden.test_shallow_multigrid_condition_number((256, 128, 8))
+
+
+PINS.append(_golden_condition_number)
+
+
+def test_golden_pin_alone_catches_coarse_assembly_mutants(tmp_path, monkeypatch):
+    """The Section 2.3 figures by themselves catch the two coarse-operator
+    mutants."""
+    for name, fname, old, new in MUTANTS:
+        if not name.startswith("coarse"):
+            continue
+        sub = tmp_path / name.replace(" ", "_")
+        sub.mkdir()
+        lib = _build_mutant(str(sub), fname, old, new)
+        monkeypatch.setattr(O, "_LIB", None)
+        monkeypatch.setattr(O._build, "build", lambda force=False, lib=lib: lib)
+        with pytest.raises(AssertionError):
+            _golden_condition_number()
+        monkeypatch.setattr(O, "_LIB", None)
 
 
 def _build_mutant(tmp, fname, old, new):
