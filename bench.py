@@ -185,6 +185,10 @@ KERNEL_WORDS = {
 # DRAM bytes per fine cell of one k_smooth_dot<float> launch (ncu capture at
 # 512x384x70: 397.3 MB read + 34.8 MB written for 13,762,560 cells)
 SMOOTH_DOT_DRAM_BYTES_PER_CELL = (397.266944e6 + 34.799616e6) / (512 * 384 * 70)
+# DRAM bytes per fine cell of one k_resid_restrict<float> launch on the finest
+# level (ncu capture at 512x384x70: 359.0 MB read + 16.2 MB written for
+# 13,762,560 fine cells)
+RESID_RESTRICT_DRAM_BYTES_PER_CELL = (358.980864e6 + 16.153088e6) / (512 * 384 * 70)
 
 
 def kernel_table(H, L, N):
@@ -269,9 +273,11 @@ def run_ours(args):
     ms_mixed = max_over_ranks(ms_mixed / args.steps)
     info_m = infos[-1]
     # the same timed steps again with CUDA events around every launch
-    H.profile(2 if args.profile_out else 1)
+    H.profile(2)  # events around every launch of every level
     ms_prof, _ = timed(mixed_step, args.steps)
     sm_calls, sm_ms = H.profile_read(L.K_SMOOTH, 0, L.MG_PREC_FP32)
+    rr_calls, rr_ms = H.profile_read(L.K_RESID, 0, L.MG_PREC_FP32)
+    rr_all = [H.profile_read(L.K_RESID, lvl, L.MG_PREC_FP32) for lvl in range(H.num_levels)]
     res_calls, res_ms = H.profile_read(L.K_RESID, 0, L.MG_PREC_FP64)
     kernels = kernel_table(H, L, N)
     if args.profile_out:
@@ -314,21 +320,40 @@ def run_ours(args):
                "d2h_bytes_per_step": int(hx.numel() * 8)}
 
     peak, peak_kind = load_peaks()
-    # FP32 smoother sweep, algorithmic bytes: reads u, b, tx, ty, tz, m, dq; writes u (8 x 4 B)
-    sm_bytes = 32 * N
-    sm_avg_ms = sm_ms / max(sm_calls, 1)
-    achieved = sm_bytes / (sm_avg_ms * 1e-3) / 1e9 if sm_calls else None
-    roofline = {"kernel": "k_smooth_dot<float>: fine-level block-Jacobi sweep of Eq. (1) "
-                          "(last sweep of the V-cycle, CG inner product fused)", "bound": "hbm",
+    # the kernel with the largest share of the mixed solve: the FP32 V-cycle's
+    # fused residual + restriction; its finest-level launches.  Algorithmic
+    # bytes: reads u, b, tx, ty, tz, h of the fine level, writes the coarse
+    # right-hand side (level-1 cells)
+    c1 = H.level_shape(1) if H.num_levels > 1 else (0, 0, 0)
+    rr_bytes = 4 * (6 * N + c1[0] * c1[1] * c1[2])
+    rr_avg_ms = rr_ms / max(rr_calls, 1)
+    achieved = rr_bytes / (rr_avg_ms * 1e-3) / 1e9 if rr_calls else None
+    rr_traffic = (RESID_RESTRICT_DRAM_BYTES_PER_CELL * N
+                  if RESID_RESTRICT_DRAM_BYTES_PER_CELL is not None else None)
+    ms_rr_all = sum(ms for _, ms in rr_all)
+    roofline = {"kernel": "k_resid_restrict<float>: residual b - H u and its restriction R = P^T "
+                          "in one pass (FP32 V-cycle), finest-level launches", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
-                "traffic": SMOOTH_DOT_DRAM_BYTES_PER_CELL * N,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at "
-                                  "512x384x70, scaled per cell to this grid",
-                "launches_timed": sm_calls, "avg_ms": sm_avg_ms,
-                "bytes_per_launch": sm_bytes, "peak_source": peak_kind,
+                "traffic": rr_traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                  "finest-level launch at 512x384x70, scaled per fine cell",
+                "launches_timed": rr_calls, "avg_ms": rr_avg_ms,
+                "bytes_per_launch": rr_bytes, "peak_source": peak_kind,
+                "share_of_step_all_levels": (ms_rr_all / args.steps) / ms_prof if ms_prof else None,
                 "timed_region": "repeat of the K timed mixed solves with events around "
-                                "fine-level launches", "ms_per_step_profiled": ms_prof}
+                                "every launch", "ms_per_step_profiled": ms_prof}
+    # the next kernel: the V-cycle's last fine-level sweep with <r, z> fused
+    # (reads u, b, tx, ty, tz, m, dq; writes u: 8 x 4 B per cell)
+    sm_bytes = 32 * N
+    sm_avg_ms = sm_ms / max(sm_calls, 1)
+    sm_gbs = sm_bytes / (sm_avg_ms * 1e-3) / 1e9 if sm_calls else None
+    roofline_next = {"kernel": "k_smooth_dot<float>: fine-level block-Jacobi sweep of Eq. (1) "
+                               "with the CG inner product", "achieved": sm_gbs, "unit": "GB/s",
+                     "frac": (sm_gbs / peak) if sm_gbs else None,
+                     "traffic": SMOOTH_DOT_DRAM_BYTES_PER_CELL * N,
+                     "launches_timed": sm_calls, "avg_ms": sm_avg_ms,
+                     "bytes_per_launch": sm_bytes}
     res_avg = res_ms / max(res_calls, 1)
 
     out = {
@@ -349,6 +374,7 @@ def run_ours(args):
         "kernels_fine_level": kernels,
         "clocks": clk,
         "roofline": roofline,
+        "roofline_next": roofline_next,
     }
     if e2e:
         out["e2e"] = e2e
