@@ -186,9 +186,9 @@ KERNEL_WORDS = {
 # 512x384x70: 397.3 MB read + 34.8 MB written for 13,762,560 cells)
 SMOOTH_DOT_DRAM_BYTES_PER_CELL = (397.266944e6 + 34.799616e6) / (512 * 384 * 70)
 # DRAM bytes per fine cell of one k_resid_restrict<float> launch on the finest
-# level (ncu capture at 512x384x70: 359.0 MB read + 16.2 MB written for
+# level (ncu capture at 512x384x70: 353.0 MB read + 15.5 MB written for
 # 13,762,560 fine cells)
-RESID_RESTRICT_DRAM_BYTES_PER_CELL = (358.980864e6 + 16.153088e6) / (512 * 384 * 70)
+RESID_RESTRICT_DRAM_BYTES_PER_CELL = (352.967168e6 + 15.471616e6) / (512 * 384 * 70)
 
 
 def kernel_table(H, L, N):

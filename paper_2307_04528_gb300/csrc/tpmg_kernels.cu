@@ -369,7 +369,10 @@ k_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ r, T *__restrict__ bc
 }
 
 // Residual and restriction fused (resid_restrict_band): grid x = warps of
-// kRROwned coarse columns, y = bands of kRRBand coarse rows, z = layers.
+// kRROwned coarse columns, y = layers, z = bands of kRRBand coarse rows.  With
+// the layers before the bands in launch order, the blocks of one band at
+// neighbouring layers run together and share the planes above and below in
+// L2 (bands before layers: 0.662 instead of 0.614 ms at 1536 x 1152 x 70).
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_resid_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ b, const T *__restrict__ u,
@@ -378,8 +381,8 @@ k_resid_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ b, const T *__r
     if (flag && !*flag) return;
     const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     if (warp * kRROwned >= F.nlon / 2) return;  // whole warps
-    resid_restrict_band<T>(F, K, b, u, bc, warp, threadIdx.x & 31, blockIdx.y * kRRBand,
-                           blockIdx.z);
+    resid_restrict_band<T>(F, K, b, u, bc, warp, threadIdx.x & 31, blockIdx.z * kRRBand,
+                           blockIdx.y);
 }
 
 bool resid_restrict_fits(const void *b, const void *u, size_t value_bytes)
@@ -393,7 +396,7 @@ cudaError_t launch_resid_restrict(const LevelDev<T> &F, const LinkDev &K, const 
 {
     const int nc = F.nlon / 2;
     const int warps = (nc + kRROwned - 1) / kRROwned;
-    const dim3 grid((warps * 32 + kBlock - 1) / kBlock, (K.nlat_c + kRRBand - 1) / kRRBand, F.nz);
+    const dim3 grid((warps * 32 + kBlock - 1) / kBlock, F.nz, (K.nlat_c + kRRBand - 1) / kRRBand);
     k_resid_restrict<T><<<grid, kBlock, 0, s>>>(F, K, b, u, bc, flag);
     return cudaGetLastError();
 }
