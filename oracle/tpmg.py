@@ -70,7 +70,9 @@ class MGParams:
     nu2: int = 1               # post-smoothing sweeps
     omega: float = 0.85        # Eq. (1) relaxation factor (value not printed; tuned)
     coarse_iters: int = 12     # Section 2.3's simple coarsest-grid iteration: block-Jacobi sweeps
-    #                            (count not printed; measured)
+    #                            (count not printed; measured), or PCG iterations
+    coarse_method: str = "jacobi"  # coarsest-level solve: "jacobi" sweeps or "pcg" (CG
+    #                                preconditioned by the column solves), both from zero
     alpha_c: float = 0.6       # Section 2.2 anisotropy threshold (value not printed; tuned)
     method: str = "cg"         # outer iteration: "cg" (V-cycle-preconditioned CG) or "stationary"
     maxit: int = 200
@@ -312,21 +314,66 @@ def norm2(x) -> float:
     return float(np.sqrt(dot(x, x)))
 
 
+# --------------------------------------------------------------------- coarsest level
+def coarse_pcg(lev: Level, b, iters: int):
+    """Conjugate gradients on one level from a zero guess, preconditioned by
+    the column solves of Eq. (1) (z = H_z^{-1} r: a sweep from zero with
+    omega = 1), exactly `iters` iterations: the conjugate-gradient form of
+    the coarsest-grid iteration of Section 2.3.  Scalars in FP64, vectors in
+    b's precision (x += alpha d, r -= alpha H d, d = z + beta d in that
+    precision).  A zero <r, z> or <d, H d> ends it (exact solution reached)."""
+    one = b.dtype.type(1.0)
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = np.zeros_like(b)
+    smooth(lev, r, z, one)
+    d = z.copy()
+    rz = dot(r, z)
+    for it in range(iters):
+        q = apply(lev, d)
+        dq = dot(d, q)
+        if rz == 0.0 or dq == 0.0:
+            break
+        alpha = b.dtype.type(rz / dq)
+        x += alpha * d
+        r -= alpha * q
+        if it + 1 == iters:
+            break
+        z = np.zeros_like(b)
+        smooth(lev, r, z, one)
+        rz_new = dot(r, z)
+        beta = b.dtype.type(rz_new / rz)
+        rz = rz_new
+        d = z + beta * d
+    return x
+
+
+def coarse_solve(lev: Level, b, p: MGParams):
+    """The coarsest-level solve of the V-cycle from a zero guess (Section
+    2.3): coarse_iters block-Jacobi sweeps, or coarse_iters PCG iterations."""
+    if p.coarse_method == "pcg":
+        return coarse_pcg(lev, b, p.coarse_iters)
+    om = np.float32(p.omega) if b.dtype == np.float32 else p.omega
+    u = np.zeros_like(b)
+    work = np.empty_like(b)
+    for _ in range(p.coarse_iters):
+        smooth(lev, b, u, om, work)
+    return u
+
+
 # --------------------------------------------------------------------- V-cycle
 def vcycle(levels, b, params: MGParams | None = None, l: int = 0):
     """One V(nu1, nu2) cycle from a zero initial guess (Section 2, Fig. 1):
     smooth, restrict the residual, recurse, prolongate the correction, smooth.
-    On the coarsest level: coarse_iters smoother sweeps from zero
-    (Section 2.3's 'simple iterative method')."""
+    On the coarsest level: coarse_solve (Section 2.3's simple iteration on
+    the coarsest grid)."""
     p = params or MGParams()
     lev = levels[l]
+    if l == len(levels) - 1:
+        return coarse_solve(lev, b, p)
     om = np.float32(p.omega) if b.dtype == np.float32 else p.omega
     u = np.zeros_like(b)
     work = np.empty_like(b)
-    if l == len(levels) - 1:
-        for _ in range(p.coarse_iters):
-            smooth(lev, b, u, om, work)
-        return u
     for _ in range(p.nu1):
         smooth(lev, b, u, om, work)
     r = residual(lev, b, u)

@@ -312,6 +312,78 @@ def test_restriction_gathers_at_most_four_fine_rows(alpha_c):
         assert np.all(j1[single] == -1)      # a lone child interpolates nowhere
 
 
+def _dense(lev):
+    n = lev.size
+    A = np.empty((n, n))
+    e = np.zeros(n)
+    for c in range(n):
+        e[c] = 1.0
+        A[:, c] = O.apply(lev, e.reshape(lev.shape)).ravel()
+        e[c] = 0.0
+    return A
+
+
+def _dense_column_blocks(lev):
+    """H_z written out: per column the tridiagonal with diagonal h + the six
+    face couplings and off-diagonals -t_z (Eq. (1)'s split)."""
+    nz, nlat, nlon = lev.shape
+    idx = np.arange(lev.size).reshape(lev.shape)
+    Hz = np.zeros((lev.size, lev.size))
+    for k in range(nz):
+        for j in range(nlat):
+            for i in range(nlon):
+                c = idx[k, j, i]
+                d = lev.h[k, j, i] + lev.tx[k, j, i] + lev.tx[k, j, (i - 1) % nlon]
+                if j + 1 < nlat:
+                    d += lev.ty[k, j, i]
+                if j > 0:
+                    d += lev.ty[k, j - 1, i]
+                if k + 1 < nz:
+                    d += lev.tz[k, j, i]
+                    Hz[c, idx[k + 1, j, i]] = -lev.tz[k, j, i]
+                if k > 0:
+                    d += lev.tz[k - 1, j, i]
+                    Hz[c, idx[k - 1, j, i]] = -lev.tz[k - 1, j, i]
+                Hz[c, c] = d
+    return Hz
+
+
+def test_coarse_pcg_first_step_and_finite_termination():
+    """The PCG form of the coarsest-grid iteration: its first iterate is the
+    exact line search along z = H_z^{-1} b (H_z assembled by hand), the
+    H-norm error falls monotonically, and after n iterations on n unknowns
+    it reaches the dense solution (finite termination of CG)."""
+    P = small(nlon=8, nlat=4, nz=3, sigma=0.2, seed=5)
+    lev = levels_of(P, levels=1)[0][0]
+    A = _dense(lev)
+    b = np.random.default_rng(8).standard_normal(lev.shape)
+    z = np.linalg.solve(_dense_column_blocks(lev), b.ravel())
+    x1 = (b.ravel() @ z) / (z @ A @ z) * z
+    # cond(H_z) ~ 3e4 here: the dense solve itself is good to ~1e-12
+    assert np.abs(O.coarse_pcg(lev, b, 1).ravel() - x1).max() <= 1e-10 * np.abs(x1).max()
+    xs = np.linalg.solve(A, b.ravel())
+    errs = []
+    for it in (1, 2, 4, 8, 16):
+        e = O.coarse_pcg(lev, b, it).ravel() - xs
+        errs.append(e @ A @ e)
+    assert all(a > b_ for a, b_ in zip(errs, errs[1:]))
+    x = O.coarse_pcg(lev, b, lev.size).ravel()
+    assert np.linalg.norm(x - xs) <= 1e-9 * np.linalg.norm(xs)
+    assert np.array_equal(O.coarse_pcg(lev, np.zeros(lev.shape), 5), np.zeros(lev.shape))
+
+
+def test_coarse_pcg_in_the_vcycle():
+    """coarse_method = "pcg" replaces the coarsest level's sweeps: a V-cycle
+    over one level is the PCG itself, and with enough iterations a two-level
+    cycle's coarse correction solves the coarse system exactly."""
+    P = small(nlon=16, nlat=8, nz=3, sigma=0.1, seed=6)
+    lev, p = levels_of(P, levels=2, coarse_method="pcg", coarse_iters=200)
+    b = np.random.default_rng(9).standard_normal(lev[1].shape)
+    xs = np.linalg.solve(_dense(lev[1]), b.ravel())
+    got = O.vcycle(lev, b, p, l=1).ravel()
+    assert np.linalg.norm(got - xs) <= 1e-9 * np.linalg.norm(xs)
+
+
 def test_coarse_operator_conserves_volume_and_stays_spd():
     P = small(nlon=16, nlat=8, nz=3)
     lev, _ = levels_of(P, levels=3)
