@@ -54,6 +54,7 @@ typedef enum {
 
 enum { MG_METHOD_CG = 0, MG_METHOD_STATIONARY = 1 };
 enum { MG_PREC_FP64 = 0, MG_PREC_FP32 = 1 };
+enum { MG_COARSE_JACOBI = 0, MG_COARSE_PCG = 1 };
 
 typedef struct mg_handle mg_handle;
 
@@ -83,6 +84,13 @@ typedef struct {
     double alpha_c;    /* Section 2.2 anisotropy threshold for merging rows (0.6) */
     double inner_tol;  /* mixed: FP32 relative tolerance per refinement step (5e-4; loosened
                           when the outer target needs less) */
+    int coarse_method; /* coarsest-level solve from zero (Section 2.3's simple iteration on
+                          the coarsest grid): MG_COARSE_JACOBI, coarse_iters block-Jacobi
+                          sweeps (default; V stays a fixed linear operator), or MG_COARSE_PCG,
+                          coarse_iters iterations of CG preconditioned by the column solves
+                          (for shallow hierarchies; V then depends nonlinearly on its input,
+                          which the stationary method tolerates; CG usually does).  Single
+                          systems only: mg_batch_setup rejects MG_COARSE_PCG. */
 } mg_params;
 
 typedef struct {
@@ -163,6 +171,12 @@ int mg_level_apply(mg_handle *h, int level, int prec, const void *x, void *y, vo
 /* r = b - H_l u. */
 int mg_level_residual(mg_handle *h, int level, int prec, const void *b, const void *u,
                       void *r, void *stream);
+
+/* out = the V-cycle's coarsest-level solve applied to b (the configured
+ * coarse_method and coarse_iters, from a zero guess), on the coarsest level
+ * (b, out: its shape, distinct).  Uses the handle's coarsest-level work
+ * vectors: calls on one handle must not overlap. */
+int mg_coarse_solve(mg_handle *h, int prec, const void *b, void *out, void *stream);
 
 /* bc = R_l (b - H_l u): the residual restricted to level l+1 in one pass,
  * the residual itself never stored (the FP32 V-cycle's form; equal term for

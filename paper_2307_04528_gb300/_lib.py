@@ -16,6 +16,7 @@ MG_OK, MG_ERR_ARG, MG_ERR_COEFF, MG_ERR_NONFINITE, MG_ERR_NOT_CONVERGED = 0, 1, 
 MG_ERR_DIVERGED, MG_ERR_TIMEOUT, MG_ERR_CUDA, MG_ERR_WORKSPACE = 5, 6, 7, 8
 MG_METHOD_CG, MG_METHOD_STATIONARY = 0, 1
 MG_PREC_FP64, MG_PREC_FP32 = 0, 1
+MG_COARSE_JACOBI, MG_COARSE_PCG = 0, 1
 # kernel classes of mg_profile_read
 K_SMOOTH, K_SMOOTH0, K_RESID, K_APPLY, K_RESTRICT, K_PROLONG, K_VEC = range(7)
 
@@ -44,7 +45,7 @@ class mg_params(ctypes.Structure):
                 ("coarse_iters", ctypes.c_int), ("method", ctypes.c_int), ("mixed", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("inner_maxit", ctypes.c_int),
                 ("omega", ctypes.c_double), ("alpha_c", ctypes.c_double),
-                ("inner_tol", ctypes.c_double)]
+                ("inner_tol", ctypes.c_double), ("coarse_method", ctypes.c_int)]
 
 
 class mg_stats(ctypes.Structure):
@@ -87,6 +88,7 @@ def load() -> ctypes.CDLL:
         "mg_level_smooth": (I, [H, I, I, P, P, P, P]),
         "mg_level_smooth_dot": (I, [H, I, I, P, P, P, ctypes.POINTER(D), P]),
         "mg_level_relax": (I, [H, I, I, I, P, P, P]),
+        "mg_coarse_solve": (I, [H, I, P, P, P]),
         "mg_level_residual_restrict": (I, [H, I, I, P, P, P, P]),
         "mg_level_restrict": (I, [H, I, I, P, P, P]),
         "mg_level_prolong_add": (I, [H, I, I, P, P, P]),

@@ -178,6 +178,8 @@ static int check_grid(const mg_grid *g, const mg_params *p, int *L_out)
     if (L > 1 && (g->nlon % (1 << (L - 1)) || (g->nlon >> (L - 1)) < 2))
         return fail(MG_ERR_ARG, "nlon=%d not divisible by 2^(levels-1) = %d", g->nlon,
                     1 << (L - 1));
+    if (p->coarse_method != MG_COARSE_JACOBI && p->coarse_method != MG_COARSE_PCG)
+        return fail(MG_ERR_ARG, "coarse_method %d unknown", p->coarse_method);
     if (p->nu1 < 1 || p->nu2 < 0 || p->coarse_iters < 1 || p->maxit < 0 ||
         !(p->omega > 0.0 && p->omega < 2.0) || (p->method != MG_METHOD_CG &&
                                                  p->method != MG_METHOD_STATIONARY))
@@ -235,6 +237,11 @@ static size_t carve(mg_handle *H, void *base)
         v.w = cv.take<double>(n);
         v.r = cv.take<double>(n);
         if (l > 0) v.b = cv.take<double>(n);
+        const bool pcg = l == H->L - 1 && H->p.coarse_method == MG_COARSE_PCG;
+        if (pcg) {
+            v.cd = cv.take<double>(n);
+            v.cq = cv.take<double>(n);
+        }
         if (mixed) {
             v.tx32 = cv.take<float>(n);
             v.ty32 = cv.take<float>(n);
@@ -246,6 +253,10 @@ static size_t carve(mg_handle *H, void *base)
             v.w32 = cv.take<float>(n);
             v.r32 = cv.take<float>(n);
             v.b32 = cv.take<float>(n);  // level 0: right-hand side of the inner solve
+            if (pcg) {
+                v.cd32 = cv.take<float>(n);
+                v.cq32 = cv.take<float>(n);
+            }
         }
         if (l + 1 < H->L) {
             LinkHost &K = v.link;
@@ -279,6 +290,7 @@ static size_t carve(mg_handle *H, void *base)
     }
     H->partial = cv.take<double>(kReduceSlots);
     H->sc = cv.take<CgScalars>(1);
+    H->sc_coarse = cv.take<CgScalars>(1);
     H->flag = cv.take<int>(4);
     return cv.off + 256;
 }
@@ -298,6 +310,7 @@ extern "C" void mg_default_params(mg_params *p)
     p->omega = 0.85;
     p->alpha_c = 0.6;
     p->inner_tol = 5e-4;
+    p->coarse_method = MG_COARSE_JACOBI;
 }
 
 extern "C" const char *mg_last_error(void) { return g_last_error.c_str(); }
@@ -570,6 +583,49 @@ static int smooth_from_zero(mg_handle *H, int l, const LevelDev<T> &D, const T *
     return MG_OK;
 }
 
+// The coarsest-level solve as coarse_iters iterations of conjugate
+// gradients from zero, preconditioned by the column solves (z = H_z^{-1} r:
+// the zero-guess sweep with omega = 1), every scalar on the device (its own
+// CgScalars), so the whole solve is captured in the V-cycle's graph.
+// Vectors: out = x, the level's r, w = z, cd = d, cq = H d.
+template <typename T>
+static int coarse_pcg(mg_handle *H, int l, const LevelDev<T> &D, const T *b, T *out, cudaStream_t s)
+{
+    LevelHost &v = H->lev[l];
+    const size_t n = v.n;
+    constexpr int P = prec_of<T>();
+    T *r = Vec<T>::r(v), *z = Vec<T>::w(v), *d = Vec<T>::cd(v), *q = Vec<T>::cq(v);
+    CgScalars *sc = H->sc_coarse;
+    if (!d || !q) return fail(MG_ERR_ARG, "PCG coarse solve without its vectors");
+    CU(cudaMemsetAsync(out, 0, n * sizeof(T), s));
+    KRUN(K_VEC, l, P, launch_cg_direction<T>(b, nullptr, r, n, sc, true, s));  // r = b
+    KRUN(K_SMOOTH0, l, P, launch_smooth<T>(D, r, nullptr, z, 1.0, s));
+    int nb = 0;
+    KRUN(K_VEC, l, P, nb = launch_dot<T>(r, z, n, H->partial, s));
+    KRUN(K_VEC, l, P, launch_finalize(H->partial, nb, sc, S_RZ, 0, s));
+    KRUN(K_VEC, l, P, launch_cg_direction<T>(z, nullptr, d, n, sc, true, s));  // d = z
+    for (int it = 0; it < H->p.coarse_iters; ++it) {
+        KRUN(K_APPLY, l, P, nb = launch_stencil<T>(D, 0, nullptr, d, q, H->partial, s));
+        KRUN(K_VEC, l, P, launch_finalize(H->partial, nb, sc, S_DAD, 1, s));
+        KRUN(K_VEC, l, P, launch_cg_update<T>(out, r, d, q, n, sc, H->partial, s));
+        if (it + 1 == H->p.coarse_iters) break;
+        KRUN(K_SMOOTH0, l, P, launch_smooth<T>(D, r, nullptr, z, 1.0, s));
+        KRUN(K_VEC, l, P, nb = launch_dot<T>(r, z, n, H->partial, s));
+        KRUN(K_VEC, l, P, launch_finalize(H->partial, nb, sc, S_RZNEW, 2, s));
+        KRUN(K_VEC, l, P, launch_cg_direction<T>(z, d, d, n, sc, false, s));
+    }
+    return MG_OK;
+}
+
+// The V-cycle's coarsest-level solve from zero (Section 2.3).
+template <typename T>
+static int coarse_solve(mg_handle *H, int l, const LevelDev<T> &D, const T *b, T *out, T *scratch,
+                        cudaStream_t s)
+{
+    if (H->p.coarse_method == MG_COARSE_PCG) return coarse_pcg<T>(H, l, D, b, out, s);
+    return smooth_from_zero<T>(H, l, D, b, out, scratch, H->p.coarse_iters, H->p.omega, s);
+}
+
 // out = V_l b (zero initial guess).  scratch, rbuf: level-l work vectors.
 // dot_blocks (level 0 only, may be null): fuse <b, out> into the last sweep
 // and set *dot_blocks to the number of partial sums written (0 if the cycle
@@ -582,8 +638,7 @@ static int vcycle_level(mg_handle *H, int l, const T *b, T *out, T *scratch, T *
     LevelHost &v = H->lev[l];
     const LevelDev<T> D = dev<T>(v);
     const double om = H->p.omega;
-    if (l == H->L - 1)
-        return smooth_from_zero<T>(H, l, D, b, out, scratch, H->p.coarse_iters, om, s);
+    if (l == H->L - 1) return coarse_solve<T>(H, l, D, b, out, scratch, s);
     const int writes = H->p.nu1 + H->p.nu2;
     T *cur = (writes % 2 == 1) ? out : scratch;
     T *oth = (cur == out) ? scratch : out;
@@ -1069,6 +1124,29 @@ extern "C" int mg_level_residual_restrict(mg_handle *H, int level, int prec, con
     }
     CHK(level_op<float>(H, level, 1, b, u, Vec<float>::r(v), s));
     return level_op<float>(H, level, 3, Vec<float>::r(v), nullptr, bc, s);
+}
+
+extern "C" int mg_coarse_solve(mg_handle *H, int prec, const void *b, void *out, void *stream)
+{
+    if (!H) return fail(MG_ERR_ARG, "null handle");
+    const int l = H->L - 1;
+    CHK(level_check(H, l, prec, false));
+    if (!b || !out || b == out) return fail(MG_ERR_ARG, "bad coarse-solve buffers");
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelHost &v = H->lev[l];
+    if (prec == MG_PREC_FP64) {
+        const void *own[] = {Vec<double>::w(v), Vec<double>::r(v), Vec<double>::cd(v),
+                             Vec<double>::cq(v)};
+        for (const void *p : own)
+            if (p && (p == b || p == out)) return fail(MG_ERR_ARG, "buffer aliases a work vector");
+        return coarse_solve<double>(H, l, dev<double>(v), (const double *)b, (double *)out,
+                                    Vec<double>::w(v), s);
+    }
+    const void *own[] = {Vec<float>::w(v), Vec<float>::r(v), Vec<float>::cd(v), Vec<float>::cq(v)};
+    for (const void *p : own)
+        if (p && (p == b || p == out)) return fail(MG_ERR_ARG, "buffer aliases a work vector");
+    return coarse_solve<float>(H, l, dev<float>(v), (const float *)b, (float *)out,
+                               Vec<float>::w(v), s);
 }
 
 extern "C" int mg_level_relax(mg_handle *H, int level, int prec, int sweeps, const void *b,

@@ -1089,6 +1089,8 @@ extern "C" int mg_batch_workspace_bytes(int n, const mg_grid *grids, const mg_pa
                                         size_t *bytes)
 {
     if (n < 1 || !grids || !params || !bytes) return fail(MG_ERR_ARG, "bad batch arguments");
+    if (params->coarse_method != MG_COARSE_JACOBI)
+        return fail(MG_ERR_ARG, "batched solves take the block-Jacobi coarsest-level solve");
     mg_batch *B = batch_new(n, grids, params);
     size_t total = 0;
     const int st = batch_layout(B, nullptr, &total);
@@ -1104,6 +1106,8 @@ extern "C" int mg_batch_setup(int n, const mg_grid *grids, const mg_coeffs *coef
     if (!out) return fail(MG_ERR_ARG, "null out");
     *out = nullptr;
     if (n < 1 || !grids || !coeffs || !params) return fail(MG_ERR_ARG, "bad batch arguments");
+    if (params->coarse_method != MG_COARSE_JACOBI)
+        return fail(MG_ERR_ARG, "batched solves take the block-Jacobi coarsest-level solve");
     if (!workspace || (uintptr_t)workspace % 256)
         return fail(MG_ERR_WORKSPACE, "workspace null or not 256-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;

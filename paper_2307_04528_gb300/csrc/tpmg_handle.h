@@ -58,6 +58,9 @@ struct LevelHost {
     // V-cycle vectors: rhs, result, ping-pong scratch, residual
     double *b = nullptr, *u = nullptr, *w = nullptr, *r = nullptr;
     float *b32 = nullptr, *u32 = nullptr, *w32 = nullptr, *r32 = nullptr;
+    // coarsest level with the PCG coarse solve: direction and its image
+    double *cd = nullptr, *cq = nullptr;
+    float *cd32 = nullptr, *cq32 = nullptr;
     LinkHost link;
     LinkDev linkdev{};
 };
@@ -106,6 +109,7 @@ struct mg_handle {
     CgVecs<float> cg32;
     double *partial = nullptr;
     CgScalars *sc = nullptr;
+    CgScalars *sc_coarse = nullptr;  // scalars of the PCG coarse solve
     int *flag = nullptr;
     double scale32 = 0.0;
 };
@@ -126,6 +130,8 @@ template <typename T>
 struct Vec;
 template <>
 struct Vec<double> {
+    static double *cd(LevelHost &l) { return l.cd; }
+    static double *cq(LevelHost &l) { return l.cq; }
     static double *b(LevelHost &l) { return l.b; }
     static double *u(LevelHost &l) { return l.u; }
     static double *w(LevelHost &l) { return l.w; }
@@ -134,6 +140,8 @@ struct Vec<double> {
 };
 template <>
 struct Vec<float> {
+    static float *cd(LevelHost &l) { return l.cd32; }
+    static float *cq(LevelHost &l) { return l.cq32; }
     static float *b(LevelHost &l) { return l.b32; }
     static float *u(LevelHost &l) { return l.u32; }
     static float *w(LevelHost &l) { return l.w32; }

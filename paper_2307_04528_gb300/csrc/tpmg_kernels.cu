@@ -622,9 +622,11 @@ k_finalize(const double *__restrict__ partial, int n, CgScalars *sc, int which, 
         if (lane == 0) {
             double *slots = reinterpret_cast<double *>(sc);
             slots[which] = v;
-            if (op == 1) sc->alpha = sc->rz / v;
+            // a zero denominator only follows an exact solution (r = 0): the
+            // step and the new direction's history are then zero
+            if (op == 1) sc->alpha = v != 0.0 ? sc->rz / v : 0.0;
             if (op == 2) {
-                sc->beta = v / sc->rz;
+                sc->beta = sc->rz != 0.0 ? v / sc->rz : 0.0;
                 sc->rz = v;
             }
         }

@@ -35,7 +35,8 @@ class MGHandle:
 
     tx, ty, tz, h: CUDA float64 tensors (copied into the workspace at setup).
     params: keyword overrides of mg_params (levels, nu1, nu2, coarse_iters,
-    method, mixed, maxit, inner_maxit, omega, alpha_c, inner_tol).
+    method, mixed, maxit, inner_maxit, omega, alpha_c, inner_tol,
+    coarse_method).
     """
 
     @classmethod
@@ -179,6 +180,13 @@ class MGHandle:
         L.check(self.lib.mg_level_residual_restrict(self._hh, level, prec, _ptr(b), _ptr(u),
                                                     _ptr(bc), _stream()))
         return bc
+
+    def coarse_solve(self, b, prec=L.MG_PREC_FP64):
+        """The V-cycle's coarsest-level solve (block-Jacobi sweeps or PCG, as
+        configured) applied to b on the coarsest level."""
+        out = torch.empty_like(b)
+        L.check(self.lib.mg_coarse_solve(self._hh, prec, _ptr(b), _ptr(out), _stream()))
+        return out
 
     def level_relax(self, level, b, sweeps, prec=L.MG_PREC_FP64):
         """`sweeps` sweeps from the zero guess (on the coarsest level with

@@ -43,7 +43,7 @@ def test_default_params(lib):
     p = L.default_params()
     assert (p.levels, p.nu1, p.nu2, p.coarse_iters, p.method, p.mixed) == (0, 1, 1, 12, 0, 0)
     assert p.omega == 0.85 and p.alpha_c == 0.6 and p.maxit == 200 and p.inner_tol == 5e-4
-    assert p.inner_maxit == 12
+    assert p.inner_maxit == 12 and p.coarse_method == L.MG_COARSE_JACOBI
 
 
 def _bytes(lib, nlon, nlat, nz, **kw):
@@ -74,11 +74,23 @@ def test_workspace_sizing(lib):
                                       ((64, 32, 193), {}),       # nz = MG_MAX_NZ + 1
                                       ((48, 32, 4), {"levels": 6}),  # 48 not divisible by 32
                                       ((64, 32, 4), {"omega": 2.5}),
-                                      ((64, 32, 4), {"nu1": 0})])
+                                      ((64, 32, 4), {"nu1": 0}),
+                                      ((64, 32, 4), {"coarse_method": 2})])
 def test_bad_arguments_rejected_on_host(lib, shape, kw):
     st, _ = _bytes(lib, *shape, **kw)
     assert st == 1
     assert lib.mg_last_error()
+
+
+def test_pcg_coarse_solve_sizes_and_batch_rejection(lib):
+    from paper_2307_04528_gb300 import _lib as L
+    st, jac = _bytes(lib, 64, 32, 16, mixed=1)
+    st2, pcg = _bytes(lib, 64, 32, 16, mixed=1, coarse_method=L.MG_COARSE_PCG)
+    assert st == st2 == 0 and pcg > jac  # two coarsest-level vectors per precision
+    g = (L.mg_grid * 1)(L.mg_grid(64, 32, 16))
+    p = L.default_params(mixed=1, coarse_method=L.MG_COARSE_PCG)
+    n = ctypes.c_size_t(0)
+    assert lib.mg_batch_workspace_bytes(1, g, ctypes.byref(p), ctypes.byref(n)) == L.MG_ERR_ARG
 
 
 def test_level_counts_follow_nlon(lib):

@@ -126,6 +126,36 @@ def test_relax_and_coarsest_solve(case):
         assert rel_inf(got, want) <= 2e-5
 
 
+@pytest.mark.parametrize("shape,levels", [((64, 32, 16), 3), ((96, 46, 9), 2), ((64, 32, 16), 0)])
+def test_coarse_pcg(shape, levels):
+    """coarse_method = PCG: the coarsest-level solve against the oracle's
+    coarse_pcg (FP64 1e-10; FP32 2e-5, its FP32 rounding drift measured at
+    ~5e-7 on these levels), the FP64 V-cycle against the oracle's (1e-10),
+    and a 3-level FP64 and mixed solve to 1e-10 against the oracle's FP64
+    solution (1e-9)."""
+    P = problem(*shape, sigma=0.2, seed=sum(shape) + levels)
+    lev, p = oracle_levels(P, levels=levels, coarse_method="pcg")
+    H = handle_for(P, levels=levels, coarse_method=1)
+    assert H.num_levels == len(lev)
+    l32 = O.float_levels(lev)
+    rng = np.random.default_rng(16)
+    b = rng.standard_normal(lev[-1].shape)
+    got = host(H.coarse_solve(dev(b)))
+    assert rel_inf(got, O.coarse_pcg(lev[-1], b, p.coarse_iters)) <= 1e-10
+    b32 = b.astype(np.float32)
+    got = host(H.coarse_solve(dev(b32, torch.float32), prec=1))
+    assert rel_inf(got, O.coarse_pcg(l32[-1], b32, p.coarse_iters)) <= 2e-5
+    r = rng.standard_normal(lev[0].shape)
+    assert rel_inf(host(H.vcycle(dev(r))), O.vcycle(lev, r, p)) <= 1e-10
+    if levels == 3:
+        xr, _, sr = O.solve(lev, P["b"], 1e-11, params=p)
+        assert sr == O.OK
+        for fn in (H.solve, H.solve_mixed):
+            x, info = fn(dev(P["b"]), tol=1e-10)
+            assert info["status"] == 0 and info["rel_res"] <= 1e-10
+            assert rel_2(host(x), xr) <= 1e-9
+
+
 def test_coarsest_solve_beyond_shared_memory():
     """A shallow hierarchy whose coarsest level (40 x 30 x 32 cells) exceeds
     one block's shared memory: the FP32 coarsest-level solve runs from
