@@ -272,6 +272,26 @@ def run_ours(args):
     clk = clocks.stop()
     ms_mixed = max_over_ranks(ms_mixed / args.steps)
     info_m = infos[-1]
+    # end to end through the public API with host buffers (pinned), right
+    # after the device-resident steps (before the FP64 comparison solves)
+    e2e = None
+    if not args.no_e2e:
+        hb = torch.from_numpy(P["b"]).pin_memory()
+        hx = torch.empty_like(hb).pin_memory()
+
+        def e2e_step():
+            bd = hb.to("cuda", non_blocking=True)
+            xd = torch.zeros_like(bd)
+            _, info = H.solve_mixed(bd, xd, tol=TOL)
+            hx.copy_(xd, non_blocking=True)
+            return info
+
+        e2e_step()
+        ms_e2e, _ = timed(e2e_step, args.steps)
+        ms_e2e = max_over_ranks(ms_e2e / args.steps)
+        e2e = {"value": ms_e2e, "unit": UNIT, "h2d_bytes_per_step": int(hb.numel() * 8),
+               "d2h_bytes_per_step": int(hx.numel() * 8)}
+
     # the same timed steps again with CUDA events around every launch
     H.profile(2)  # events around every launch of every level
     ms_prof, _ = timed(mixed_step, args.steps)
@@ -299,25 +319,6 @@ def run_ours(args):
     ms_fp64, infos64 = timed(fp64_step, args.steps)
     ms_fp64 = max_over_ranks(ms_fp64 / args.steps)
     info_d = infos64[-1]
-
-    # end to end through the public API with host buffers (pinned)
-    e2e = None
-    if not args.no_e2e:
-        hb = torch.from_numpy(P["b"]).pin_memory()
-        hx = torch.empty_like(hb).pin_memory()
-
-        def e2e_step():
-            bd = hb.to("cuda", non_blocking=True)
-            xd = torch.zeros_like(bd)
-            _, info = H.solve_mixed(bd, xd, tol=TOL)
-            hx.copy_(xd, non_blocking=True)
-            return info
-
-        e2e_step()
-        ms_e2e, _ = timed(e2e_step, args.steps)
-        ms_e2e = max_over_ranks(ms_e2e / args.steps)
-        e2e = {"value": ms_e2e, "unit": UNIT, "h2d_bytes_per_step": int(hb.numel() * 8),
-               "d2h_bytes_per_step": int(hx.numel() * 8)}
 
     peak, peak_kind = load_peaks()
     # the kernel with the largest share of the mixed solve: the FP32 V-cycle's
