@@ -175,6 +175,7 @@ KERNEL_WORDS = {
     (1, 1): ("smooth fp32 zero guess", 5),            # b tz m dq -> u
     (2, 1): ("residual + restriction fp32", 6),       # u b tx ty tz h -> b_c (+ coarse write)
     (3, 1): ("direction update + apply fp32", 8),     # z d tx ty tz h -> d q
+    (5, 1): ("prolongation + correction fp32", 2),    # u e_c -> u (+ coarse read)
     (0, 0): ("smooth fp64", 8),                       # u b tx ty tz m dq -> u
     (1, 0): ("smooth fp64 zero guess", 5),
     (2, 0): ("residual fp64 -> scaled fp32", 6.5),    # x b tx ty tz h -> r32
@@ -199,7 +200,7 @@ def kernel_table(H, L, N):
         n, ms = H.profile_read(kind, 0, prec)
         if n == 0:
             continue
-        if (kind, prec) == (2, 1):
+        if (kind, prec) in ((2, 1), (5, 1)):
             words = words + coarse_ratio
         avg = ms / n
         nbytes = words * (4 if prec == 1 else 8) * N
