@@ -649,7 +649,7 @@ static int vcycle_level(mg_handle *H, int l, const T *b, T *out, T *scratch, T *
         std::swap(cur, oth);
     }
     LevelHost &c = H->lev[l + 1];
-    if (sizeof(T) == 4 && resid_restrict_fits(b, cur, sizeof(T))) {
+    if (sizeof(T) == 4 && resid_restrict_fits(b, cur, sizeof(T), v.linkdev.nlat_c)) {
         // FP32: one pass, the residual never stored (the FP64 stencil is
         // bound by FP64 arithmetic, which the fused pass would increase)
         KRUN(K_RESID, l, P, launch_resid_restrict<T>(D, v.linkdev, b, cur, Vec<T>::b(c), s));
@@ -1106,7 +1106,7 @@ extern "C" int mg_level_residual_restrict(mg_handle *H, int level, int prec, con
     cudaStream_t s = (cudaStream_t)stream;
     LevelHost &v = H->lev[level];
     const size_t vb = prec == MG_PREC_FP64 ? 8 : 4;
-    if (resid_restrict_fits(b, u, vb)) {
+    if (resid_restrict_fits(b, u, vb, v.linkdev.nlat_c)) {
         if (prec == MG_PREC_FP64)
             KRUN(K_RESID, level, 0,
                  launch_resid_restrict<double>(dev<double>(v), v.linkdev, (const double *)b,

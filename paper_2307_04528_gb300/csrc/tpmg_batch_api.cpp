@@ -229,7 +229,7 @@ void gen_level(mg_handle *H, int sys, int l, int Lmax, const T *b, T *out, T *sc
     }
     LevelHost &c = H->lev[l + 1];
     if (sizeof(T) == 4 && (long long)D.nlon * D.nlat >= kBigColumns &&
-        resid_restrict_fits(b, cur, sizeof(T))) {
+        resid_restrict_fits(b, cur, sizeof(T), v.linkdev.nlat_c)) {
         // a large FP32 level: the single-system fused pass
         push(down, BK_RESID_RESTRICT, b, cur, Vec<T>::b(c), D, v.linkdev);
     } else {

@@ -93,8 +93,8 @@ cudaError_t set_dynamic_smem_limit(const void *kernel, int lim);
 size_t smooth_smem_bytes(int nz, size_t value_bytes);
 
 // b_c = R (b - H u) in one pass (FP32 V-cycle); b and u aligned to two
-// values (resid_restrict_fits).
-bool resid_restrict_fits(const void *b, const void *u, size_t value_bytes);
+// values and at most 65535 bands of coarse rows (resid_restrict_fits).
+bool resid_restrict_fits(const void *b, const void *u, size_t value_bytes, int nlat_c);
 template <typename T>
 cudaError_t launch_resid_restrict(const LevelDev<T> &F, const LinkDev &K, const T *b, const T *u,
                                   T *bc, cudaStream_t s, const int *flag = nullptr);

@@ -388,9 +388,10 @@ k_resid_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ b, const T *__r
                            blockIdx.y);
 }
 
-bool resid_restrict_fits(const void *b, const void *u, size_t value_bytes)
+bool resid_restrict_fits(const void *b, const void *u, size_t value_bytes, int nlat_c)
 {
-    return (uintptr_t)b % (2 * value_bytes) == 0 && (uintptr_t)u % (2 * value_bytes) == 0;
+    return (uintptr_t)b % (2 * value_bytes) == 0 && (uintptr_t)u % (2 * value_bytes) == 0 &&
+           (nlat_c + kRRBand - 1) / kRRBand <= 65535;  // bands on the grid's z axis
 }
 
 template <typename T>
