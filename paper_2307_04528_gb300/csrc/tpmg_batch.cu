@@ -148,6 +148,15 @@ k_bcells(const BOp<T> *__restrict__ ops, const BItem *__restrict__ items, int ni
         const BItem item = items[it];
         const BOp<T> &op = ops[item.op];
         if (active && !active[op.sys]) continue;
+        if (KIND == 3) {  // fused residual + restriction: tile = (band * nz + k) * nblk + xb
+            const int xb = item.tile % op.nblk, rest = item.tile / op.nblk;
+            const int k = rest % op.L.nz, band = rest / op.L.nz;
+            const int warp = (xb * blockDim.x + threadIdx.x) >> 5;
+            if (warp * kRROwned < op.L.nlon / 2)  // whole warps
+                resid_restrict_band<T>(op.L, op.K, op.a, op.x, op.y, warp, threadIdx.x & 31,
+                                       band * kRRBand, k);
+            continue;
+        }
         const int zc = item.tile / op.nblk;
         const int c = (item.tile - zc * op.nblk) * blockDim.x + threadIdx.x;
         const int k0 = zc * op.kz, k1 = min(op.L.nz, k0 + op.kz);
@@ -170,12 +179,15 @@ cudaError_t launch_bcells(int kind, const BOp<T> *ops, const BItem *items, int n
                           const int *active, int grid, cudaStream_t s)
 {
     if (nitems <= 0) return cudaSuccess;
-    const void *k = kind == 0 ? (const void *)k_bcells<T, 0>
-                              : (kind == 1 ? (const void *)k_bcells<T, 1> : (const void *)k_bcells<T, 2>);
+    const void *k = kind == 0   ? (const void *)k_bcells<T, 0>
+                    : kind == 1 ? (const void *)k_bcells<T, 1>
+                    : kind == 2 ? (const void *)k_bcells<T, 2>
+                                : (const void *)k_bcells<T, 3>;
     grid = std::min(grid, resident_grid(k, kBlock, 0));
     if (kind == 0) k_bcells<T, 0><<<grid, kBlock, 0, s>>>(ops, items, nitems, active);
     else if (kind == 1) k_bcells<T, 1><<<grid, kBlock, 0, s>>>(ops, items, nitems, active);
-    else k_bcells<T, 2><<<grid, kBlock, 0, s>>>(ops, items, nitems, active);
+    else if (kind == 2) k_bcells<T, 2><<<grid, kBlock, 0, s>>>(ops, items, nitems, active);
+    else k_bcells<T, 3><<<grid, kBlock, 0, s>>>(ops, items, nitems, active);
     return cudaGetLastError();
 }
 

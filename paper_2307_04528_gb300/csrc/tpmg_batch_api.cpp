@@ -228,9 +228,9 @@ void gen_level(mg_handle *H, int sys, int l, int Lmax, const T *b, T *out, T *sc
         std::swap(cur, oth);
     }
     LevelHost &c = H->lev[l + 1];
-    if (sizeof(T) == 4 && (long long)D.nlon * D.nlat >= kBigColumns &&
-        resid_restrict_fits(b, cur, sizeof(T), v.linkdev.nlat_c)) {
-        // a large FP32 level: the single-system fused pass
+    if (sizeof(T) == 4 && resid_restrict_fits(b, cur, sizeof(T), v.linkdev.nlat_c)) {
+        // FP32: the fused pass (the single-system kernel on large levels,
+        // the work list on the others)
         push(down, BK_RESID_RESTRICT, b, cur, Vec<T>::b(c), D, v.linkdev);
     } else {
         push(down, BK_RESID, b, cur, rbuf, D, nolink);
@@ -269,8 +269,12 @@ int tiles_of(int kind, const BOp<T> &op, int block, int *nblk)
     case BK_RESTRICT:
         *nblk = cdiv((long long)(op.L.nlon / 2) * op.K.nlat_c, kBlock);
         return *nblk * cdiv(op.L.nz, op.kz);
-    case BK_RESID_RESTRICT:  // large levels only, launched on their own
-    case BK_COARSE:          // one block per system, launched on its own
+    case BK_RESID_RESTRICT: {  // warp blocks along longitude x layers x bands
+        const int warps = cdiv(op.L.nlon / 2, kRROwned);
+        *nblk = cdiv((long long)warps * 32, kBlock);
+        return *nblk * op.L.nz * cdiv(op.K.nlat_c, kRRBand);
+    }
+    case BK_COARSE:  // one block per system, launched on its own
         *nblk = 0;
         return 0;
     default:
@@ -706,8 +710,11 @@ static int run_vstep(mg_batch *B, StepHost<T> &st, cudaStream_t s)
                                   B->smooth_block, B->nzmax, B->partial, s);
         break;
     }
-    case BK_RESID_RESTRICT:  // large levels only: no work-list items
+    case BK_RESID_RESTRICT: {
+        const int grid = ni;  // the launcher clamps to occupancy
+        e = launch_bcells<T>(3, st.ops_dev, st.items_dev, ni, B->active, grid, s);
         break;
+    }
     case BK_COARSE: {
         size_t smem = 0;
         for (const BOp<T> &op : st.ops)

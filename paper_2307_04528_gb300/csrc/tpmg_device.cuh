@@ -947,10 +947,6 @@ __device__ __forceinline__ typename Pair<T>::type ld_pair(const T *p)
     return __ldg(reinterpret_cast<const typename Pair<T>::type *>(p));
 }
 
-// Coarse rows per band and owned coarse columns per warp of the fused
-// residual + restriction.
-constexpr int kRRBand = 8;
-constexpr int kRROwned = 30;
 
 // b_c = R (b - H u) on one layer k, for a band of kRRBand coarse rows
 // [Jb, Je) and one coarse column per lane: lanes 1..30 of a warp own coarse

@@ -42,6 +42,10 @@ constexpr int kBlock = 128;          // threads per block, one column per thread
 constexpr int kMaxLayers = 192;      // MG_MAX_NZ of the C ABI (checked in tpmg_api.cpp)
 constexpr int kMaxRestrictRows = 4;  // fine rows per coarse row of the restriction (checked at setup)
 constexpr int kCoarseSolveThreads = 1024;  // one-block coarsest-level solve: 32 warps (FP32 only)
+// Fused residual + restriction: coarse rows per band, coarse columns owned
+// by a warp (lanes 1..30; lanes 0 and 31 carry the neighbours).
+constexpr int kRRBand = 8;
+constexpr int kRROwned = 30;
 constexpr int kReduceSlots = 65536;  // per-block partial sums kept in the workspace
 
 // ---- launchers (tpmg_kernels.cu); all asynchronous on `s` -----------------
@@ -221,8 +225,10 @@ template <typename T>
 cudaError_t launch_bsmooth(const BOp<T> *ops, const BItem *items, int nitems, bool zero,
                            double omega, const int *active, int grid, int block, int nzmax,
                            cudaStream_t s);
-// kind: 0 residual y = a - H x, 1 restriction, 2 prolongation (cell pairs); an item is a
-// column tile over op.kz layers (op.kz == nz: column walk of the residual)
+// kind: 0 residual y = a - H x, 1 restriction, 2 prolongation (cell pairs), 3 residual and
+// restriction fused (y = R (a - H x), resid_restrict_band); an item is a column tile over
+// op.kz layers (op.kz == nz: column walk of the residual), for kind 3 a (band, layer, warp
+// block) tile with op.nblk warp blocks along longitude
 template <typename T>
 cudaError_t launch_bcells(int kind, const BOp<T> *ops, const BItem *items, int nitems,
                           const int *active, int grid, cudaStream_t s);
