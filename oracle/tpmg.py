@@ -276,6 +276,23 @@ def residual(lev: Level, b, u):
     return r
 
 
+def presmooth_residual(lev: Level, b, u, omega):
+    """The residual b - H u of u = omega H_z^{-1} b, the sweep of Eq. (1) from
+    a zero guess, written without the column couplings it cancels: since
+    H_z u = omega b, b - H u = (1 - omega) b - dH u = (1 - omega) b + the sum
+    over the four horizontal faces of T_f u_nb(f).  Evaluated in u's
+    precision, the terms added in the order east, west, north, south."""
+    one = u.dtype.type(1.0)
+    om = u.dtype.type(omega)
+    tx, ty = lev.tx, lev.ty
+    v = (one - om) * b
+    v = v + tx * np.roll(u, -1, axis=2)
+    v = v + np.roll(tx, 1, axis=2) * np.roll(u, 1, axis=2)
+    v[:, :-1, :] = v[:, :-1, :] + ty[:, :-1, :] * u[:, 1:, :]
+    v[:, 1:, :] = v[:, 1:, :] + ty[:, :-1, :] * u[:, :-1, :]
+    return v
+
+
 def column_solve(lev: Level, r):
     x = np.empty_like(r)
     getattr(_lib(), "orc_column_solve_all" + _sfx(r))(lev.nlon, lev.nlat, lev.nz,
@@ -376,7 +393,8 @@ def vcycle(levels, b, params: MGParams | None = None, l: int = 0):
     work = np.empty_like(b)
     for _ in range(p.nu1):
         smooth(lev, b, u, om, work)
-    r = residual(lev, b, u)
+    # after a single sweep from zero the residual needs no column couplings
+    r = presmooth_residual(lev, b, u, om) if p.nu1 == 1 else residual(lev, b, u)
     ec = vcycle(levels, restrict(lev, r), p, l + 1)
     prolong_add(lev, ec, u)
     for _ in range(p.nu2):
