@@ -173,7 +173,8 @@ KERNEL_WORDS = {
     # (kind, prec): (name, words per cell)
     (0, 1): ("smooth fp32 (+ <r, z>)", 8),            # u b tx ty tz m dq -> u
     (1, 1): ("smooth fp32 zero guess", 5),            # b tz m dq -> u
-    (2, 1): ("residual + restriction fp32", 6),       # u b tx ty tz h -> b_c (+ coarse write)
+    (2, 1): ("residual + restriction fp32", 6),       # u b tx ty tz h -> b_c (+ coarse write;
+                                                      # u b tx ty after a sweep from zero)
     (3, 1): ("direction update + apply fp32", 8),     # z d tx ty tz h -> d q
     (5, 1): ("prolongation + correction fp32", 2),    # u e_c -> u (+ coarse read)
     (0, 0): ("smooth fp64", 8),                       # u b tx ty tz m dq -> u
@@ -186,10 +187,10 @@ KERNEL_WORDS = {
 # DRAM bytes per fine cell of one k_smooth_dot<float> launch (ncu capture at
 # 512x384x70: 397.3 MB read + 34.8 MB written for 13,762,560 cells)
 SMOOTH_DOT_DRAM_BYTES_PER_CELL = (397.266944e6 + 34.799616e6) / (512 * 384 * 70)
-# DRAM bytes per fine cell of one k_resid_restrict<float> launch on the finest
-# level (ncu capture at 512x384x70: 353.0 MB read + 15.5 MB written for
-# 13,762,560 fine cells)
-RESID_RESTRICT_DRAM_BYTES_PER_CELL = (352.967168e6 + 15.471616e6) / (512 * 384 * 70)
+# DRAM bytes per fine cell of one k_resid_restrict<float> launch in its
+# presmoothing form on the finest level (ncu capture at 512x384x70); None
+# until captured for the current kernel
+RESID_RESTRICT_PRE_DRAM_BYTES_PER_CELL = None
 
 
 def kernel_table(H, L, N):
@@ -200,6 +201,8 @@ def kernel_table(H, L, N):
         n, ms = H.profile_read(kind, 0, prec)
         if n == 0:
             continue
+        if (kind, prec) == (2, 1) and H.params.nu1 == 1:
+            words = 4  # the presmoothing form reads u, b, tx, ty
         if (kind, prec) in ((2, 1), (5, 1)):
             words = words + coarse_ratio
         avg = ms / n
@@ -322,40 +325,44 @@ def run_ours(args):
     info_d = infos64[-1]
 
     peak, peak_kind = load_peaks()
-    # the kernel with the largest share of the mixed solve: the FP32 V-cycle's
-    # fused residual + restriction; its finest-level launches.  Algorithmic
-    # bytes: reads u, b, tx, ty, tz, h of the fine level, writes the coarse
-    # right-hand side (level-1 cells)
-    c1 = H.level_shape(1) if H.num_levels > 1 else (0, 0, 0)
-    rr_bytes = 4 * (6 * N + c1[0] * c1[1] * c1[2])
-    rr_avg_ms = rr_ms / max(rr_calls, 1)
-    achieved = rr_bytes / (rr_avg_ms * 1e-3) / 1e9 if rr_calls else None
-    rr_traffic = (RESID_RESTRICT_DRAM_BYTES_PER_CELL * N
-                  if RESID_RESTRICT_DRAM_BYTES_PER_CELL is not None else None)
-    ms_rr_all = sum(ms for _, ms in rr_all)
-    roofline = {"kernel": "k_resid_restrict<float>: residual b - H u and its restriction R = P^T "
-                          "in one pass (FP32 V-cycle), finest-level launches", "bound": "hbm",
-                "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None,
-                "traffic": rr_traffic,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                  "finest-level launch at 512x384x70, scaled per fine cell",
-                "launches_timed": rr_calls, "avg_ms": rr_avg_ms,
-                "bytes_per_launch": rr_bytes, "peak_source": peak_kind,
-                "share_of_step_all_levels": (ms_rr_all / args.steps) / ms_prof if ms_prof else None,
-                "timed_region": "repeat of the K timed mixed solves with events around "
-                                "every launch", "ms_per_step_profiled": ms_prof}
-    # the next kernel: the V-cycle's last fine-level sweep with <r, z> fused
-    # (reads u, b, tx, ty, tz, m, dq; writes u: 8 x 4 B per cell)
+    # the kernel with the largest share of the mixed solve: the V-cycle's last
+    # fine-level sweep with <r, z> fused (reads u, b, tx, ty, tz, m, dq; writes
+    # u: 8 x 4 B per cell)
     sm_bytes = 32 * N
     sm_avg_ms = sm_ms / max(sm_calls, 1)
-    sm_gbs = sm_bytes / (sm_avg_ms * 1e-3) / 1e9 if sm_calls else None
-    roofline_next = {"kernel": "k_smooth_dot<float>: fine-level block-Jacobi sweep of Eq. (1) "
-                               "with the CG inner product", "achieved": sm_gbs, "unit": "GB/s",
-                     "frac": (sm_gbs / peak) if sm_gbs else None,
-                     "traffic": SMOOTH_DOT_DRAM_BYTES_PER_CELL * N,
-                     "launches_timed": sm_calls, "avg_ms": sm_avg_ms,
-                     "bytes_per_launch": sm_bytes}
+    achieved = sm_bytes / (sm_avg_ms * 1e-3) / 1e9 if sm_calls else None
+    roofline = {"kernel": "k_smooth_dot<float>: fine-level block-Jacobi sweep of Eq. (1) "
+                          "(last sweep of the V-cycle, CG inner product fused)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": SMOOTH_DOT_DRAM_BYTES_PER_CELL * N,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at "
+                                  "512x384x70, scaled per cell to this grid",
+                "launches_timed": sm_calls, "avg_ms": sm_avg_ms,
+                "bytes_per_launch": sm_bytes, "peak_source": peak_kind,
+                "share_of_step": (sm_ms / args.steps) / ms_prof if ms_prof else None,
+                "timed_region": "repeat of the K timed mixed solves with events around "
+                                "every launch", "ms_per_step_profiled": ms_prof}
+    # the next kernel: the FP32 V-cycle's residual and restriction in one pass,
+    # finest-level launches.  After the single pre-smoothing sweep from zero it
+    # reads u, b, tx, ty (the presmoothing form); otherwise also tz and h.
+    # Both write the coarse right-hand side (level-1 cells).
+    c1 = H.level_shape(1) if H.num_levels > 1 else (0, 0, 0)
+    pre = H.params.nu1 == 1
+    rr_bytes = 4 * ((4 if pre else 6) * N + c1[0] * c1[1] * c1[2])
+    rr_avg_ms = rr_ms / max(rr_calls, 1)
+    rr_gbs = rr_bytes / (rr_avg_ms * 1e-3) / 1e9 if rr_calls else None
+    rr_cells = RESID_RESTRICT_PRE_DRAM_BYTES_PER_CELL if pre else None
+    ms_rr_all = sum(ms for _, ms in rr_all)
+    roofline_next = {"kernel": "k_resid_restrict<float>: residual and its restriction R = P^T in "
+                               "one pass (" + ("presmoothing form" if pre else "full stencil") +
+                               "), finest-level launches", "achieved": rr_gbs, "unit": "GB/s",
+                     "frac": (rr_gbs / peak) if rr_gbs else None,
+                     "traffic": rr_cells * N if rr_cells is not None else None,
+                     "launches_timed": rr_calls, "avg_ms": rr_avg_ms,
+                     "bytes_per_launch": rr_bytes,
+                     "share_of_step_all_levels": (ms_rr_all / args.steps) / ms_prof
+                     if ms_prof else None}
     res_avg = res_ms / max(res_calls, 1)
 
     out = {

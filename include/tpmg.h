@@ -187,6 +187,15 @@ int mg_coarse_solve(mg_handle *h, int prec, const void *b, void *out, void *stre
 int mg_level_residual_restrict(mg_handle *h, int level, int prec, const void *b, const void *u,
                                void *bc, void *stream);
 
+/* bc = R_l ((1 - omega) b + the horizontal couplings of u): the restricted
+ * residual b - H_l u for u the sweep of Eq. (1) from zero on b, u = omega
+ * H_z^{-1} b, written without the column couplings H_z u = omega b cancels
+ * (the V-cycle's form when nu1 = 1).  b, u: level l; bc: level l+1.
+ * Unaligned b or u are first copied into the handle's level-l work vectors
+ * (calls on one handle must not overlap).  MG_ERR_ARG on the coarsest level. */
+int mg_level_presmooth_restrict(mg_handle *h, int level, int prec, const void *b, const void *u,
+                                void *bc, void *stream);
+
 /* One smoother sweep of Eq. (1) on level l:
  *   u_out = u_in + omega H_z^{-1} (b - H u_in), evaluated as
  *   (1 - omega) u_in + omega H_z^{-1} (b - dH u_in).

@@ -90,6 +90,7 @@ def load() -> ctypes.CDLL:
         "mg_level_relax": (I, [H, I, I, I, P, P, P]),
         "mg_coarse_solve": (I, [H, I, P, P, P]),
         "mg_level_residual_restrict": (I, [H, I, I, P, P, P, P]),
+        "mg_level_presmooth_restrict": (I, [H, I, I, P, P, P, P]),
         "mg_level_restrict": (I, [H, I, I, P, P, P]),
         "mg_level_prolong_add": (I, [H, I, I, P, P, P]),
         "mg_fp32_scale": (D, [H]),

@@ -649,10 +649,24 @@ static int vcycle_level(mg_handle *H, int l, const T *b, T *out, T *scratch, T *
         std::swap(cur, oth);
     }
     LevelHost &c = H->lev[l + 1];
-    if (sizeof(T) == 4 && resid_restrict_fits(b, cur, sizeof(T), v.linkdev.nlat_c)) {
-        // FP32: one pass, the residual never stored (the FP64 stencil is
-        // bound by FP64 arithmetic, which the fused pass would increase)
-        KRUN(K_RESID, l, P, launch_resid_restrict<T>(D, v.linkdev, b, cur, Vec<T>::b(c), s));
+    // After a single sweep from zero the residual is (1 - omega) b plus the
+    // horizontal couplings (both precisions); after more sweeps the full
+    // stencil (FP32 fused; FP64, bound by FP64 arithmetic, in two passes).
+    const bool pre = H->p.nu1 == 1;
+    if (pre || sizeof(T) == 4) {
+        const T *bb = b, *uu = cur;
+        if (!resid_restrict_fits(b, cur, sizeof(T))) {  // a caller's unaligned vector
+            if ((uintptr_t)b % (2 * sizeof(T))) {
+                CU(cudaMemcpyAsync(rbuf, b, v.n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+                bb = rbuf;
+            }
+            if ((uintptr_t)cur % (2 * sizeof(T))) {  // cur is out, oth the level's scratch
+                CU(cudaMemcpyAsync(oth, cur, v.n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+                uu = oth;
+            }
+        }
+        KRUN(K_RESID, l, P,
+             launch_resid_restrict<T>(D, v.linkdev, bb, uu, Vec<T>::b(c), s, nullptr, pre, om));
     } else {
         KRUN(K_RESID, l, P, launch_stencil<T>(D, 1, b, cur, rbuf, nullptr, s));
         KRUN(K_RESTRICT, l, P, launch_restrict<T>(D, v.linkdev, rbuf, Vec<T>::b(c), s));
@@ -1106,7 +1120,7 @@ extern "C" int mg_level_residual_restrict(mg_handle *H, int level, int prec, con
     cudaStream_t s = (cudaStream_t)stream;
     LevelHost &v = H->lev[level];
     const size_t vb = prec == MG_PREC_FP64 ? 8 : 4;
-    if (resid_restrict_fits(b, u, vb, v.linkdev.nlat_c)) {
+    if (resid_restrict_fits(b, u, vb)) {
         if (prec == MG_PREC_FP64)
             KRUN(K_RESID, level, 0,
                  launch_resid_restrict<double>(dev<double>(v), v.linkdev, (const double *)b,
@@ -1124,6 +1138,39 @@ extern "C" int mg_level_residual_restrict(mg_handle *H, int level, int prec, con
     }
     CHK(level_op<float>(H, level, 1, b, u, Vec<float>::r(v), s));
     return level_op<float>(H, level, 3, Vec<float>::r(v), nullptr, bc, s);
+}
+
+template <typename T>
+static int presmooth_restrict(mg_handle *H, int level, const T *b, const T *u, T *bc,
+                              cudaStream_t s)
+{
+    LevelHost &v = H->lev[level];
+    const T *bb = b, *uu = u;
+    if ((uintptr_t)b % (2 * sizeof(T))) {
+        CU(cudaMemcpyAsync(Vec<T>::r(v), b, v.n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        bb = Vec<T>::r(v);
+    }
+    if ((uintptr_t)u % (2 * sizeof(T))) {
+        CU(cudaMemcpyAsync(Vec<T>::w(v), u, v.n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        uu = Vec<T>::w(v);
+    }
+    KRUN(K_RESID, level, prec_of<T>(),
+         launch_resid_restrict<T>(dev<T>(v), v.linkdev, bb, uu, bc, s, nullptr, true,
+                                  H->p.omega));
+    return MG_OK;
+}
+
+extern "C" int mg_level_presmooth_restrict(mg_handle *H, int level, int prec, const void *b,
+                                           const void *u, void *bc, void *stream)
+{
+    CHK(level_check(H, level, prec, true));
+    if (!b || !u || !bc || bc == b || bc == u) return fail(MG_ERR_ARG, "bad buffers");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == MG_PREC_FP64)
+        return presmooth_restrict<double>(H, level, (const double *)b, (const double *)u,
+                                          (double *)bc, s);
+    return presmooth_restrict<float>(H, level, (const float *)b, (const float *)u, (float *)bc,
+                                     s);
 }
 
 extern "C" int mg_coarse_solve(mg_handle *H, int prec, const void *b, void *out, void *stream)

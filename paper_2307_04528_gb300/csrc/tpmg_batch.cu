@@ -142,19 +142,19 @@ cudaError_t bsmooth_prepare()
 template <typename T, int KIND>
 __global__ void __launch_bounds__(kBlock)
 k_bcells(const BOp<T> *__restrict__ ops, const BItem *__restrict__ items, int nitems,
-         const int *__restrict__ active)
+         const int *__restrict__ active, T om1)
 {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const BItem item = items[it];
         const BOp<T> &op = ops[item.op];
         if (active && !active[op.sys]) continue;
-        if (KIND == 3) {  // fused residual + restriction: tile = (band * nz + k) * nblk + xb
+        if (KIND >= 3) {  // fused residual + restriction: tile = (band * nz + k) * nblk + xb
             const int xb = item.tile % op.nblk, rest = item.tile / op.nblk;
             const int k = rest % op.L.nz, band = rest / op.L.nz;
             const int warp = (xb * blockDim.x + threadIdx.x) >> 5;
             if (warp * kRROwned < op.L.nlon / 2)  // whole warps
-                resid_restrict_band<T>(op.L, op.K, op.a, op.x, op.y, warp, threadIdx.x & 31,
-                                       band * kRRBand, k);
+                resid_restrict_band<T, KIND == 4>(op.L, op.K, op.a, op.x, op.y, warp,
+                                                  threadIdx.x & 31, band * kRRBand, k, om1);
             continue;
         }
         const int zc = item.tile / op.nblk;
@@ -176,18 +176,21 @@ k_bcells(const BOp<T> *__restrict__ ops, const BItem *__restrict__ items, int ni
 
 template <typename T>
 cudaError_t launch_bcells(int kind, const BOp<T> *ops, const BItem *items, int nitems,
-                          const int *active, int grid, cudaStream_t s)
+                          const int *active, int grid, cudaStream_t s, double omega)
 {
     if (nitems <= 0) return cudaSuccess;
     const void *k = kind == 0   ? (const void *)k_bcells<T, 0>
                     : kind == 1 ? (const void *)k_bcells<T, 1>
                     : kind == 2 ? (const void *)k_bcells<T, 2>
-                                : (const void *)k_bcells<T, 3>;
+                    : kind == 3 ? (const void *)k_bcells<T, 3>
+                                : (const void *)k_bcells<T, 4>;
     grid = std::min(grid, resident_grid(k, kBlock, 0));
-    if (kind == 0) k_bcells<T, 0><<<grid, kBlock, 0, s>>>(ops, items, nitems, active);
-    else if (kind == 1) k_bcells<T, 1><<<grid, kBlock, 0, s>>>(ops, items, nitems, active);
-    else if (kind == 2) k_bcells<T, 2><<<grid, kBlock, 0, s>>>(ops, items, nitems, active);
-    else k_bcells<T, 3><<<grid, kBlock, 0, s>>>(ops, items, nitems, active);
+    const T om1 = T(1) - (T)omega;
+    if (kind == 0) k_bcells<T, 0><<<grid, kBlock, 0, s>>>(ops, items, nitems, active, om1);
+    else if (kind == 1) k_bcells<T, 1><<<grid, kBlock, 0, s>>>(ops, items, nitems, active, om1);
+    else if (kind == 2) k_bcells<T, 2><<<grid, kBlock, 0, s>>>(ops, items, nitems, active, om1);
+    else if (kind == 3) k_bcells<T, 3><<<grid, kBlock, 0, s>>>(ops, items, nitems, active, om1);
+    else k_bcells<T, 4><<<grid, kBlock, 0, s>>>(ops, items, nitems, active, om1);
     return cudaGetLastError();
 }
 
@@ -445,7 +448,7 @@ cudaError_t launch_bfinalize(const double *partial, const int *beg, const int *e
     template cudaError_t launch_bsmooth_dot<T>(const BOp<T> *, const BItem *, int, double,        \
                                                const int *, int, int, int, double *, cudaStream_t); \
     template cudaError_t launch_bcells<T>(int, const BOp<T> *, const BItem *, int, const int *,   \
-                                          int, cudaStream_t);                                     \
+                                          int, cudaStream_t, double);                             \
     template cudaError_t launch_bstencil_red<T>(int, const BOp<T> *, const BItem *, int,          \
                                                 double *, const int *, int, cudaStream_t);        \
     template cudaError_t launch_bvec<T>(int, const BVec<T> *, const BItem *, int,                 \

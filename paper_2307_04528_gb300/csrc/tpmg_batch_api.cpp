@@ -228,9 +228,9 @@ void gen_level(mg_handle *H, int sys, int l, int Lmax, const T *b, T *out, T *sc
         std::swap(cur, oth);
     }
     LevelHost &c = H->lev[l + 1];
-    if (sizeof(T) == 4 && resid_restrict_fits(b, cur, sizeof(T), v.linkdev.nlat_c)) {
-        // FP32: the fused pass (the single-system kernel on large levels,
-        // the work list on the others)
+    if ((H->p.nu1 == 1 || sizeof(T) == 4) && resid_restrict_fits(b, cur, sizeof(T))) {
+        // the fused pass as in the single-system V-cycle (the single-system
+        // kernel on large levels, the work list on the others)
         push(down, BK_RESID_RESTRICT, b, cur, Vec<T>::b(c), D, v.linkdev);
     } else {
         push(down, BK_RESID, b, cur, rbuf, D, nolink);
@@ -712,7 +712,8 @@ static int run_vstep(mg_batch *B, StepHost<T> &st, cudaStream_t s)
     }
     case BK_RESID_RESTRICT: {
         const int grid = ni;  // the launcher clamps to occupancy
-        e = launch_bcells<T>(3, st.ops_dev, st.items_dev, ni, B->active, grid, s);
+        e = launch_bcells<T>(B->p.nu1 == 1 ? 4 : 3, st.ops_dev, st.items_dev, ni, B->active,
+                             grid, s, B->p.omega);
         break;
     }
     case BK_COARSE: {
@@ -750,7 +751,8 @@ static int run_vstep(mg_batch *B, StepHost<T> &st, cudaStream_t s)
             break;
         case BK_RESTRICT: e = launch_restrict<T>(op.L, op.K, op.a, op.y, s, flag); break;
         case BK_RESID_RESTRICT:
-            e = launch_resid_restrict<T>(op.L, op.K, op.a, op.x, op.y, s, flag);
+            e = launch_resid_restrict<T>(op.L, op.K, op.a, op.x, op.y, s, flag, B->p.nu1 == 1,
+                                         B->p.omega);
             break;
         default: e = launch_prolong_add<T>(op.L, op.K, op.a, op.y, s, flag); break;
         }

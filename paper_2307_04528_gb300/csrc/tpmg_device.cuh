@@ -968,11 +968,17 @@ __device__ __forceinline__ typename Pair<T>::type ld_pair(const T *p)
 // fine rows shared by two bands are computed in both.  All 32 lanes of the
 // warp call it (whole warps past the last column return together); b, u and
 // the coefficient arrays aligned to two values.
-template <typename T>
+// PRE: u is the sweep of Eq. (1) from zero, u = omega H_z^{-1} b, whose
+// residual is (1 - omega) b plus the four horizontal couplings of u (H_z u =
+// omega b cancels everything else; om1 = 1 - omega): the same walk without
+// h, t_z and the layers above and below, terms added east, west, north,
+// south.
+template <typename T, bool PRE = false>
 __device__ __forceinline__ void resid_restrict_band(const LevelDev<T> &F, const LinkDev &K,
                                                     const T *__restrict__ b,
                                                     const T *__restrict__ u, T *__restrict__ bc,
-                                                    int warp, int lane, int Jb, int k)
+                                                    int warp, int lane, int Jb, int k,
+                                                    T om1 = T(0))
 {
     using P2 = typename Pair<T>::type;
     constexpr unsigned kAll = 0xffffffffu;
@@ -1005,30 +1011,45 @@ __device__ __forceinline__ void resid_restrict_band(const LevelDev<T> &F, const 
         const bool hasN = j + 1 < nlat, hasS = j > 0;
         const size_t oj = (size_t)j * nf;
         const P2 Un = hasN ? ld_pair(uk + oj + nf) : zero;
-        const P2 B = ld_pair(bk + oj), Hh = ld_pair(hk + oj), TX = ld_pair(txk + oj);
+        const P2 B = ld_pair(bk + oj), TX = ld_pair(txk + oj);
         const P2 TYN = hasN ? ld_pair(tyk + oj) : zero;
-        const P2 TZ = ld_pair(tzk + oj);
-        const P2 TZD = dn ? ld_pair(tzd + oj) : zero;
-        const P2 UU = up ? ld_pair(uu + oj) : zero;
-        const P2 UD = dn ? ld_pair(ud + oj) : zero;
         const T uw = __shfl_up_sync(kAll, Uc.y, 1);    // u[2I-1]
         const T ue = __shfl_down_sync(kAll, Uc.x, 1);  // u[2I+2]
         const T txw = __shfl_up_sync(kAll, TX.y, 1);   // t_x[2I-1], west face of 2I
-        T v0 = Hh.x * Uc.x;
-        v0 = fma(TX.x, Uc.x - Uc.y, v0);
-        v0 = fma(txw, Uc.x - uw, v0);
-        if (hasN) v0 = fma(TYN.x, Uc.x - Un.x, v0);
-        if (hasS) v0 = fma(Tys.x, Uc.x - Us.x, v0);
-        v0 = fma(TZ.x, Uc.x - UU.x, v0);
-        v0 = fma(TZD.x, Uc.x - UD.x, v0);
-        T v1 = Hh.y * Uc.y;
-        v1 = fma(TX.y, Uc.y - ue, v1);
-        v1 = fma(TX.x, Uc.y - Uc.x, v1);
-        if (hasN) v1 = fma(TYN.y, Uc.y - Un.y, v1);
-        if (hasS) v1 = fma(Tys.y, Uc.y - Us.y, v1);
-        v1 = fma(TZ.y, Uc.y - UU.y, v1);
-        v1 = fma(TZD.y, Uc.y - UD.y, v1);
-        const T r0 = B.x - v0, r1 = B.y - v1;
+        T r0, r1;
+        if (PRE) {
+            r0 = om1 * B.x;
+            r0 = fma(TX.x, Uc.y, r0);
+            r0 = fma(txw, uw, r0);
+            if (hasN) r0 = fma(TYN.x, Un.x, r0);
+            if (hasS) r0 = fma(Tys.x, Us.x, r0);
+            r1 = om1 * B.y;
+            r1 = fma(TX.y, ue, r1);
+            r1 = fma(TX.x, Uc.x, r1);
+            if (hasN) r1 = fma(TYN.y, Un.y, r1);
+            if (hasS) r1 = fma(Tys.y, Us.y, r1);
+        } else {
+            const P2 Hh = ld_pair(hk + oj), TZ = ld_pair(tzk + oj);
+            const P2 TZD = dn ? ld_pair(tzd + oj) : zero;
+            const P2 UU = up ? ld_pair(uu + oj) : zero;
+            const P2 UD = dn ? ld_pair(ud + oj) : zero;
+            T v0 = Hh.x * Uc.x;
+            v0 = fma(TX.x, Uc.x - Uc.y, v0);
+            v0 = fma(txw, Uc.x - uw, v0);
+            if (hasN) v0 = fma(TYN.x, Uc.x - Un.x, v0);
+            if (hasS) v0 = fma(Tys.x, Uc.x - Us.x, v0);
+            v0 = fma(TZ.x, Uc.x - UU.x, v0);
+            v0 = fma(TZD.x, Uc.x - UD.x, v0);
+            T v1 = Hh.y * Uc.y;
+            v1 = fma(TX.y, Uc.y - ue, v1);
+            v1 = fma(TX.x, Uc.y - Uc.x, v1);
+            if (hasN) v1 = fma(TYN.y, Uc.y - Un.y, v1);
+            if (hasS) v1 = fma(Tys.y, Uc.y - Us.y, v1);
+            v1 = fma(TZ.y, Uc.y - UU.y, v1);
+            v1 = fma(TZD.y, Uc.y - UD.y, v1);
+            r0 = B.x - v0;
+            r1 = B.y - v1;
+        }
         const T rw = __shfl_up_sync(kAll, r1, 1);    // r[2I-1]
         const T re = __shfl_down_sync(kAll, r0, 1);  // r[2I+2]
         const T sv = fma(q1, rw + re, q3 * (r0 + r1));

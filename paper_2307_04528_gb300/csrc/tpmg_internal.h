@@ -96,12 +96,15 @@ cudaError_t set_dynamic_smem_limit(const void *kernel, int lim);
 // value_bytes-wide values
 size_t smooth_smem_bytes(int nz, size_t value_bytes);
 
-// b_c = R (b - H u) in one pass (FP32 V-cycle); b and u aligned to two
-// values and at most 65535 bands of coarse rows (resid_restrict_fits).
-bool resid_restrict_fits(const void *b, const void *u, size_t value_bytes, int nlat_c);
+// b_c = R (b - H u) in one pass; b and u aligned to two values
+// (resid_restrict_fits).
+bool resid_restrict_fits(const void *b, const void *u, size_t value_bytes);
+// presmooth: u is the sweep of Eq. (1) from zero with this omega, and the
+// residual is taken as (1 - omega) b plus u's horizontal couplings.
 template <typename T>
 cudaError_t launch_resid_restrict(const LevelDev<T> &F, const LinkDev &K, const T *b, const T *u,
-                                  T *bc, cudaStream_t s, const int *flag = nullptr);
+                                  T *bc, cudaStream_t s, const int *flag = nullptr,
+                                  bool presmooth = false, double omega = 0.0);
 template <typename T>
 cudaError_t launch_restrict(const LevelDev<T> &F, const LinkDev &K, const T *r, T *bc,
                             cudaStream_t s, const int *flag = nullptr);
@@ -226,12 +229,13 @@ cudaError_t launch_bsmooth(const BOp<T> *ops, const BItem *items, int nitems, bo
                            double omega, const int *active, int grid, int block, int nzmax,
                            cudaStream_t s);
 // kind: 0 residual y = a - H x, 1 restriction, 2 prolongation (cell pairs), 3 residual and
-// restriction fused (y = R (a - H x), resid_restrict_band); an item is a column tile over
-// op.kz layers (op.kz == nz: column walk of the residual), for kind 3 a (band, layer, warp
-// block) tile with op.nblk warp blocks along longitude
+// restriction fused (y = R (a - H x), resid_restrict_band), 4 the same after a sweep from
+// zero with this omega (the presmoothing form); an item is a column tile over op.kz layers
+// (op.kz == nz: column walk of the residual), for kinds 3 and 4 a (band, layer, warp block)
+// tile with op.nblk warp blocks along longitude
 template <typename T>
 cudaError_t launch_bcells(int kind, const BOp<T> *ops, const BItem *items, int nitems,
-                          const int *active, int grid, cudaStream_t s);
+                          const int *active, int grid, cudaStream_t s, double omega = 0.0);
 // Column-loop stencil with one partial sum per item (mode 1: residual + sum r^2;
 // mode 0: apply + sum x*y).
 template <typename T>

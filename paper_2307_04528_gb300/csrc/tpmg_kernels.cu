@@ -16,6 +16,7 @@
 // FP64 ops per cell) and reads precomputed column factors.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "tpmg_device.cuh"
@@ -376,32 +377,41 @@ k_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ r, T *__restrict__ bc
 // the layers before the bands in launch order, the blocks of one band at
 // neighbouring layers run together and share the planes above and below in
 // L2 (bands before layers: 0.662 instead of 0.614 ms at 1536 x 1152 x 70).
-template <typename T>
+// PRE: u is the sweep from zero (the residual's presmoothing form).  band0:
+// first band of this launch (more than 65535 bands take several launches).
+template <typename T, bool PRE>
 __global__ void __launch_bounds__(kBlock)
 k_resid_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ b, const T *__restrict__ u,
-                 T *__restrict__ bc, const int *__restrict__ flag)
+                 T *__restrict__ bc, T om1, int band0, const int *__restrict__ flag)
 {
     if (flag && !*flag) return;
     const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     if (warp * kRROwned >= F.nlon / 2) return;  // whole warps
-    resid_restrict_band<T>(F, K, b, u, bc, warp, threadIdx.x & 31, blockIdx.z * kRRBand,
-                           blockIdx.y);
+    resid_restrict_band<T, PRE>(F, K, b, u, bc, warp, threadIdx.x & 31,
+                                (band0 + (int)blockIdx.z) * kRRBand, blockIdx.y, om1);
 }
 
-bool resid_restrict_fits(const void *b, const void *u, size_t value_bytes, int nlat_c)
+bool resid_restrict_fits(const void *b, const void *u, size_t value_bytes)
 {
-    return (uintptr_t)b % (2 * value_bytes) == 0 && (uintptr_t)u % (2 * value_bytes) == 0 &&
-           (nlat_c + kRRBand - 1) / kRRBand <= 65535;  // bands on the grid's z axis
+    return (uintptr_t)b % (2 * value_bytes) == 0 && (uintptr_t)u % (2 * value_bytes) == 0;
 }
 
 template <typename T>
 cudaError_t launch_resid_restrict(const LevelDev<T> &F, const LinkDev &K, const T *b, const T *u,
-                                  T *bc, cudaStream_t s, const int *flag)
+                                  T *bc, cudaStream_t s, const int *flag, bool presmooth,
+                                  double omega)
 {
     const int nc = F.nlon / 2;
     const int warps = (nc + kRROwned - 1) / kRROwned;
-    const dim3 grid((warps * 32 + kBlock - 1) / kBlock, F.nz, (K.nlat_c + kRRBand - 1) / kRRBand);
-    k_resid_restrict<T><<<grid, kBlock, 0, s>>>(F, K, b, u, bc, flag);
+    const int bands = (K.nlat_c + kRRBand - 1) / kRRBand;
+    const T om1 = T(1) - (T)omega;
+    for (int band0 = 0; band0 < bands; band0 += 65535) {  // grid z limit
+        const dim3 grid((warps * 32 + kBlock - 1) / kBlock, F.nz, std::min(65535, bands - band0));
+        if (presmooth)
+            k_resid_restrict<T, true><<<grid, kBlock, 0, s>>>(F, K, b, u, bc, om1, band0, flag);
+        else
+            k_resid_restrict<T, false><<<grid, kBlock, 0, s>>>(F, K, b, u, bc, om1, band0, flag);
+    }
     return cudaGetLastError();
 }
 
@@ -811,7 +821,8 @@ cudaError_t launch_coeff_grad(int nlon, int nlat, int nz, const double *lam, con
     template int launch_smooth_dot<T>(const LevelDev<T> &, const T *, const T *, T *, double,      \
                                       double *, cudaStream_t, const int *);                       \
     template cudaError_t launch_resid_restrict<T>(const LevelDev<T> &, const LinkDev &, const T *, \
-                                                  const T *, T *, cudaStream_t, const int *);     \
+                                                  const T *, T *, cudaStream_t, const int *, bool, \
+                                                  double);                                        \
     template cudaError_t launch_restrict<T>(const LevelDev<T> &, const LinkDev &, const T *, T *,  \
                                             cudaStream_t, const int *);                           \
     template cudaError_t launch_prolong_add<T>(const LevelDev<T> &, const LinkDev &, const T *,    \

@@ -28,6 +28,7 @@ KERNELS = {
     "apply32": (1, "apply", 6),
     "restrict32": (1, "restrict", None),
     "resid_restrict32": (1, "resid_restrict", None),
+    "presmooth_restrict32": (1, "presmooth_restrict", None),
     "prolong32": (1, "prolong", None),
     "smooth64": (0, "smooth", 8),
     "smooth64_zero": (0, "smooth0", 5),
@@ -77,6 +78,8 @@ def main():
             return H.level_restrict(0, u, prec=prec)
         if op == "resid_restrict":
             return H.level_residual_restrict(0, b, u, prec=prec)
+        if op == "presmooth_restrict":
+            return H.level_presmooth_restrict(0, b, u, prec=prec)
         return H.level_prolong_add(0, ec, u, prec=prec)
 
     run()
@@ -90,8 +93,8 @@ def main():
     ms = ev[0].elapsed_time(ev[1]) / args.launches
     n = nz * nlat * nlon
     out = {"kernel": args.kernel, "shape": args.shape, "avg_ms": ms}
-    if op == "resid_restrict":  # 6 fine arrays read, the coarse right-hand side written
-        words = 6 + cshape[0] * cshape[1] * cshape[2] / n
+    if op in ("resid_restrict", "presmooth_restrict"):  # 6 (4) fine arrays read, coarse written
+        words = (6 if op == "resid_restrict" else 4) + cshape[0] * cshape[1] * cshape[2] / n
     if words:
         nbytes = words * (4 if prec == 1 else 8) * n
         out.update(alg_bytes=nbytes, gbs=nbytes / (ms * 1e-3) / 1e9)

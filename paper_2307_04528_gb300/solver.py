@@ -181,6 +181,15 @@ class MGHandle:
                                                     _ptr(bc), _stream()))
         return bc
 
+    def level_presmooth_restrict(self, level, b, u, prec=L.MG_PREC_FP64):
+        """R ((1 - omega) b + horizontal couplings of u): the restricted residual
+        after the sweep from zero u = omega H_z^{-1} b."""
+        shp = self.level_shape(level + 1)
+        bc = torch.empty(shp, dtype=b.dtype, device=b.device)
+        L.check(self.lib.mg_level_presmooth_restrict(self._hh, level, prec, _ptr(b), _ptr(u),
+                                                     _ptr(bc), _stream()))
+        return bc
+
     def coarse_solve(self, b, prec=L.MG_PREC_FP64):
         """The V-cycle's coarsest-level solve (block-Jacobi sweeps or PCG, as
         configured) applied to b on the coarsest level."""
