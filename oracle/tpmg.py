@@ -41,6 +41,7 @@ def _lib():
         for sfx, a, real in (("_d", d, ctypes.c_double), ("_f", f, ctypes.c_float)):
             getattr(lib, "orc_apply" + sfx).argtypes = [I, I, I, a, a, a, a, a, a]
             getattr(lib, "orc_residual" + sfx).argtypes = [I, I, I, a, a, a, a, a, a, a]
+            getattr(lib, "orc_presmooth_residual" + sfx).argtypes = [I, I, I, a, a, a, a, real, a]
             getattr(lib, "orc_smooth" + sfx).argtypes = [I, I, I, a, a, a, a, a, a, real, a]
             getattr(lib, "orc_column_solve_all" + sfx).argtypes = [I, I, I, a, a, a, a, a, a]
             getattr(lib, "orc_restrict" + sfx).argtypes = [I, I, I, I, ip, d, ip, d, a, a]
@@ -282,15 +283,11 @@ def presmooth_residual(lev: Level, b, u, omega):
     H_z u = omega b, b - H u = (1 - omega) b - dH u = (1 - omega) b + the sum
     over the four horizontal faces of T_f u_nb(f).  Evaluated in u's
     precision, the terms added in the order east, west, north, south."""
-    one = u.dtype.type(1.0)
-    om = u.dtype.type(omega)
-    tx, ty = lev.tx, lev.ty
-    v = (one - om) * b
-    v = v + tx * np.roll(u, -1, axis=2)
-    v = v + np.roll(tx, 1, axis=2) * np.roll(u, 1, axis=2)
-    v[:, :-1, :] = v[:, :-1, :] + ty[:, :-1, :] * u[:, 1:, :]
-    v[:, 1:, :] = v[:, 1:, :] + ty[:, :-1, :] * u[:, :-1, :]
-    return v
+    r = np.empty_like(u)
+    om1 = u.dtype.type(1.0) - u.dtype.type(omega)
+    getattr(_lib(), "orc_presmooth_residual" + _sfx(u))(lev.nlon, lev.nlat, lev.nz, lev.tx,
+                                                         lev.ty, b, u, om1, r)
+    return r
 
 
 def column_solve(lev: Level, r):

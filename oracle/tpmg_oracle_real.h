@@ -51,6 +51,28 @@ void SFX(orc_residual)(int nlon, int nlat, int nz,
             }
 }
 
+/* r = b - H u for u = omega H_z^{-1} b (the sweep of Eq. (1) from zero):
+ * H_z u = omega b leaves (1 - omega) b plus the four horizontal couplings
+ * of u, added east, west, north, south (om1 = 1 - omega). */
+void SFX(orc_presmooth_residual)(int nlon, int nlat, int nz, const REAL *tx, const REAL *ty,
+                                 const REAL *b, const REAL *u, REAL om1, REAL *r)
+{
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < nlat; ++j)
+            for (int i = 0; i < nlon; ++i) {
+                size_t c = IX(k, j, i);
+                int ie = (i + 1) % nlon;
+                int iw = (i + nlon - 1) % nlon;
+                REAL v = om1 * b[c];
+                v += tx[c] * u[IX(k, j, ie)];
+                v += tx[IX(k, j, iw)] * u[IX(k, j, iw)];
+                if (j + 1 < nlat) v += ty[c] * u[IX(k, j + 1, i)];
+                if (j > 0) v += ty[IX(k, j - 1, i)] * u[IX(k, j - 1, i)];
+                r[c] = v;
+            }
+}
+
 /*
  * x = H_z^{-1} r for the column (j, i) (Section 2.1: H_z holds the diagonal of
  * H and the couplings within a vertical column).
