@@ -67,8 +67,8 @@ void SFX(orc_presmooth_residual)(int nlon, int nlat, int nz, const REAL *tx, con
                 REAL v = om1 * b[c];
                 v += tx[c] * u[IX(k, j, ie)];
                 v += tx[IX(k, j, iw)] * u[IX(k, j, iw)];
-                if (j + 1 < nlat) v += ty[c] * u[IX(k, j + 1, i)];
-                if (j > 0) v += ty[IX(k, j - 1, i)] * u[IX(k, j - 1, i)];
+                if (j + 1 < nlat) v += ty[IX(k, j, i)] * u[IX(k, j + 1, i)];  /* north */
+                if (j > 0) v += ty[IX(k, j - 1, i)] * u[IX(k, j - 1, i)];     /* south */
                 r[c] = v;
             }
 }

@@ -44,6 +44,10 @@ MUTANTS = [
      "txc[c] *= sx;", "txc[c] *= 1.0;"),
     ("coarse Helmholtz term misses a child", "tpmg_oracle.c",
      "hc[c] += h[f];", "if (i % 2 == 0) hc[c] += h[f];"),
+    ("presmoothing residual misses the (1 - omega) factor", "tpmg_oracle_real.h",
+     "REAL v = om1 * b[c];", "REAL v = b[c];"),
+    ("presmoothing residual misses the north coupling", "tpmg_oracle_real.h",
+     "if (j + 1 < nlat) v += ty[IX(k, j, i)] * u[IX(k, j + 1, i)];  /* north */", ""),
     ("gradient face term sign", "tpmg_oracle.c",
      "gtx[c] = -(lam[c] - lam[e]) * (x[c] - x[e]);", "gtx[c] = (lam[c] - lam[e]) * (x[c] - x[e]);"),
 ]
@@ -58,6 +62,7 @@ PINS = [
     pins.test_vcycle_symmetric_positive_linear,
     pins.test_convergence_factor_on_small_workload,
     pins.test_gradient_matches_dense_lu_and_finite_differences,
+    pins.test_presmooth_residual_is_the_exact_residual_of_the_sweep,
 ]
 
 
