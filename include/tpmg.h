@@ -168,7 +168,8 @@ int mg_level_coeffs(mg_handle *h, int level, double *tx, double *ty, double *tz,
  * copies, see mg_fp32_scale). */
 int mg_level_apply(mg_handle *h, int level, int prec, const void *x, void *y, void *stream);
 
-/* r = b - H_l u. */
+/* r = b - H_l u, H_l in the flux form of Section 2's operator (the
+ * Helmholtz term plus T_f (u_c - u_nb) over the six faces). */
 int mg_level_residual(mg_handle *h, int level, int prec, const void *b, const void *u,
                       void *r, void *stream);
 
@@ -178,9 +179,11 @@ int mg_level_residual(mg_handle *h, int level, int prec, const void *b, const vo
  * vectors: calls on one handle must not overlap. */
 int mg_coarse_solve(mg_handle *h, int prec, const void *b, void *out, void *stream);
 
-/* bc = R_l (b - H_l u): the residual restricted to level l+1 in one pass,
- * the residual itself never stored (the FP32 V-cycle's form; equal term for
- * term to mg_level_residual followed by mg_level_restrict).  b, u: level l;
+/* bc = R_l (b - H_l u): the residual restricted to level l+1 in one pass
+ * (Section 2's V-cycle: restrict the residual to the coarse grid), the
+ * residual itself never stored (the FP32 V-cycle's form after more than one
+ * pre-smoothing sweep; equal term for term to mg_level_residual followed by
+ * mg_level_restrict).  b, u: level l;
  * bc: level l+1, aliasing neither.  Buffers not aligned to two values take
  * the two passes through the handle's level-l residual vector (calls on one
  * handle must not overlap).  MG_ERR_ARG on the coarsest level. */
@@ -219,11 +222,14 @@ int mg_level_relax(mg_handle *h, int level, int prec, int sweeps, const void *b,
 int mg_level_smooth_dot(mg_handle *h, int level, int prec, const void *b, const void *u_in,
                         void *u_out, double *dot, void *stream);
 
-/* bc = R r: restriction from level l to l+1 (R = P^T). */
+/* bc = R r: restriction from level l to l+1 (R = P^T; the coarse grid of
+ * Section 2.2: longitude halved, latitude rows merged where the anisotropy
+ * allows). */
 int mg_level_restrict(mg_handle *h, int level, int prec, const void *r, void *bc,
                       void *stream);
 
-/* u += P ec: bilinear horizontal prolongation from level l+1 to level l. */
+/* u += P ec: bilinear horizontal prolongation from level l+1 to level l
+ * (the coarse-grid correction of Section 2's V-cycle). */
 int mg_level_prolong_add(mg_handle *h, int level, int prec, const void *ec, void *u,
                          void *stream);
 
@@ -231,7 +237,7 @@ int mg_level_prolong_add(mg_handle *h, int level, int prec, const void *ec, void
  * scaled (FP32 level l holds c * coefficients); 0 when not built. */
 double mg_fp32_scale(const mg_handle *h);
 
-/* ---- batched ensemble of independent systems (spec batching form).
+/* ---- batched ensemble of independent systems.
  * n systems of possibly different shapes share one device workspace and the
  * same parameters; every V-cycle step and fine-level vector operation of all
  * systems is one persistent-kernel launch over a precomputed work list of
