@@ -2,7 +2,7 @@
  * tpmg.h -- C ABI of the GB300 tensor-product multigrid library (libtpmg.so).
  *
  * Solves H u = b for the pressure-correction system of the paper (Section 2:
- * "H is a sparse, discrete Laplacian-like matrix") on a cell-centred
+ * a sparse discrete operator of Laplacian type) on a cell-centred
  * latitude-longitude grid of nz layers, nlat latitude rows and nlon
  * longitudes, with the tensor-product multigrid of Sections 2.1-2.3: a
  * vertical line (block-Jacobi) smoother, Eq. (1); horizontal-only coarsening

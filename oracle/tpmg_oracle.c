@@ -16,7 +16,7 @@
  *   tx[k,j,i]: face (i, i+1 mod nlon)   ty[k,j,i]: face (j, j+1), 0 on j = nlat-1
  *   tz[k,j,i]: face (k, k+1), 0 on k = nz-1   h[k,j,i]: Helmholtz term
  *
- * Operator (Section 2, H u = b, "Laplacian-like"), flux form:
+ * Operator (Section 2, H u = b, of Laplacian type), flux form:
  *   (H u)_c = h_c u_c + sum_faces T_f (u_c - u_nb(f))
  * Split H = H_z + dH (Section 2.1): H_z holds the diagonal of H and the
  * couplings inside a column (-tz); dH the horizontal couplings.

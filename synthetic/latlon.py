@@ -1,7 +1,7 @@
 """Cell-centred finite-volume lat-lon shell grid and the seeded coefficient fields.
 
 The pressure-correction system of the paper (Section 2) is H u = b with H a
-sparse, Laplacian-like operator on a latitude-longitude grid with a strongly
+sparse operator of Laplacian type on a latitude-longitude grid with a strongly
 stretched vertical (Section 1: high aspect ratio; Section 2.2: the
 anisotropy alpha(theta) = dx_lon / dx_lat of the lat-lon grid).  The paper
 prints no discretisation, so this module fixes one (a reading, documented in
