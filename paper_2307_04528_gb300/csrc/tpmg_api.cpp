@@ -242,6 +242,7 @@ static size_t carve(mg_handle *H, void *base)
             v.cd = cv.take<double>(n);
             v.cq = cv.take<double>(n);
         }
+        if (mixed && l == 0) v.dh = cv.take<double>(n);
         if (mixed) {
             v.tx32 = cv.take<float>(n);
             v.ty32 = cv.take<float>(n);
@@ -434,6 +435,7 @@ static int setup_impl(mg_handle *H, const mg_coeffs *co, void *ws, size_t ws_byt
         int ex = 0;
         std::frexp(big, &ex);
         H->scale32 = std::ldexp(1.0, -ex);
+        KRUN(K_VEC, 0, 0, launch_hdiag(dev<double>(H->lev[0]), H->lev[0].dh, s));
         for (int l = 0; l < H->L; ++l) {
             LevelHost &v = H->lev[l];
             KRUN(K_VEC, l, 1, launch_to_float(v.tx, v.tx32, H->scale32, v.n, s));
@@ -897,7 +899,8 @@ extern "C" int mg_solve_mixed(mg_handle *H, const double *b, double *x, double t
     if (!(tol >= 0)) return fail(MG_ERR_ARG, "tol must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
     LevelHost &f = H->lev[0];
-    const LevelDev<double> D = dev<double>(f);
+    LevelDev<double> D = dev<double>(f);
+    D.h = f.dh;  // the refinement residual takes the horizontal diagonal (launch_residual_cast)
     const size_t n = f.n;
     std::vector<double> hist;
     double bb = 0;

@@ -80,7 +80,13 @@ __device__ __forceinline__ void stencil_load(StencilLoads<T> &s, const LevelDev<
 // handed to the FP32 inner solve; yscale a power of two).  NARROW_MUL: the
 // product is formed in TO after the rounding, exact for a yscale that is a
 // normal TO value (one FP64 operation fewer per cell).  The reduction uses out.
-template <typename T, int MODE, bool RED, typename TO = T, bool NARROW_MUL = false>
+// HSUM: L.h holds the horizontal diagonal h + the four horizontal couplings,
+// and the horizontal terms are taken in sum form, dh x_c - sum T x_nb (four
+// FMAs instead of four subtractions and four FMAs); the vertical couplings,
+// up to ~1e6 times h, keep the difference form whose subtraction is exact
+// for neighbouring values of a smooth column.
+template <typename T, int MODE, bool RED, typename TO = T, bool NARROW_MUL = false,
+          bool HSUM = false>
 __device__ __forceinline__ T stencil_column(const LevelDev<T> &L, const T *__restrict__ b,
                                             const T *__restrict__ x, TO *__restrict__ y, int col,
                                             T yscale = T(1))
@@ -111,10 +117,17 @@ __device__ __forceinline__ T stencil_column(const LevelDev<T> &L, const T *__res
                     const T xc = c.xc;
                     const T xup = (k + 1 < nz) ? st[(d + 1) % kDepth].xc : T(0);
                     T v = c.h * xc;
-                    v = fma(c.txc, xc - c.xe, v);
-                    v = fma(c.txw, xc - c.xw, v);
-                    if (hasN) v = fma(c.tyn, xc - c.xn, v);
-                    if (hasS) v = fma(c.tys, xc - c.xs, v);
+                    if (HSUM) {
+                        v = fma(-c.txc, c.xe, v);
+                        v = fma(-c.txw, c.xw, v);
+                        if (hasN) v = fma(-c.tyn, c.xn, v);
+                        if (hasS) v = fma(-c.tys, c.xs, v);
+                    } else {
+                        v = fma(c.txc, xc - c.xe, v);
+                        v = fma(c.txw, xc - c.xw, v);
+                        if (hasN) v = fma(c.tyn, xc - c.xn, v);
+                        if (hasS) v = fma(c.tys, xc - c.xs, v);
+                    }
                     v = fma(c.tz, xc - xup, v);
                     v = fma(tdn, xc - xdn, v);
                     const T out = MODE ? c.b - v : v;

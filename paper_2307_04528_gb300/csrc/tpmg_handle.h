@@ -60,6 +60,8 @@ struct LevelHost {
     float *b32 = nullptr, *u32 = nullptr, *w32 = nullptr, *r32 = nullptr;
     // coarsest level with the PCG coarse solve: direction and its image
     double *cd = nullptr, *cq = nullptr;
+    // finest level, mixed precision: h + the horizontal couplings
+    double *dh = nullptr;
     float *cd32 = nullptr, *cq32 = nullptr;
     LinkHost link;
     LinkDev linkdev{};

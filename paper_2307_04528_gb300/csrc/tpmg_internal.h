@@ -141,11 +141,14 @@ cudaError_t launch_cg_direction(const T *z, const T *d_in, T *d_out, size_t n,
 template <typename T>
 cudaError_t launch_add(T *x, const T *e, size_t n, cudaStream_t s);
 
-// r32 = (float)(r64 * inv_scale)
-// r32 = (float)((b - H x) * inv_scale) and ||b - H x||^2 partial sums;
-// returns the number of partial sums.
+// dh = h + the four horizontal couplings (the refinement residual's diagonal).
+cudaError_t launch_hdiag(const LevelDev<double> &L, double *dh, cudaStream_t s);
+// r32 = (float)((b - H x) * inv_scale) and ||b - H x||^2 partial sums, L.h
+// replaced by the horizontal diagonal (launch_hdiag); returns the number of
+// partial sums.
 int launch_residual_cast(const LevelDev<double> &L, const double *b, const double *x, float *r32,
                          double inv_scale, double *partial, cudaStream_t s);
+// r32 = (float)(r64 * inv_scale)
 cudaError_t launch_cast_scaled(const double *r, float *r32, double inv_scale, size_t n,
                                cudaStream_t s);
 // x64 += scale * (double)e32

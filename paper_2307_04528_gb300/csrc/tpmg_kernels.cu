@@ -77,11 +77,41 @@ __global__ void __launch_bounds__(kBlock)
 k_resid_cast(LevelDev<double> L, const double *__restrict__ b, const double *__restrict__ x,
              float *__restrict__ r32, double inv_scale, double *__restrict__ partial)
 {
-    const double acc = stencil_column<double, 1, true, float, NARROW_MUL>(
+    const double acc = stencil_column<double, 1, true, float, NARROW_MUL, true>(
         L, b, x, r32, blockIdx.x * blockDim.x + threadIdx.x, inv_scale);
     block_store<0>(acc, partial);
 }
 
+// dh = h + the four horizontal couplings of each cell (pole faces carry none).
+__global__ void __launch_bounds__(kBlock) k_hdiag(LevelDev<double> L, double *__restrict__ dh)
+{
+    const int nlon = L.nlon, nlat = L.nlat;
+    const size_t plane = (size_t)nlon * nlat, n = plane * L.nz;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+         c += (size_t)gridDim.x * blockDim.x) {
+        const size_t col = c % plane;
+        const int j = (int)(col / nlon), i = (int)(col - (size_t)j * nlon);
+        const size_t iw = (i == 0) ? c + nlon - 1 : c - 1;
+        double d = L.h[c] + L.tx[c];
+        d += L.tx[iw];
+        if (j + 1 < nlat) d += L.ty[c];
+        if (j > 0) d += L.ty[c - nlon];
+        dh[c] = d;
+    }
+}
+
+cudaError_t launch_hdiag(const LevelDev<double> &L, double *dh, cudaStream_t s)
+{
+    const size_t n = (size_t)L.nlon * L.nlat * L.nz;
+    const size_t g = std::min((n + (size_t)kBlock * 8 - 1) / ((size_t)kBlock * 8),
+                              (size_t)g_sms * 16);
+    k_hdiag<<<(int)std::max<size_t>(g, 1), kBlock, 0, s>>>(L, dh);
+    return cudaGetLastError();
+}
+
+// The refinement's residual: L.h must hold the horizontal diagonal
+// (launch_hdiag), the horizontal terms taken in sum form (stencil_column,
+// HSUM).
 int launch_residual_cast(const LevelDev<double> &L, const double *b, const double *x, float *r32,
                          double inv_scale, double *partial, cudaStream_t s)
 {
