@@ -5,7 +5,7 @@
 // threads of a warp touch consecutive addresses (coalesced, one 128-byte
 // line per warp per array in FP32, two in FP64).  Horizontal neighbours
 // (i +- 1, j +- 1) are re-reads of lines that neighbouring threads of the
-// same or an adjacent block load, served by L1/L2.  The FP32 V-cycle's fused
+// same or an adjacent block load, served by L1/L2.  The V-cycle's fused
 // residual + restriction is the exception: a thread walks the fine rows of a
 // latitude band on one layer (k_resid_restrict), because the restriction
 // gathers across rows, not along the column.
