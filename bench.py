@@ -45,9 +45,18 @@ def parse():
     ap.add_argument("--workload", default="latlon_1536x1152x70")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-paper", action="store_true",
+                    help="skip the one-off solves of the paper's own configuration")
     ap.add_argument("--profile-out", default=None,
                     help="write per-(kernel, level, precision) event times of the profiled "
                          "repeat to this JSON file")
+    ap.add_argument("--kernel", choices=sorted(PROBE_KERNELS), default=None,
+                    help="time one kernel (or one solve) in isolation on --shape instead of "
+                         "the benchmark; the mode the committed ncu summaries run")
+    ap.add_argument("--shape", type=int, nargs=3, default=[512, 384, 70],
+                    metavar=("NLON", "NLAT", "NZ"))
+    ap.add_argument("--launches", type=int, default=5)
+    ap.add_argument("--sigma", type=float, default=0.2)
     return ap.parse_args()
 
 
@@ -114,53 +123,90 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- CPU oracle
-def oracle_iteration_ms(P, its: int):
-    """Time one V-cycle-preconditioned CG iteration of the FP64 oracle (V-cycle,
-    operator apply, two inner products, vector updates) on the host cores."""
+def oracle_setup(P):
+    """The oracle's hierarchy and its FP32 copies (setup, untimed, as the
+    GPU's mg_setup is untimed)."""
     from oracle import tpmg as O
     p = O.MGParams()
     lev = O.build_hierarchy(P["tx"], P["ty"], P["tz"], P["h"], p)
-    b = P["b"]
-    r = b.copy()
+    return lev, O.float_levels(lev), p
+
+
+def oracle_solve_ms(P, lev, l32, p, mixed: bool):
+    """One complete solve of the oracle from x = 0 to ||b - H x|| <= 1e-10 ||b||
+    on the host cores, wall-clock timed: the mixed-precision solve (FP32
+    V-cycles inside FP64 refinement) or the FP64 solve.  Returns (ms, outer
+    iterations, status)."""
+    from oracle import tpmg as O
     t0 = time.perf_counter()
-    z = O.vcycle(lev, r, p)
-    Ad = O.apply(lev[0], z)
-    a = O.dot(r, z) / O.dot(z, Ad)
-    r -= a * Ad
-    z *= a
-    t1 = time.perf_counter()
-    per_it = (t1 - t0) * 1e3
-    return per_it, O.num_threads(), lev, p
+    if mixed:
+        _, hist, st = O.solve_mixed(lev, P["b"], TOL, params=p, levels32=l32)
+    else:
+        _, hist, st = O.solve(lev, P["b"], TOL, params=p)
+    return (time.perf_counter() - t0) * 1e3, len(hist) - 1, int(st)
 
 
 def run_reference(args):
+    """The oracle's mixed-precision solve of the workload, timed on the host
+    cores.  A complete solve takes ~30 s there, so a step is one of its
+    refinement steps, in rotation: step s runs refinement step k = s mod m
+    (m of them to 1e-10) from the iterate the oracle's own solve had entering
+    it (prepared untimed), i.e. the FP64 residual, its norm, the FP32 inner
+    solve and the FP64 update, plus, for the last one, the final residual
+    and stopping test.  The m step kinds add up to exactly the work of one
+    solve, so `value` = the sum over k of the mean time of step kind k (a
+    solve assembled from measured parts, no extrapolation) and ms_per_step
+    is the mean time of one step.  The W warm-up steps are one oracle FP32
+    V-cycle each (pages every level in and starts the thread pool)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     from oracle import tpmg as O
     w = WORKLOADS[args.workload]
     P = make_problem(w["nlon"], w["nlat"], w["nz"], w["sigma"], workload_seed(args.workload))
-    # iteration count of the oracle's own FP64 solve to 1e-10 (untimed, once)
-    p = O.MGParams()
-    lev = O.build_hierarchy(P["tx"], P["ty"], P["tz"], P["h"], p)
-    _, hist, st = O.solve(lev, P["b"], TOL, params=p)
-    its = len(hist) - 1
-    times = []
-    for step in range(args.warmup + args.steps):
-        per_it, cores, _, _ = oracle_iteration_ms(P, its)
-        if step >= args.warmup:
-            times.append(per_it * its)
-    v = statistics.mean(times)
+    lev, l32, p = oracle_setup(P)
+    b = P["b"]
+    bn = O.norm2(b)
+    starts = [np.zeros_like(b)]
+    _, hist, st = O.solve_mixed(lev, b, TOL, params=p, levels32=l32,
+                                track=lambda x: starts.append(x.copy()))
+    m = len(hist) - 1
+    if st != O.OK or m < 1:
+        raise RuntimeError(f"oracle mixed solve status {st} after {m} refinement steps")
+    r32 = (b / np.max(np.abs(b))).astype(np.float32)
+    for _ in range(args.warmup):
+        O.vcycle(l32, r32, p)
+    times = [[] for _ in range(m)]
+    final = None
+    for step in range(args.steps):
+        k = step % m
+        x = starts[k].copy()
+        t0 = time.perf_counter()
+        r = O.residual(lev[0], b, x)
+        rn = O.norm2(r)
+        O.refine_correct(l32, x, r, rn, bn, TOL, p)
+        if k == m - 1:
+            final = O.norm2(O.residual(lev[0], b, x)) / bn
+        times[k].append((time.perf_counter() - t0) * 1e3)
+    done = [t for t in times if t]
+    if len(done) < m:
+        raise RuntimeError(f"--steps {args.steps} < {m} refinement steps: no complete solve")
+    v = sum(statistics.mean(t) for t in times)
+    per_step = statistics.mean(t for ts in times for t in ts)
     out = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "tol": TOL, "iterations": its,
-                   "oracle_status": int(st)},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"each step: one FP64 CG iteration of the oracle at "
-                                   f"{args.workload} x {its} iterations (its own solve)"},
+        "config": {"workload": args.workload, "tol": TOL, "refinement_steps": m,
+                   "step": "one refinement step of the oracle's mixed solve, in rotation",
+                   "step_ms_by_refinement_step": [statistics.mean(t) for t in times],
+                   "final_rel_res": final, "oracle_status": int(st),
+                   "warmup": "one oracle FP32 V-cycle per warm-up step"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"the oracle's mixed-precision solve at {args.workload} to "
+                                   f"1e-10 from x = 0, its {m} refinement steps timed one per "
+                                   f"step in rotation and summed (wall clock)"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -212,6 +258,48 @@ def kernel_table(H, L, N):
     return rows
 
 
+# the paper's configuration: (label, mg_params overrides, mixed, maxit cap)
+PAPER_RUNS = [
+    ("stationary_default_hierarchy_fp64", dict(method=1), False, 200),
+    ("stationary_default_hierarchy_mixed", dict(method=1, inner_maxit=40), True, 40),
+    ("stationary_4_levels_fp64", dict(method=1, levels=4), False, 60),
+    ("cg_4_levels_mixed", dict(levels=4, inner_maxit=200), True, 40),
+]
+
+
+def paper_config(MGHandle, coeffs, b, barrier):
+    """Time one solve of each PAPER_RUNS entry to 1e-10 (or its iteration cap)
+    with CUDA events, on a handle built for it; returns a dict of times,
+    iteration counts, the residual reached and the mean residual reduction per
+    outer FP64 iteration (the quantity Section 2 puts near 0.1)."""
+    import torch
+    out = {}
+    stream = torch.cuda.current_stream()
+    for label, over, mixed, cap in PAPER_RUNS:
+        Hp = MGHandle(*coeffs, mixed=int(mixed), maxit=cap, **over)
+        x = torch.zeros_like(b)
+        fn = Hp.solve_mixed if mixed else Hp.solve
+        fn(b, x, tol=TOL, raise_on_error=False)  # warm-up (captures the V-cycle graph)
+        x.zero_()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        _, info = fn(b, x, tol=TOL, raise_on_error=False)
+        ev1.record(stream)
+        barrier()
+        hist = info["history"]
+        its = max(len(hist) - 1, 1)
+        out[label] = {"ms": ev0.elapsed_time(ev1), "status": info["status"],
+                      "iterations": info["iterations"],
+                      "fp32_iterations": info["inner_iterations"] if mixed else None,
+                      "rel_res": info["rel_res"], "levels": Hp.num_levels,
+                      "reduction_per_iteration": (hist[-1] / hist[0]) ** (1.0 / its)
+                      if hist and hist[0] > 0 else None}
+        del Hp, x
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2307_04528_gb300 import replicas
@@ -233,7 +321,6 @@ def run_ours(args):
     H = MGHandle(tx, ty, tz, hh, mixed=1)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
-    del tx, ty, tz, hh
     x = torch.zeros_like(b)
     lib = L.load()
     stream = torch.cuda.current_stream()
@@ -324,6 +411,13 @@ def run_ours(args):
     ms_fp64 = max_over_ranks(ms_fp64 / args.steps)
     info_d = infos64[-1]
 
+    # the paper's own configuration, each solve timed once: the stationary
+    # iteration x <- x + V(b - H x) (Section 2) on the default hierarchy, and
+    # on the 4-level shallow hierarchy of Section 2.3 (capped: its iteration
+    # count grows with resolution), beside the CG-accelerated default
+    paper = paper_config(MGHandle, (tx, ty, tz, hh), b, barrier) if not args.no_paper else None
+    del tx, ty, tz, hh
+
     peak, peak_kind = load_peaks()
     # the kernel with the largest share of the mixed solve: the V-cycle's last
     # fine-level sweep with <r, z> fused (reads u, b, tx, ty, tz, m, dq; writes
@@ -378,7 +472,8 @@ def run_ours(args):
                    "fp64_rel_res": info_d["rel_res"],
                    "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed,
                    "levels": H.num_levels, "setup_ms": setup_ms,
-                   "fp64_residual_kernel_avg_ms": res_avg},
+                   "fp64_residual_kernel_avg_ms": res_avg,
+                   "paper_configuration": paper},
         "gpu_launches": int(launches),
         "kernels_fine_level": kernels,
         "clocks": clk,
@@ -388,12 +483,14 @@ def run_ours(args):
     if e2e:
         out["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        per_it, cores, _, _ = oracle_iteration_ms(P, info_d["iterations"])
+        from oracle import tpmg as O
+        lev, l32, p = oracle_setup(P)
+        ms, its, st = oracle_solve_ms(P, lev, l32, p, mixed=True)
         out["cpu_baseline"] = {
-            "value": per_it * info_d["iterations"], "unit": UNIT, "cores": cores,
-            "kind": "oracle",
-            "sample": f"one FP64 CG iteration of the oracle at {args.workload}, scaled by the "
-                      f"FP64 iteration count to 1e-10 ({info_d['iterations']})"}
+            "value": ms, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"one complete mixed-precision solve of the oracle at {args.workload} to "
+                      f"1e-10 from x = 0, timed (wall clock)",
+            "refinement_steps": its, "status": st}
     if rank == 0:
         print(json.dumps(out))
     replicas.finalize()
@@ -495,8 +592,120 @@ def run_ensemble(args):
     print(json.dumps(out))
 
 
+# ----------------------------------------------------------------- one kernel
+# --kernel name -> (precision, what runs, algorithmic words per fine cell or None)
+PROBE_KERNELS = {
+    "smooth32": (1, "smooth", 8),
+    "smooth32_dot": (1, "smooth_dot", 8),
+    "smooth32_zero": (1, "smooth0", 5),
+    "resid32": (1, "residual", 7),
+    "apply32": (1, "apply", 6),
+    "restrict32": (1, "restrict", None),
+    "resid_restrict32": (1, "resid_restrict", None),
+    "presmooth_restrict32": (1, "presmooth_restrict", None),
+    "prolong32": (1, "prolong", None),
+    "coarse32": (1, "coarse", None),
+    "vcycle32": (1, "vcycle", None),
+    "smooth64": (0, "smooth", 8),
+    "smooth64_zero": (0, "smooth0", 5),
+    "resid64": (0, "residual", 7),
+    "apply64": (0, "apply", 6),
+    "coarse64": (0, "coarse", None),
+    "vcycle64": (0, "vcycle", None),
+    "coeff_grad64": (0, "coeff_grad", 10),
+    # whole solves (ncu picks the kernels of interest by name: the CG vector
+    # kernels, the fused direction update + apply, the FP64 refinement residual)
+    "solve_mixed": (1, "solve_mixed", None),
+    "solve64": (0, "solve", None),
+}
+
+
+def run_kernel(args):
+    """Run one fine-level kernel of the multigrid `--launches` times on a
+    seeded system of `--shape` through the library's per-level C ABI and
+    print its mean event time (and algorithmic GB/s where the bytes are
+    known).  Small cases (a few GB on the device, every array above the
+    129 MB L2) are what the ncu captures of the profiles run."""
+    import torch
+
+    from paper_2307_04528_gb300.solver import MGHandle
+
+    nlon, nlat, nz = args.shape
+    P = make_problem(nlon, nlat, nz, args.sigma, 3000)
+    d = lambda a, dt=torch.float64: torch.as_tensor(a).to("cuda", dt)
+    H = MGHandle(d(P["tx"]), d(P["ty"]), d(P["tz"]), d(P["h"]), mixed=1)
+    prec, op, words = PROBE_KERNELS[args.kernel]
+    dt = torch.float32 if prec == 1 else torch.float64
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    shape = (nz, nlat, nlon)
+    b = torch.randn(shape, generator=gen, device="cuda", dtype=dt)
+    u = torch.randn(shape, generator=gen, device="cuda", dtype=dt)
+    cshape = H.level_shape(1) if H.num_levels > 1 else shape
+    ec = torch.randn(cshape, generator=gen, device="cuda", dtype=dt)
+    lshape = H.level_shape(H.num_levels - 1)
+    bcoarse = torch.randn(lshape, generator=gen, device="cuda", dtype=dt)
+    b64 = d(P["b"])
+    x64 = torch.zeros_like(b64)
+
+    def run():
+        if op == "smooth":
+            return H.level_smooth(0, b, u, prec=prec)
+        if op == "smooth_dot":
+            return H.level_smooth_dot(0, b, u, prec=prec)
+        if op == "smooth0":
+            return H.level_smooth(0, b, None, prec=prec)
+        if op == "residual":
+            return H.level_residual(0, b, u, prec=prec)
+        if op == "apply":
+            return H.level_apply(0, u, prec=prec)
+        if op == "restrict":
+            return H.level_restrict(0, u, prec=prec)
+        if op == "resid_restrict":
+            return H.level_residual_restrict(0, b, u, prec=prec)
+        if op == "presmooth_restrict":
+            return H.level_presmooth_restrict(0, b, u, prec=prec)
+        if op == "coarse":
+            return H.coarse_solve(bcoarse, prec=prec)
+        if op == "vcycle":
+            return H.vcycle(b, prec=prec)
+        if op == "coeff_grad":
+            return H.coeff_grad(b, u)
+        if op == "solve_mixed":
+            x64.zero_()
+            return H.solve_mixed(b64, x64, tol=TOL)
+        if op == "solve":
+            x64.zero_()
+            return H.solve(b64, x64, tol=TOL)
+        return H.level_prolong_add(0, ec, u, prec=prec)
+
+    run()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(args.launches):
+        run()
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / args.launches
+    n = nz * nlat * nlon
+    out = {"kernel": args.kernel, "shape": args.shape, "avg_ms": ms}
+    if op in ("resid_restrict", "presmooth_restrict"):  # 6 (4) fine arrays read, coarse written
+        words = (6 if op == "resid_restrict" else 4) + cshape[0] * cshape[1] * cshape[2] / n
+    if op == "restrict":
+        words = 1 + cshape[0] * cshape[1] * cshape[2] / n
+    if op == "prolong":
+        words = 2 + cshape[0] * cshape[1] * cshape[2] / n
+    if words:
+        nbytes = words * (4 if prec == 1 else 8) * n
+        out.update(alg_bytes=nbytes, gbs=nbytes / (ms * 1e-3) / 1e9)
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.kernel:
+        run_kernel(args)
+        return
     if args.workload == "ensemble":
         run_ensemble(args)
         return

@@ -128,6 +128,14 @@ int mg_apply(mg_handle *h, const double *x, double *y, void *stream);
  * Fig. 1).  r, e: device FP64 fine-level fields; r is not modified. */
 int mg_vcycle(mg_handle *h, const double *r, double *e, void *stream);
 
+/* The same V-cycle in either precision: prec MG_PREC_FP64 (as mg_vcycle) or
+ * MG_PREC_FP32, the FP32 hierarchy the inner solve of mg_solve_mixed uses
+ * (needs params->mixed = 1; its coefficients are the FP64 ones scaled by
+ * mg_fp32_scale, so e approximates (c H)^{-1} r).  r, e: device fields of
+ * that precision on the fine level, distinct; r is not modified.  Uses the
+ * handle's level work vectors: calls on one handle must not overlap. */
+int mg_vcycle_prec(mg_handle *h, int prec, const void *r, void *e, void *stream);
+
 /* Solve H x = b to ||b - H x||_2 <= tol ||b||_2 in FP64 (Section 2).
  * x: in = initial guess, out = solution.  stats may be NULL.  Returns
  * MG_OK, MG_ERR_NOT_CONVERGED (x holds the last iterate), MG_ERR_NONFINITE
@@ -306,8 +314,12 @@ int mg_profile_read(mg_handle *h, int kind, int level, int prec, int *launches, 
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the array and leave their partial sums in it: calls that
  * overlap on the GPU (other streams, other host threads) race.  Calls
- * cudaMalloc/cudaFree never.  b, x, r: device FP64 fields; rel_out: host.
- * Synchronises `stream`. */
+ * cudaMalloc/cudaFree never.  The coefficients are not validated (mg_setup
+ * does that for a handle); the operator is the one mg_setup accepts, the
+ * top-face coupling tz[nz-1] not being read.  b, x, r: device FP64 fields;
+ * rel_out: host.  MG_ERR_NONFINITE when either norm is NaN or Inf,
+ * MG_ERR_CUDA when a launch or the copy fails (*rel_out is then left as it
+ * was).  Synchronises `stream`. */
 int mg_residual_norm_noalloc(const mg_grid *grid, const mg_coeffs *coeffs, const double *b,
                              const double *x, double *r, double *rel_out, void *stream);
 

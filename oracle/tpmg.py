@@ -9,11 +9,13 @@ Arithmetic lives in tpmg_oracle.c (double and float instances, built with
 V-cycle recursion (Section 2 and Fig. 1), the multigrid solvers (Section 2:
 the stationary iteration, and the V-cycle as preconditioner of conjugate
 gradients), the mixed-precision refinement (Section 1's single-precision
-remark) and the gradient of the differentiable solve, in the order the method
-states them.
+remark), the gradient of the differentiable solve, in the order the method
+states them, and the spectrum of H_z^{-1} H whose condition number Section
+2.3's shallow-hierarchy argument rests on.
 
-Pinned by tests/test_oracle_pins.py; the mixed-precision trajectory is pinned
-only by its convergence (parity unpinned beyond that, no number in the paper).
+Pinned by tests/test_oracle_pins.py and tests/test_oracle_convergence.py; the
+mixed-precision trajectory is pinned only by its convergence (parity unpinned
+beyond that, no number in the paper).
 """
 from __future__ import annotations
 
@@ -482,7 +484,6 @@ def solve_mixed(levels, b, tol: float = 1e-10, params: MGParams | None = None,
     p = params or MGParams()
     maxit = p.maxit if maxit is None else maxit
     l32 = levels32 if levels32 is not None else float_levels(levels)
-    c = l32[0].scale
     x = np.zeros_like(b)
     bn = norm2(b)
     hist = []
@@ -494,16 +495,26 @@ def solve_mixed(levels, b, tol: float = 1e-10, params: MGParams | None = None,
             return x, hist, OK
         if it == maxit:
             break
-        _, ex = np.frexp(np.max(np.abs(r)))
-        s = float(np.ldexp(1.0, int(ex)))
-        r32 = (r / s).astype(np.float32)
-        # no further than the outer target still needs (safety 0.3), at most 0.5
-        itol = min(max(p.inner_tol, 0.3 * tol / (rn / bn)), 0.5)
-        e, _, _ = solve(l32, r32, itol, params=p, maxit=p.inner_maxit)
-        x += (c * s) * e.astype(np.float64)
+        refine_correct(l32, x, r, rn, bn, tol, p)
         if track is not None:
             track(x)
     return x, hist, NOT_CONVERGED
+
+
+def refine_correct(levels32, x, r, rn, bn, tol, p: MGParams):
+    """The correction of one refinement step of solve_mixed, in place on the
+    FP64 iterate x given its FP64 residual r (norm rn; bn = ||b||): scale r by
+    the power of two s at its largest magnitude, round to FP32, solve
+    (c H) e = r / s with the FP32 multigrid to the inner tolerance, and add
+    c s e in FP64."""
+    c = levels32[0].scale
+    _, ex = np.frexp(np.max(np.abs(r)))
+    s = float(np.ldexp(1.0, int(ex)))
+    r32 = (r / s).astype(np.float32)
+    # no further than the outer target still needs (safety 0.3), at most 0.5
+    itol = min(max(p.inner_tol, 0.3 * tol / (rn / bn)), 0.5)
+    e, _, _ = solve(levels32, r32, itol, params=p, maxit=p.inner_maxit)
+    x += (c * s) * e.astype(np.float64)
 
 
 # ------------------------------------------------------------------- gradient
@@ -522,6 +533,86 @@ def solve_with_grad(levels, b, dLdx_fn, tol=1e-13, params=None):
     lam, _, _ = solve(levels, g, tol, params=params)
     gh, gtx, gty, gtz = coeff_grad(levels[0], lam, x)
     return x, dict(b=lam, h=gh, tx=gtx, ty=gty, tz=gtz)
+
+
+# ----------------------------------------------- condition number (Section 2.3)
+def sparse_operator(lev: Level):
+    """H of one level as a scipy CSR matrix, read off the oracle's own apply:
+    every cell's stencil reaches layers k-1..k+1, rows j-1..j+1 and
+    longitudes i-1..i+1 (mod nlon), so the 36 colourings (k mod 3, j mod 3,
+    i mod 4) give each stencil at most one probed cell per colour (nlon a
+    multiple of 4), and H applied to a colour's indicator holds column
+    entries H[row, col] for the probed cells col.  Tiny or moderate grids."""
+    import scipy.sparse as sp
+    nz, nlat, nlon = lev.shape
+    if nlon % 4:
+        raise ValueError("probing needs nlon divisible by 4")
+    K, J, I = np.meshgrid(np.arange(nz), np.arange(nlat), np.arange(nlon), indexing="ij")
+    colour = (K % 3) * 12 + (J % 3) * 4 + (I % 4)
+    idx = np.arange(lev.size).reshape(lev.shape)
+    rows, cols, vals = [], [], []
+    for c in range(36):
+        y = apply(lev, (colour == c).astype(np.float64))
+        for dk, dj, di in ((0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0),
+                           (0, 0, 1), (0, 0, -1)):
+            kk, jj, ii = K + dk, J + dj, (I + di) % nlon
+            ok = (kk >= 0) & (kk < nz) & (jj >= 0) & (jj < nlat)
+            kk, jj = np.clip(kk, 0, nz - 1), np.clip(jj, 0, nlat - 1)
+            m = ok & (colour[kk, jj, ii] == c)
+            rows.append(idx[m])
+            cols.append(idx[kk, jj, ii][m])
+            vals.append(y[m])
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(lev.size, lev.size)).tocsr()
+    A.eliminate_zeros()
+    return A
+
+
+def column_part(A, lev: Level):
+    """H_z of Section 2.1: the entries of H that couple cells of one vertical
+    column (its diagonal and the couplings between layers)."""
+    import scipy.sparse as sp
+    C = A.tocoo()
+    ncol = lev.nlat * lev.nlon
+    m = (C.row % ncol) == (C.col % ncol)
+    return sp.csr_matrix((C.data[m], (C.row[m], C.col[m])), shape=A.shape)
+
+
+def row_band(lev: Level, j0: int, j1: int) -> Level:
+    """Rows j0..j1-1 of a level as a level of their own, with zero-flux faces
+    at the band's southern and northern edges (the couplings to the rows
+    outside are dropped, so the constant stays the smoothest mode)."""
+    s = slice(j0, j1)
+    ty = lev.ty[:, s, :].copy()
+    ty[:, -1, :] = 0.0
+    cut = lambda a: np.ascontiguousarray(a[:, s, :])
+    return Level(lev.nlon, j1 - j0, lev.nz, cut(lev.tx), ty, cut(lev.tz), cut(lev.h),
+                 lev.south[s].copy(), lev.north[s].copy())
+
+
+def hz_spectrum(lev: Level, tol: float = 1e-9):
+    """Extreme eigenvalues (lambda_min, lambda_max) of H_z^{-1} H, whose ratio
+    is the condition number that Section 2.3 says governs the block-Jacobi
+    iteration of Eq. (1): the generalised symmetric problem H v = lambda H_z v
+    by Lanczos (scipy's eigsh, relative accuracy tol), the smallest by
+    shift-invert about 0."""
+    import scipy.sparse.linalg as spla
+    A = sparse_operator(lev)
+    Z = column_part(A, lev)
+    lmax = spla.eigsh(A, k=1, M=Z, which="LA", tol=tol, return_eigenvectors=False)[0]
+    lmin = spla.eigsh(A, k=1, M=Z, sigma=0.0, which="LM", tol=tol,
+                      return_eigenvectors=False)[0]
+    return float(lmin), float(lmax)
+
+
+def courant_squared(lmin: float, horizontal_faces: int = 4) -> float:
+    """The squared horizontal Courant number read off lambda_min of
+    H_z^{-1} H.  For the constant mode of a band with zero-flux edges H u =
+    h u and H_z u = (h + sum of the horizontal couplings) u, so
+    1 / lambda_min - 1 = (sum of the four horizontal couplings) / h, which is
+    4 nu^2 on a grid of square cells (t_x / h = t_y / h = nu^2 at the
+    equator of the generator): nu^2 = (1 / lambda_min - 1) / 4."""
+    return (1.0 / lmin - 1.0) / horizontal_faces
 
 
 def dense_operator(lev: Level) -> np.ndarray:

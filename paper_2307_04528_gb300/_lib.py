@@ -77,6 +77,7 @@ def load() -> ctypes.CDLL:
         "mg_destroy": (None, [H]),
         "mg_apply": (I, [H, P, P, P]),
         "mg_vcycle": (I, [H, P, P, P]),
+        "mg_vcycle_prec": (I, [H, I, P, P, P]),
         "mg_solve": (I, [H, P, P, D, ctypes.POINTER(mg_stats), P]),
         "mg_solve_mixed": (I, [H, P, P, D, ctypes.POINTER(mg_stats), P]),
         "mg_coeff_grad": (I, [H, P, P, P, P, P, P, P]),

@@ -563,6 +563,8 @@ extern "C" int mg_profile_read(mg_handle *H, int kind, int level, int prec, int 
 
 extern "C" unsigned long long mg_launch_count(void) { return g_launches.load(); }
 
+static int level_check(mg_handle *H, int level, int prec, bool need_coarser);
+
 // ------------------------------------------------------------------ V-cycle
 // Smoother sweeps from a zero guess, alternating between two buffers so that
 // the last sweep writes `out`.
@@ -996,6 +998,22 @@ extern "C" int mg_vcycle(mg_handle *H, const double *r, double *e, void *stream)
 {
     if (!H || !r || !e) return fail(MG_ERR_ARG, "null argument");
     return vcycle_fine<double>(H, r, e, (cudaStream_t)stream);
+}
+
+extern "C" int mg_vcycle_prec(mg_handle *H, int prec, const void *r, void *e, void *stream)
+{
+    CHK(level_check(H, 0, prec, false));
+    if (!r || !e || r == e) return fail(MG_ERR_ARG, "bad V-cycle buffers");
+    LevelHost &f = H->lev[0];
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == MG_PREC_FP64) {
+        if (r == f.w || e == f.w || r == f.r || e == f.r)
+            return fail(MG_ERR_ARG, "buffer aliases a level work vector");
+        return vcycle_fine<double>(H, (const double *)r, (double *)e, s);
+    }
+    if (r == f.w32 || e == f.w32 || r == f.r32 || e == f.r32)
+        return fail(MG_ERR_ARG, "buffer aliases a level work vector");
+    return vcycle_fine<float>(H, (const float *)r, (float *)e, s);
 }
 
 extern "C" int mg_coeff_grad(mg_handle *H, const double *lam, const double *x, double *gh,

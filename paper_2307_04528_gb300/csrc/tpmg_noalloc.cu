@@ -13,12 +13,18 @@
 // kMaxBlocks * kThreads columns (nlon * nlat) are rejected.  Every call on a
 // device uses the same array and leaves its contents behind; calls that
 // overlap on the GPU (two streams, or two host threads) race on it.
+//
+// The coefficients are not validated here (mg_setup does that for a handle);
+// the operator is the one mg_setup accepts: the model-top coupling
+// tz[nz-1] is never read, as the top face carries no flux.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 
 #include "../../include/tpmg.h"
+#include "tpmg_handle.h"
 #include "tpmg_internal.h"
 
 namespace {
@@ -91,7 +97,7 @@ k_residual_norm_static(int nlon, int nlat, int nz, const double *__restrict__ tx
         for (int k = 0; k < nz; ++k) {
             const size_t o = (size_t)k * plane;
             const double xup = (k + 1 < nz) ? x[o + plane + col] : 0.0;
-            const double tup = tz[o + col];
+            const double tup = (k + 1 < nz) ? tz[o + col] : 0.0;  // no flux through the top
             double v = h[o + col] * xc;
             v = fma(tx[o + col], xc - x[o + ie], v);
             v = fma(tx[o + iw], xc - x[o + iw], v);
@@ -166,16 +172,25 @@ extern "C" int mg_residual_norm_noalloc(const mg_grid *grid, const mg_coeffs *co
     int st = scratch_for_current_device(&scratch);
     if (st != MG_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // A launch that fails (no kernel image, a bad stream) must not let the
+    // copy below return the previous call's result from the shared array.
     k_residual_norm_static<<<(int)nblocks, kThreads, 0, s>>>(
         grid->nlon, grid->nlat, grid->nz, coeffs->tx, coeffs->ty, coeffs->tz, coeffs->h, b, x, r,
         scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return err(MG_ERR_CUDA, cudaGetErrorString(e));
     k_finalize_static<<<1, 1024, 0, s>>>((int)nblocks, scratch);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return err(MG_ERR_CUDA, cudaGetErrorString(e));
+    tpmg::g_launches.fetch_add(2, std::memory_order_relaxed);
     double res[2] = {0, 0};
-    cudaError_t e = cudaMemcpyAsync(res, scratch + 2 * kMaxBlocks, sizeof res,
-                                    cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(res, scratch + 2 * kMaxBlocks, sizeof res, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return err(MG_ERR_CUDA, cudaGetErrorString(e));
-    if (!(res[0] == res[0]) || !(res[1] == res[1])) return err(MG_ERR_NONFINITE, "non-finite norm");
-    *rel_out = res[1] > 0 ? sqrt(res[0] / res[1]) : sqrt(res[0]);
+    if (!std::isfinite(res[0]) || !std::isfinite(res[1]))
+        return err(MG_ERR_NONFINITE, "non-finite norm");
+    const double rel = res[1] > 0 ? std::sqrt(res[0] / res[1]) : std::sqrt(res[0]);
+    if (!std::isfinite(rel)) return err(MG_ERR_NONFINITE, "non-finite norm");
+    *rel_out = rel;
     return MG_OK;
 }

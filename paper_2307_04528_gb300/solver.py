@@ -6,6 +6,7 @@ CUDA stream; every numerical step runs in libtpmg's kernels.
 from __future__ import annotations
 
 import ctypes
+import warnings
 
 import torch
 
@@ -109,10 +110,15 @@ class MGHandle:
         L.check(self.lib.mg_apply(self._hh, _ptr(x), _ptr(y), _stream()))
         return y
 
-    def vcycle(self, r, e=None):
-        _field(r, torch.float64, self.shape, "r")
+    def vcycle(self, r, e=None, prec=L.MG_PREC_FP64):
+        """e = V r, one V-cycle from zero; prec MG_PREC_FP32 runs the FP32
+        hierarchy (scaled coefficients, see fp32_scale) on float32 r."""
+        _field(r, self._dt(prec), self.shape, "r")
         e = torch.empty_like(r) if e is None else e
-        L.check(self.lib.mg_vcycle(self._hh, _ptr(r), _ptr(e), _stream()))
+        if prec == L.MG_PREC_FP64:
+            L.check(self.lib.mg_vcycle(self._hh, _ptr(r), _ptr(e), _stream()))
+        else:
+            L.check(self.lib.mg_vcycle_prec(self._hh, prec, _ptr(r), _ptr(e), _stream()))
         return e
 
     def _solve(self, fn, b, x, tol, history_cap, raise_on):
@@ -225,18 +231,30 @@ class MGHandle:
         return u
 
 
-# A solve that stops on `maxit` with the residual stuck at the FP64 rounding
-# floor (rounding of x times the vertical couplings: ~1e-12..1e-10 relative,
-# higher for smooth right-hand sides such as an adjoint dL/dx) still
-# returns an accurate solution; accept it below this relative residual.
-FLOOR_ACCEPT = 1e-8
+class MGFloorWarning(RuntimeWarning):
+    """A differentiable solve stopped on maxit above its tolerance but below the
+    caller's floor_accept, and its solution was used."""
 
 
-def _solve_checked(handle, b, tol):
+def _solve_checked(handle, b, tol, floor_accept=None):
+    """Solve and raise on any failure, except that a solve stopping on maxit
+    with rel_res <= floor_accept is accepted with an MGFloorWarning.  The
+    FP64 rounding floor of the residual (rounding of x times the vertical
+    couplings: ~1e-12..1e-10 relative, higher for smooth right-hand sides
+    such as an adjoint dL/dx) can sit above a tight tol while the solution
+    is accurate; floor_accept=None (the default) accepts nothing."""
     x, info = handle.solve(b, tol=tol, raise_on_error=False)
     st = info["status"]
-    if st != L.MG_OK and not (st == L.MG_ERR_NOT_CONVERGED and info["rel_res"] <= FLOOR_ACCEPT):
-        L.check(st)
+    if st == L.MG_OK:
+        return x, info
+    if (st == L.MG_ERR_NOT_CONVERGED and floor_accept is not None
+            and info["rel_res"] <= floor_accept):
+        warnings.warn(MGFloorWarning(
+            f"solve stopped after {info['iterations']} iterations at relative residual "
+            f"{info['rel_res']:.3e} > tol {tol:.1e}; accepted (floor_accept {floor_accept:.1e})"),
+            stacklevel=3)
+        return x, info
+    L.check(st)
     return x, info
 
 
@@ -317,26 +335,33 @@ class MGSolveFn(torch.autograd.Function):
     hierarchy (H is symmetric: each face couples its two cells with one
     coefficient, so the transposed stencil is the stencil) and forms the
     coefficient gradient with one fused kernel; only the solution x is kept
-    from the forward pass, no iterate."""
+    from the forward pass, no iterate.  Both solves must reach tol; with
+    floor_accept set, a solve that stops on maxit at or below that relative
+    residual is used with an MGFloorWarning.  The statuses of the two solves
+    are kept in ctx.infos (forward, then adjoint)."""
 
     @staticmethod
-    def forward(ctx, b, h, tx, ty, tz, tol=1e-11, params=None):
+    def forward(ctx, b, h, tx, ty, tz, tol=1e-11, params=None, floor_accept=None):
         params = dict(params or {})
         handle = MGHandle(tx.detach().contiguous(), ty.detach().contiguous(),
                           tz.detach().contiguous(), h.detach().contiguous(), **params)
-        x, _ = _solve_checked(handle, b.detach().contiguous(), tol)
+        x, info = _solve_checked(handle, b.detach().contiguous(), tol, floor_accept)
         ctx.handle = handle
         ctx.tol = tol
+        ctx.floor_accept = floor_accept
+        ctx.infos = [info]
         ctx.save_for_backward(x)
         return x
 
     @staticmethod
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
-        lam, _ = _solve_checked(ctx.handle, gx.contiguous(), ctx.tol)
+        lam, info = _solve_checked(ctx.handle, gx.contiguous(), ctx.tol, ctx.floor_accept)
+        ctx.infos.append(info)
         gh, gtx, gty, gtz = ctx.handle.coeff_grad(lam, x)
-        return lam, gh, gtx, gty, gtz, None, None
+        return lam, gh, gtx, gty, gtz, None, None, None
 
 
-def mg_solve_fn(b, h, tx, ty, tz, tol=1e-11, **params):
-    return MGSolveFn.apply(b, h, tx, ty, tz, tol, params)
+def mg_solve_fn(b, h, tx, ty, tz, tol=1e-11, floor_accept=None, **params):
+    """Differentiable solve (MGSolveFn); params: mg_params overrides."""
+    return MGSolveFn.apply(b, h, tx, ty, tz, tol, params, floor_accept)

@@ -95,3 +95,27 @@ def test_batched_large_members_column_paths():
         xi, inf1 = B.handle(i).solve(bs[i], tol=1e-10)
         assert abs(inf1["iterations"] - inf64[i]["iterations"]) <= 1
         assert rel_2(host(x64[i]), host(xi)) <= 1e-8
+
+
+def test_batch_with_an_operational_size_member():
+    """A batch whose members include a 1024 x 768 x 70 system (the ensemble's
+    third member size: its finest level runs the single-system kernels inside
+    the batched steps) next to small ones: mixed solve to 1e-8, each member
+    within one FP32 iteration of its single-system solve on the same handle,
+    and its residual recomputed by the oracle from the GPU solution."""
+    from paper_2307_04528_gb300.solver import MGBatch
+    shapes = [(1024, 768, 70), (64, 32, 16), (256, 192, 70)]
+    probs = [problem(*shp, sigma=0.1, seed=5100 + i) for i, shp in enumerate(shapes)]
+    systems = [tuple(dev(P[k]) for k in ("tx", "ty", "tz", "h")) for P in probs]
+    B = MGBatch(systems, mixed=1)
+    del systems
+    bs = [dev(P["b"]) for P in probs]
+    xs, infos = B.solve(bs, tol=1e-8, mixed=True)
+    for i, P in enumerate(probs):
+        assert infos[i]["status"] == 0 and infos[i]["rel_res"] <= 1e-8
+        lev, _ = oracle_levels(P, levels=1)
+        rel = O.norm2(O.residual(lev[0], P["b"], host(xs[i]))) / O.norm2(P["b"])
+        assert rel <= 1e-8 and abs(rel - infos[i]["rel_res"]) <= 1e-12
+        xi, inf1 = B.handle(i).solve_mixed(bs[i], tol=1e-8)
+        assert abs(inf1["inner_iterations"] - infos[i]["inner_iterations"]) <= 1
+        assert rel_2(host(xs[i]), host(xi)) <= 1e-6

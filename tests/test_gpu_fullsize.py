@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_common import dev, handle_for, host, oracle_levels, rel_inf
+from gpu_common import dev, handle_for, host, oracle_levels, rel_2, rel_inf
 from oracle import tpmg as O
 from synthetic import make_problem
 
@@ -94,6 +94,33 @@ def test_fine_level_kernels_fp32(full):
     assert rel_inf(host(got), O.restrict(f, O.residual(f, b, x))) <= 2e-5
     two = H.level_restrict(0, H.level_residual(0, f32(b), f32(x), prec=1), prec=1)
     assert torch.equal(got, two)
+
+
+def test_presmooth_restrict_fp32(full):
+    """The V-cycle's residual + restriction after its sweep from zero (the
+    form the benchmarked FP32 cycle runs) at full size: the band walk over
+    1536-wide rows and every band of 8 coarse rows."""
+    P, lev, p, H = full
+    l32 = O.float_levels(lev)
+    f = l32[0]
+    b = np.random.default_rng(24).standard_normal(f.shape).astype(np.float32)
+    u = H.level_smooth(0, dev(b, torch.float32), prec=1)
+    got = host(H.level_presmooth_restrict(0, dev(b, torch.float32), u, prec=1))
+    ref = O.restrict(f, O.presmooth_residual(f, b, host(u), np.float32(p.omega)))
+    assert rel_inf(got, ref) <= 2e-5
+
+
+def test_vcycle_fp32(full):
+    """The whole FP32 V-cycle of the benchmarked mixed solve, element by
+    element against the oracle's float V-cycle (bounds of the small-shape
+    parity test)."""
+    P, lev, p, H = full
+    l32 = O.float_levels(lev)
+    r = np.random.default_rng(25).standard_normal(lev[0].shape).astype(np.float32)
+    got = host(H.vcycle(dev(r, torch.float32), prec=1))
+    ref = O.vcycle(l32, r, p)
+    assert rel_inf(got, ref) <= 1e-4
+    assert rel_2(got, ref) <= 2e-5
 
 
 def test_vcycle_fp64(full):

@@ -276,6 +276,27 @@ def test_fp32_kernels(case):
             assert rel_inf(host(H.level_restrict(l, f32(x), prec=1)), O.restrict(ol, x)) <= 2e-5
 
 
+# FP32 V-cycle against the oracle's float V-cycle: both run V(1,1) with the
+# same steps in FP32 but different rounding orders (fused multiply-adds, the
+# warp-scan column sweeps of the small levels); each step is good to ~1e-6
+# relative and the cycle composes ~2 L + 12 of them with a contraction, so
+# 1e-4 in the max norm and 2e-5 in the 2-norm leave a margin of ~10.
+FP32_VCYCLE_INF, FP32_VCYCLE_2 = 1e-4, 2e-5
+
+
+def test_vcycle_fp32(case):
+    P, lev, p, H = case
+    l32 = O.float_levels(lev)
+    r = np.random.default_rng(31).standard_normal(lev[0].shape).astype(np.float32)
+    got = host(H.vcycle(dev(r, torch.float32), prec=1))
+    ref = O.vcycle(l32, r, p)
+    assert rel_inf(got, ref) <= FP32_VCYCLE_INF
+    assert rel_2(got, ref) <= FP32_VCYCLE_2
+    # the FP32 hierarchy holds c H: its cycle approximates the FP64 one / c
+    e64 = host(H.vcycle(dev(r.astype(np.float64))))
+    assert rel_2(got * l32[0].scale, e64) <= 1e-4
+
+
 def test_vcycle_fp64(case):
     P, lev, p, H = case
     rng = np.random.default_rng(5)

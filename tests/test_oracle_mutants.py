@@ -13,6 +13,7 @@ import subprocess
 import pytest
 
 import test_golden_paper as golden
+import test_oracle_convergence as conv
 import test_oracle_pins as pins
 from oracle import build as obuild
 from oracle import tpmg as O
@@ -60,7 +61,7 @@ PINS = [
     pins.test_coarse_operator_conserves_volume_and_stays_spd,
     pins.test_transfers_adjoint_and_exact_for_linear_fields,
     pins.test_vcycle_symmetric_positive_linear,
-    pins.test_convergence_factor_on_small_workload,
+    conv.test_one_order_of_magnitude_per_iteration,
     pins.test_gradient_matches_dense_lu_and_finite_differences,
     pins.test_presmooth_residual_is_the_exact_residual_of_the_sweep,
 ]

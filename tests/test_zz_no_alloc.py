@@ -1,4 +1,5 @@
-"""The allocation-free residual entry point against the library's own ones.
+"""The allocation-free residual entry point against the oracle and the
+library's own entry points.
 
 mg_residual_norm_noalloc serves callers that cannot allocate device memory
 when they need a residual check (a host model owning every device buffer
@@ -14,39 +15,83 @@ import pytest
 import torch
 
 from gpu_common import dev, handle_for, host, problem, rel_inf
+from oracle import tpmg as O
 
 pytestmark = pytest.mark.gpu
 
 
-def _call(lib, L, grid, co, b, x):
-    r = torch.empty_like(b)
+def _call(lib, grid, co, b, x, r):
     rel = ctypes.c_double(-1.0)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     st = lib.mg_residual_norm_noalloc(ctypes.byref(grid), ctypes.byref(co),
                                       ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
                                       ctypes.c_void_p(r.data_ptr()), ctypes.byref(rel), stream)
-    return st, r, rel.value
+    return st, rel.value
 
 
-def test_noalloc_residual_matches_handle_entry_points_twice():
+def _setup(nlon=64, nlat=32, nz=16):
     from paper_2307_04528_gb300 import _lib as L
-    lib = L.load()
-    nlon, nlat, nz = 64, 32, 16
     P = problem(nlon, nlat, nz, sigma=0.1, seed=42)
     coeffs = [dev(P[k]) for k in ("tx", "ty", "tz", "h")]
-    H = handle_for(P, mixed=0)
-    b = dev(P["b"])
     grid = L.mg_grid(nlon, nlat, nz)
     co = L.mg_coeffs(*(t.data_ptr() for t in coeffs))
+    return L, L.load(), P, coeffs, grid, co
+
+
+def test_noalloc_residual_matches_oracle_and_handle_twice():
+    L, lib, P, coeffs, grid, co = _setup()
+    H = handle_for(P, mixed=0)
+    fine = O.build_hierarchy(P["tx"], P["ty"], P["tz"], P["h"], O.MGParams(levels=1))[0]
+    b = dev(P["b"])
+    r = torch.empty_like(b)
     # two calls in a row with different iterates: nothing may carry over
     for tol in (1e-4, 1e-9):
         x, info = H.solve(b, tol=tol)
-        st, r, rel = _call(lib, L, grid, co, b, x)
+        st, rel = _call(lib, grid, co, b, x, r)
         assert st == 0, lib.mg_last_error()
-        r_ref = H.level_residual(0, b, x)
         torch.cuda.synchronize()
+        r_orc = O.residual(fine, P["b"], host(x))
+        assert rel_inf(host(r), r_orc) <= 1e-13
+        rel_orc = O.norm2(r_orc) / O.norm2(P["b"])
+        assert abs(rel - rel_orc) <= 1e-12 * rel_orc
+        r_ref = H.level_residual(0, b, x)
         assert rel_inf(host(r), host(r_ref)) <= 1e-13
         assert abs(rel - info["rel_res"]) <= 1e-12 * info["rel_res"]
+
+
+def test_noalloc_allocates_no_device_memory():
+    L, lib, P, coeffs, grid, co = _setup()
+    b = dev(P["b"])
+    x = torch.zeros_like(b)
+    r = torch.empty_like(b)
+    assert _call(lib, grid, co, b, x, r)[0] == 0  # first call: the array's address is looked up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        st, rel = _call(lib, grid, co, b, x, r)
+        assert st == 0 and rel == pytest.approx(1.0, abs=1e-15)  # x = 0: r = b
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_noalloc_rejects_nonfinite_norms():
+    L, lib, P, coeffs, grid, co = _setup()
+    x = torch.zeros(P["b"].shape, dtype=torch.float64, device="cuda")
+    r = torch.empty_like(x)
+    for bad in (np.inf, np.nan):
+        bh = P["b"].copy()
+        bh[3, 5, 7] = bad
+        st, rel = _call(lib, grid, co, dev(bh), x, r)
+        assert st == L.MG_ERR_NONFINITE, (bad, st)
+        assert rel == -1.0  # left untouched
+    b = dev(P["b"])
+    bh = P["b"].copy()
+    bh[0, 0, 0] = 1e300  # b finite, but the squared norms overflow to Inf
+    st, _ = _call(lib, grid, co, dev(bh), x, r)
+    assert st == L.MG_ERR_NONFINITE
+    st, rel = _call(lib, grid, co, b, x, r)  # the entry point stays usable
+    assert st == 0 and rel == pytest.approx(1.0, abs=1e-15)
 
 
 def test_noalloc_rejects_grids_beyond_its_static_scratch():
@@ -55,6 +100,6 @@ def test_noalloc_rejects_grids_beyond_its_static_scratch():
     grid = L.mg_grid(4096, 1024, 1)    # 4,194,304 columns > 2,097,152
     one = torch.zeros(1, dtype=torch.float64, device="cuda")
     co = L.mg_coeffs(*(one.data_ptr(),) * 4)
-    st, _, _ = _call(lib, L, grid, co, one, one)
+    st, _ = _call(lib, grid, co, one, one, one)
     assert st == L.MG_ERR_ARG
     assert b"static scratch limit" in lib.mg_last_error()
