@@ -57,6 +57,8 @@ def parse():
                     metavar=("NLON", "NLAT", "NZ"))
     ap.add_argument("--launches", type=int, default=5)
     ap.add_argument("--sigma", type=float, default=0.2)
+    ap.add_argument("--krylov-maxit", type=int, default=8000,
+                    help="iteration cap of the line-relaxed BiCGStab in --workload krylov")
     return ap.parse_args()
 
 
@@ -617,6 +619,10 @@ PROBE_KERNELS = {
     # kernels, the fused direction update + apply, the FP64 refinement residual)
     "solve_mixed": (1, "solve_mixed", None),
     "solve64": (0, "solve", None),
+    # a batch of three systems (--shape, half and quarter of it in longitude
+    # and latitude), FP32 multigrid in FP64 refinement to 1e-8 (the batched
+    # persistent kernels)
+    "batch_mixed": (1, "batch", None),
 }
 
 
@@ -635,6 +641,12 @@ def run_kernel(args):
     d = lambda a, dt=torch.float64: torch.as_tensor(a).to("cuda", dt)
     H = MGHandle(d(P["tx"]), d(P["ty"]), d(P["tz"]), d(P["h"]), mixed=1)
     prec, op, words = PROBE_KERNELS[args.kernel]
+    if op == "batch":
+        from paper_2307_04528_gb300.solver import MGBatch
+        probs = [P] + [make_problem(nlon // f, nlat // f, nz, args.sigma, 3000 + f) for f in (2, 4)]
+        B = MGBatch([tuple(d(Q[k]) for k in ("tx", "ty", "tz", "h")) for Q in probs], mixed=1)
+        bs = [d(Q["b"]) for Q in probs]
+        xs = [torch.zeros_like(bb) for bb in bs]
     dt = torch.float32 if prec == 1 else torch.float64
     gen = torch.Generator(device="cuda").manual_seed(0)
     shape = (nz, nlat, nlon)
@@ -676,6 +688,10 @@ def run_kernel(args):
         if op == "solve":
             x64.zero_()
             return H.solve(b64, x64, tol=TOL)
+        if op == "batch":
+            for xx in xs:
+                xx.zero_()
+            return B.solve(bs, xs, tol=1e-8, mixed=True)
         return H.level_prolong_add(0, ec, u, prec=prec)
 
     run()
@@ -701,10 +717,112 @@ def run_kernel(args):
     print(json.dumps(out))
 
 
+# ----------------------------------------------------------------- Krylov comparison
+def run_krylov(args):
+    """The paper's comparison (Section 1): the BiCGStab solver preconditioned
+    by vertical line relaxation that the multigrid replaced, against the
+    multigrid, on this GPU.
+
+    1536 x 1152 x 70 (the operational-size workload), FP64 to 1e-10: BiCGStab
+    with one sweep of Eq. (1) as preconditioner (capped at --krylov-maxit
+    iterations), BiCGStab and CG preconditioned by the V-cycle.  Beside the
+    paper's "about twice as fast" (Section 1; Table 1's solver times
+    17.6 vs 26.4 min on 4608 cores, a whole-model run on CPUs).
+
+    1024 x 768 x 70, single precision (Section 1: Krylov solvers run in
+    single precision can stall at tight tolerances): each method's whole
+    solve in FP32 (mg_solve_single) to an unreachable 1e-10, with its
+    residual history, best residual and the error of its final iterate
+    against the FP64 multigrid solution; and the mixed-precision refinement
+    to 1e-10 with each method as the FP32 inner solver."""
+    import torch
+
+    from paper_2307_04528_gb300 import _lib as L
+    from paper_2307_04528_gb300.solver import MGHandle
+
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        out = fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1), out
+
+    def system(name):
+        w = WORKLOADS[name]
+        P = make_problem(w["nlon"], w["nlat"], w["nz"], w["sigma"], workload_seed(name))
+        d = lambda a: torch.as_tensor(a, dtype=torch.float64).cuda()
+        return tuple(d(P[k]) for k in ("tx", "ty", "tz", "h")), d(P["b"])
+
+    out = {"metric": "ms to 1e-10 rel residual: BiCGStab + line relaxation (Section 1) vs "
+                     "multigrid; single-precision behaviour", "unit": "ms", "n_gpus": 1,
+           "data": "synthetic"}
+    methods = {"bicgstab_line": L.MG_METHOD_BICGSTAB_LINE, "bicgstab_mg": L.MG_METHOD_BICGSTAB,
+               "cg_mg": L.MG_METHOD_CG, "stationary_mg": L.MG_METHOD_STATIONARY}
+    # ---- FP64 at the operational size
+    coeffs, b = system("latlon_1536x1152x70")
+    fp64 = {}
+    for name in ("cg_mg", "bicgstab_mg", "bicgstab_line"):
+        cap = args.krylov_maxit if name == "bicgstab_line" else 200
+        H = MGHandle(*coeffs, method=methods[name], maxit=cap)
+        x = torch.zeros_like(b)
+        if name != "bicgstab_line":  # warm-up: the V-cycle graphs are captured on first use
+            H.solve(b, x, tol=TOL, raise_on_error=False, history_cap=cap + 64)
+            x.zero_()
+        ms, (_, info) = timed(lambda: H.solve(b, x, tol=TOL, raise_on_error=False,
+                                               history_cap=cap + 64))
+        fp64[name] = {"ms": ms, "status": info["status"], "iterations": info["iterations"],
+                      "rel_res": info["rel_res"], "ms_per_iteration": ms / max(info["iterations"], 1)}
+        del H, x
+        torch.cuda.empty_cache()
+    fp64["speedup_multigrid_vs_bicgstab_line"] = fp64["bicgstab_line"]["ms"] / fp64["cg_mg"]["ms"]
+    out["latlon_1536x1152x70_fp64"] = fp64
+    del coeffs, b
+    torch.cuda.empty_cache()
+    # ---- single precision at 1024 x 768 x 70
+    coeffs, b = system("latlon_1024x768x70")
+    Href = MGHandle(*coeffs)
+    xref, _ = Href.solve(b, tol=1e-12, raise_on_error=False)
+    del Href
+    b32 = b.float()
+    single, mixed = {}, {}
+    for name, code in methods.items():
+        cap = args.krylov_maxit if name == "bicgstab_line" else 300
+        H = MGHandle(*coeffs, method=code, mixed=1, maxit=cap)
+        ms, (x32, info) = timed(lambda: H.solve_single(b32, tol=TOL, raise_on_error=False,
+                                                        history_cap=cap + 64))
+        hist = info["history"]
+        err = float(torch.linalg.vector_norm(x32.double() - xref) / torch.linalg.vector_norm(xref))
+        single[name] = {"ms": ms, "status": info["status"], "iterations": info["iterations"],
+                        "best_rel_res": min(hist) if hist else None,
+                        "best_at": hist.index(min(hist)) if hist else None,
+                        "last_rel_res": hist[-1] if hist else None,
+                        "error_vs_fp64_solution": err,
+                        "history": [float("%.3e" % h) for h in hist[:60]]}
+        Hm = MGHandle(*coeffs, method=code, mixed=1, maxit=100, inner_maxit=40)
+        x = torch.zeros_like(b)
+        Hm.solve_mixed(b, x, tol=TOL, raise_on_error=False)
+        x.zero_()
+        ms, (_, info) = timed(lambda: Hm.solve_mixed(b, x, tol=TOL, raise_on_error=False))
+        mixed[name] = {"ms": ms, "status": info["status"], "refinement_steps": info["iterations"],
+                       "fp32_iterations": info["inner_iterations"], "rel_res": info["rel_res"]}
+        del H, Hm, x
+        torch.cuda.empty_cache()
+    out["latlon_1024x768x70_single"] = single
+    out["latlon_1024x768x70_mixed"] = mixed
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.kernel:
         run_kernel(args)
+        return
+    if args.workload == "krylov":
+        run_krylov(args)
         return
     if args.workload == "ensemble":
         run_ensemble(args)

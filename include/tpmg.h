@@ -52,7 +52,8 @@ typedef enum {
     MG_ERR_WORKSPACE = 8       /* workspace too small or misaligned */
 } mg_status;
 
-enum { MG_METHOD_CG = 0, MG_METHOD_STATIONARY = 1 };
+enum { MG_METHOD_CG = 0, MG_METHOD_STATIONARY = 1, MG_METHOD_BICGSTAB = 2,
+       MG_METHOD_BICGSTAB_LINE = 3 };
 enum { MG_PREC_FP64 = 0, MG_PREC_FP32 = 1 };
 enum { MG_COARSE_JACOBI = 0, MG_COARSE_PCG = 1 };
 
@@ -75,8 +76,13 @@ typedef struct {
                           4 is the shallow hierarchy of Section 2.3 */
     int nu1, nu2;      /* pre/post smoothing sweeps (V(1,1) default) */
     int coarse_iters;  /* block-Jacobi sweeps on the coarsest level (12) */
-    int method;        /* MG_METHOD_CG (V-cycle-preconditioned CG, default) or
-                          MG_METHOD_STATIONARY (x <- x + V(b - H x), Section 2) */
+    int method;        /* outer iteration: MG_METHOD_CG (V-cycle-preconditioned CG,
+                          default), MG_METHOD_STATIONARY (x <- x + V(b - H x), Section 2),
+                          MG_METHOD_BICGSTAB (BiCGStab preconditioned by the V-cycle), or
+                          MG_METHOD_BICGSTAB_LINE (BiCGStab preconditioned by line_sweeps
+                          sweeps of Eq. (1) from zero: the solver of Section 1 that the
+                          multigrid replaced; only the fine level takes part).
+                          BiCGStab: single systems only (mg_batch_setup rejects it). */
     int mixed;         /* 1: also build the FP32 hierarchy for mg_solve_mixed */
     int maxit;         /* outer iterations (200) */
     int inner_maxit;   /* mixed: FP32 iterations per FP64 refinement step (12) */
@@ -91,6 +97,8 @@ typedef struct {
                           (for shallow hierarchies; V then depends nonlinearly on its input,
                           which the stationary method tolerates; CG usually does).  Single
                           systems only: mg_batch_setup rejects MG_COARSE_PCG. */
+    int line_sweeps;   /* MG_METHOD_BICGSTAB_LINE: sweeps of Eq. (1) per preconditioner
+                          application (1) */
 } mg_params;
 
 typedef struct {
@@ -150,6 +158,18 @@ int mg_solve(mg_handle *h, const double *b, double *x, double tol, mg_stats *sta
  * initial guess, out = solution. */
 int mg_solve_mixed(mg_handle *h, const double *b, double *x, double tol, mg_stats *stats,
                    void *stream);
+
+/* Solve H x = b entirely in single precision, as a model that runs its
+ * solver in FP32 would (Section 1: single-precision solves, where Krylov
+ * methods can stall at tight tolerances): FP32 storage and arithmetic in
+ * every vector, operator and preconditioner step (the FP32 hierarchy of
+ * params->mixed = 1, else MG_ERR_ARG), inner products accumulated in FP64,
+ * the configured method.  b, x: device FP32 fields (x: in = initial guess,
+ * out = solution).  The residuals in stats are FP32 ones relative to
+ * ||b||; a tolerance below the FP32 floor of this operator ends with
+ * MG_ERR_NOT_CONVERGED (x the last iterate) or MG_ERR_DIVERGED. */
+int mg_solve_single(mg_handle *h, const float *b, float *x, double tol, mg_stats *stats,
+                    void *stream);
 
 /* Coefficient gradient of a loss L(x) through H x = b (differentiable
  * solve), given the adjoint lambda = H^{-T} dL/dx (H is symmetric, so

@@ -77,7 +77,10 @@ class MGParams:
     coarse_method: str = "jacobi"  # coarsest-level solve: "jacobi" sweeps or "pcg" (CG
     #                                preconditioned by the column solves), both from zero
     alpha_c: float = 0.6       # Section 2.2 anisotropy threshold (value not printed; tuned)
-    method: str = "cg"         # outer iteration: "cg" (V-cycle-preconditioned CG) or "stationary"
+    method: str = "cg"         # outer iteration: "cg" (V-cycle-preconditioned CG), "stationary",
+    #                            "bicgstab" (V-cycle-preconditioned) or "bicgstab_line" (BiCGStab
+    #                            preconditioned by line_sweeps sweeps of Eq. (1): Section 1's solver)
+    line_sweeps: int = 1       # bicgstab_line: sweeps of Eq. (1) per preconditioner application
     maxit: int = 200
     inner_tol: float = 5e-4    # mixed precision: FP32 inner relative tolerance per refinement step
     inner_maxit: int = 12      # mixed precision: FP32 inner iterations per refinement step
@@ -459,6 +462,96 @@ def solve_cg(levels, b, tol, params, x0=None, maxit=None):
             d = z + beta * d
 
 
+def line_relaxation(lev: Level, r, sweeps: int, omega: float):
+    """The preconditioner of the BiCGStab solver the paper's multigrid
+    replaced (Section 1: BiCGStab preconditioned with vertical line
+    relaxation; Section 2.1: the iteration of Eq. (1) preconditions
+    BiCGStab in the original model): `sweeps` sweeps of Eq. (1) from a zero
+    guess on r."""
+    om = r.dtype.type(omega)
+    u = np.zeros_like(r)
+    work = np.empty_like(r)
+    for _ in range(sweeps):
+        smooth(lev, r, u, om, work)
+    return u
+
+
+def solve_bicgstab(levels, b, tol, params, x0=None, maxit=None, precond: str = "line",
+                   sweeps: int = 1):
+    """BiCGStab (van der Vorst's stabilised bi-conjugate gradients) with right
+    preconditioning M: precond "line" is the vertical line relaxation of
+    Eq. (1) (`sweeps` sweeps from zero, the solver of Section 1 that the
+    multigrid replaced), "mg" one V-cycle.  Per iteration, with the shadow
+    residual rh = r_0:
+        rho = <rh, r>;  beta = (rho / rho_old) (alpha / w)
+        p = r + beta (p - w v);  ph = M p;  v = H ph;  alpha = rho / <rh, v>
+        s = r - alpha v  (stop if ||s|| <= tol ||b||: x += alpha ph)
+        sh = M s;  t = H sh;  w = <t, s> / <t, t>
+        x += alpha ph + w sh;  r = s - w t
+    Scalars in FP64, vectors in b's precision; stops on the recursively
+    updated residual, then confirms with the true residual (restarting from
+    x, with a new shadow residual, if they disagree or on a breakdown
+    rho = 0, <rh, v> = 0 or <t, t> = 0).  One iteration = two
+    preconditioner applications and two operator applications.  Returns
+    (x, rel_history, status)."""
+    p = params
+    maxit = p.maxit if maxit is None else maxit
+    dt = b.dtype.type
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=b.dtype, copy=True)
+    bn = norm2(b)
+    hist = []
+    its = 0
+
+    def M(v):
+        if precond == "mg":
+            return vcycle(levels, v, p)
+        return line_relaxation(levels[0], v, sweeps, p.omega)
+
+    while True:
+        r = residual(levels[0], b, x)
+        rn = norm2(r)
+        hist.append(rn / bn if bn > 0 else 0.0)
+        if rn <= tol * bn:
+            return x, hist, OK
+        if its >= maxit:
+            return x, hist, NOT_CONVERGED
+        rh = r.copy()
+        rho_old = alpha = w = 1.0
+        v = np.zeros_like(b)
+        pv = np.zeros_like(b)
+        while its < maxit:
+            its += 1
+            rho = dot(rh, r)
+            if rho == 0.0:
+                break                                   # breakdown: restart
+            beta = (rho / rho_old) * (alpha / w)
+            pv = r + dt(beta) * (pv - dt(w) * v)
+            ph = M(pv)
+            v = apply(levels[0], ph)
+            rv = dot(rh, v)
+            if rv == 0.0:
+                break
+            alpha = rho / rv
+            s = r - dt(alpha) * v
+            if norm2(s) <= tol * bn:
+                x += dt(alpha) * ph
+                break                                   # confirm with the true residual
+            sh = M(s)
+            t = apply(levels[0], sh)
+            tt = dot(t, t)
+            if tt == 0.0:
+                x += dt(alpha) * ph
+                break
+            w = dot(t, s) / tt
+            x += dt(alpha) * ph + dt(w) * sh
+            r = s - dt(w) * t
+            rho_old = rho
+            rn = norm2(r)
+            if rn <= tol * bn or w == 0.0:
+                break                                   # confirm with the true residual
+            hist.append(rn / bn)
+
+
 def solve(levels, b, tol: float = 1e-10, x0=None, params: MGParams | None = None,
           maxit: int | None = None):
     """Multigrid solve of H x = b to ||b - H x||_2 <= tol ||b||_2.
@@ -466,6 +559,11 @@ def solve(levels, b, tol: float = 1e-10, x0=None, params: MGParams | None = None
     p = params or MGParams()
     if p.method == "stationary":
         return solve_stationary(levels, b, tol, p, x0, maxit)
+    if p.method == "bicgstab":
+        return solve_bicgstab(levels, b, tol, p, x0, maxit, precond="mg")
+    if p.method == "bicgstab_line":
+        return solve_bicgstab(levels, b, tol, p, x0, maxit, precond="line",
+                              sweeps=p.line_sweeps)
     return solve_cg(levels, b, tol, p, x0, maxit)
 
 

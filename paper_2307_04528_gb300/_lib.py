@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libtpmg.so")
 
 MG_OK, MG_ERR_ARG, MG_ERR_COEFF, MG_ERR_NONFINITE, MG_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
 MG_ERR_DIVERGED, MG_ERR_TIMEOUT, MG_ERR_CUDA, MG_ERR_WORKSPACE = 5, 6, 7, 8
-MG_METHOD_CG, MG_METHOD_STATIONARY = 0, 1
+MG_METHOD_CG, MG_METHOD_STATIONARY, MG_METHOD_BICGSTAB, MG_METHOD_BICGSTAB_LINE = 0, 1, 2, 3
 MG_PREC_FP64, MG_PREC_FP32 = 0, 1
 MG_COARSE_JACOBI, MG_COARSE_PCG = 0, 1
 # kernel classes of mg_profile_read
@@ -45,7 +45,8 @@ class mg_params(ctypes.Structure):
                 ("coarse_iters", ctypes.c_int), ("method", ctypes.c_int), ("mixed", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("inner_maxit", ctypes.c_int),
                 ("omega", ctypes.c_double), ("alpha_c", ctypes.c_double),
-                ("inner_tol", ctypes.c_double), ("coarse_method", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("coarse_method", ctypes.c_int),
+                ("line_sweeps", ctypes.c_int)]
 
 
 class mg_stats(ctypes.Structure):
@@ -80,6 +81,7 @@ def load() -> ctypes.CDLL:
         "mg_vcycle_prec": (I, [H, I, P, P, P]),
         "mg_solve": (I, [H, P, P, D, ctypes.POINTER(mg_stats), P]),
         "mg_solve_mixed": (I, [H, P, P, D, ctypes.POINTER(mg_stats), P]),
+        "mg_solve_single": (I, [H, P, P, D, ctypes.POINTER(mg_stats), P]),
         "mg_coeff_grad": (I, [H, P, P, P, P, P, P, P]),
         "mg_num_levels": (I, [H]),
         "mg_level_shape": (I, [H, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),

@@ -166,6 +166,11 @@ struct Carver {
 
 }  // namespace
 
+static bool is_bicgstab(int method)
+{
+    return method == MG_METHOD_BICGSTAB || method == MG_METHOD_BICGSTAB_LINE;
+}
+
 static int check_grid(const mg_grid *g, const mg_params *p, int *L_out)
 {
     if (!g || !p) return fail(MG_ERR_ARG, "null grid or params");
@@ -181,8 +186,10 @@ static int check_grid(const mg_grid *g, const mg_params *p, int *L_out)
     if (p->coarse_method != MG_COARSE_JACOBI && p->coarse_method != MG_COARSE_PCG)
         return fail(MG_ERR_ARG, "coarse_method %d unknown", p->coarse_method);
     if (p->nu1 < 1 || p->nu2 < 0 || p->coarse_iters < 1 || p->maxit < 0 ||
-        !(p->omega > 0.0 && p->omega < 2.0) || (p->method != MG_METHOD_CG &&
-                                                 p->method != MG_METHOD_STATIONARY))
+        !(p->omega > 0.0 && p->omega < 2.0) ||
+        (p->method != MG_METHOD_CG && p->method != MG_METHOD_STATIONARY &&
+         !is_bicgstab(p->method)) ||
+        (p->method == MG_METHOD_BICGSTAB_LINE && (p->line_sweeps < 1 || p->line_sweeps > 100)))
         return fail(MG_ERR_ARG, "invalid multigrid parameters");
     if ((size_t)g->nlon * g->nlat > (size_t)kReduceSlots * kBlock)
         return fail(MG_ERR_ARG, "nlon*nlat=%zu exceeds %zu columns", (size_t)g->nlon * g->nlat,
@@ -276,11 +283,17 @@ static size_t carve(mg_handle *H, void *base)
         }
     }
     const size_t n0 = H->lev[0].n;
+    const bool bicg = is_bicgstab(H->p.method);
     H->cg64.r = cv.take<double>(n0);
     H->cg64.z = cv.take<double>(n0);
     H->cg64.d0 = cv.take<double>(n0);
     H->cg64.d1 = cv.take<double>(n0);
     H->cg64.Ad = cv.take<double>(n0);
+    if (bicg) {
+        H->cg64.s = cv.take<double>(n0);
+        H->cg64.sh = cv.take<double>(n0);
+        H->cg64.t = cv.take<double>(n0);
+    }
     if (mixed) {
         H->cg32.r = cv.take<float>(n0);
         H->cg32.z = cv.take<float>(n0);
@@ -288,10 +301,16 @@ static size_t carve(mg_handle *H, void *base)
         H->cg32.d1 = cv.take<float>(n0);
         H->cg32.Ad = cv.take<float>(n0);
         H->cg32.x = cv.take<float>(n0);
+        if (bicg) {
+            H->cg32.s = cv.take<float>(n0);
+            H->cg32.sh = cv.take<float>(n0);
+            H->cg32.t = cv.take<float>(n0);
+        }
     }
     H->partial = cv.take<double>(kReduceSlots);
     H->sc = cv.take<CgScalars>(1);
     H->sc_coarse = cv.take<CgScalars>(1);
+    H->bsc = cv.take<BicgScalars>(1);
     H->flag = cv.take<int>(4);
     return cv.off + 256;
 }
@@ -312,6 +331,7 @@ extern "C" void mg_default_params(mg_params *p)
     p->alpha_c = 0.6;
     p->inner_tol = 5e-4;
     p->coarse_method = MG_COARSE_JACOBI;
+    p->line_sweeps = 1;
 }
 
 extern "C" const char *mg_last_error(void) { return g_last_error.c_str(); }
@@ -509,11 +529,12 @@ static void prof_release(mg_handle *H)
 
 static void graphs_release(mg_handle *H)
 {
-    for (VGraph &g : H->vg) {
-        if (g.exec) cudaGraphExecDestroy(g.exec);
-        if (g.graph) cudaGraphDestroy(g.graph);
-        g = VGraph{};
-    }
+    for (auto &per_prec : H->vg)
+        for (VGraph &g : per_prec) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            if (g.graph) cudaGraphDestroy(g.graph);
+            g = VGraph{};
+        }
 }
 
 extern "C" void mg_destroy(mg_handle *h)
@@ -697,31 +718,35 @@ static int vcycle_fine(mg_handle *H, const T *r, T *e, cudaStream_t s, int *dot_
     return vcycle_level<T>(H, 0, r, e, Vec<T>::w(f), Vec<T>::r(f), s, dot_blocks);
 }
 
-// z = V r for the solver's fixed vectors (cg.r -> cg.z), replayed from a CUDA
-// graph captured on first use; direct launches while profiling (events
-// around each kernel) or if capture is unavailable.
-// *dot_blocks: partial sums of <cg.r, cg.z> left in H->partial by the fused
-// last sweep (0: none, compute the inner product separately).
+// out = V in for one of the solver's fixed vector pairs (slot 0: cg.r -> cg.z;
+// BiCGStab: 1 p -> ph, 2 s -> sh), replayed from a CUDA graph captured on
+// first use for that pair; direct launches while profiling (events around
+// each kernel) or if capture is unavailable.
+// dot_blocks (slot 0 only): partial sums of <in, out> left in H->partial by
+// the fused last sweep (0: none, compute the inner product separately).
 template <typename T>
-static int vcycle_solver(mg_handle *H, cudaStream_t s, int *dot_blocks)
+static int vcycle_graph(mg_handle *H, int slot, const T *in, T *out, cudaStream_t s,
+                        int *dot_blocks)
 {
-    CgVecs<T> &cg = Vec<T>::cg(H);
     constexpr int P = prec_of<T>();
-    if (!H->use_graphs || H->prof.on) return vcycle_fine<T>(H, cg.r, cg.z, s, dot_blocks);
-    VGraph &g = H->vg[P];
+    if (!H->use_graphs || H->prof.on) return vcycle_fine<T>(H, in, out, s, dot_blocks);
+    VGraph &g = H->vg[P][slot];
     if (!g.exec) {
         g.kernels = 0;
         CU(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
         H->capturing = true;
-        const int st = vcycle_fine<T>(H, cg.r, cg.z, H->cap_stream, &g.dot_blocks);
+        H->cap_graph = &g;
+        const int st = vcycle_fine<T>(H, in, out, H->cap_stream, dot_blocks ? &g.dot_blocks : nullptr);
         H->capturing = false;
+        H->cap_graph = nullptr;
         cudaGraph_t graph = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(H->cap_stream, &graph);
         if (st != MG_OK || ec != cudaSuccess || !graph) {
             if (graph) cudaGraphDestroy(graph);
             cudaGetLastError();
+            g = VGraph{};
             H->use_graphs = false;  // run the same kernels without a graph from now on
-            return vcycle_fine<T>(H, cg.r, cg.z, s, dot_blocks);
+            return vcycle_fine<T>(H, in, out, s, dot_blocks);
         }
         const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
         if (ei != cudaSuccess) {
@@ -729,21 +754,144 @@ static int vcycle_solver(mg_handle *H, cudaStream_t s, int *dot_blocks)
             cudaGetLastError();
             g = VGraph{};
             H->use_graphs = false;
-            return vcycle_fine<T>(H, cg.r, cg.z, s, dot_blocks);
+            return vcycle_fine<T>(H, in, out, s, dot_blocks);
         }
         g.graph = graph;
     }
     CU(cudaGraphLaunch(g.exec, s));
-    *dot_blocks = g.dot_blocks;
+    if (dot_blocks) *dot_blocks = g.dot_blocks;
     g_launches.fetch_add(g.kernels, std::memory_order_relaxed);
     return MG_OK;
+}
+
+template <typename T>
+static int vcycle_solver(mg_handle *H, cudaStream_t s, int *dot_blocks)
+{
+    CgVecs<T> &cg = Vec<T>::cg(H);
+    return vcycle_graph<T>(H, 0, cg.r, cg.z, s, dot_blocks);
 }
 
 // ------------------------------------------------------------------ solvers
 static bool bad(double v) { return !(v == v) || std::isinf(v); }
 
+// rr and the breakdown flag of the BiCGStab scalars (one copy, synchronises).
+static int read_bicg(mg_handle *H, double *rr, double *brk, cudaStream_t s)
+{
+    double v[2] = {0, 0};
+    CU(cudaMemcpyAsync(v, &H->bsc->rr, sizeof v, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    *rr = v[0];
+    if (brk) *brk = v[1];
+    return MG_OK;
+}
+
+// The BiCGStab preconditioner, in -> out: one V-cycle (graph slot 1 or 2),
+// or line_sweeps sweeps of Eq. (1) from zero on the fine level.
+template <typename T>
+static int bicg_precond(mg_handle *H, int slot, const T *in, T *out, cudaStream_t s)
+{
+    if (H->p.method == MG_METHOD_BICGSTAB) return vcycle_graph<T>(H, slot, in, out, s, nullptr);
+    LevelHost &f = H->lev[0];
+    return smooth_from_zero<T>(H, 0, dev<T>(f), in, out, Vec<T>::w(f), H->p.line_sweeps,
+                               H->p.omega, s);
+}
+
+// BiCGStab with right preconditioning (the solver of Section 1 that the
+// multigrid replaced, with the line relaxation of Eq. (1) as preconditioner,
+// or with the V-cycle):
+//   rho = <rh, r>;  beta = (rho / rho_old) (alpha / omega)
+//   p = r + beta (p - omega v);  ph = M p;  v = H ph;  alpha = rho / <rh, v>
+//   s = r - alpha v;  sh = M s;  t = H sh;  omega = <t, s> / <t, t>
+//   x += alpha ph + omega sh;  r = s - omega t
+// Scalars on the device; one host read per iteration (||r||, breakdown).
+// Stops on the recursively updated residual and confirms with the true
+// residual, restarting with a new shadow residual rh = r when they disagree
+// or on a breakdown (rho or <rh, v> zero).  inner: as in solve_impl.
+template <typename T>
+static int solve_bicgstab(mg_handle *H, const T *b, T *x, double tol, int maxit,
+                          std::vector<double> *hist, int *its_out, double *rel_out,
+                          cudaStream_t s, bool inner, bool x_zero, double bb)
+{
+    LevelHost &f = H->lev[0];
+    const LevelDev<T> D = dev<T>(f);
+    const size_t n = f.n;
+    CgVecs<T> &cg = Vec<T>::cg(H);
+    T *r = cg.r, *rh = cg.Ad, *p = cg.d0, *ph = cg.z, *v = cg.d1;
+    T *sv = cg.s, *sh = cg.sh, *t = cg.t;
+    if (!sv || !sh || !t) return fail(MG_ERR_ARG, "handle built without the BiCGStab vectors");
+    BicgScalars *sc = H->bsc;
+    double *pa = H->partial, *pb = H->partial + kReduceSlots / 2;
+    constexpr int P = prec_of<T>();
+    const double bn = std::sqrt(bb);
+    int its = 0;
+    double rel = 0, rr0 = -1;
+    auto record = [&](double rr) {
+        rel = bn > 0 ? std::sqrt(rr) / bn : 0.0;
+        if (hist) hist->push_back(rel);
+        *its_out = its;
+        *rel_out = rel;
+    };
+    bool first_outer = true;
+    while (true) {
+        double rr = 0, brk = 0;
+        int nb = 0;
+        if (x_zero && first_outer) {
+            KRUN(K_VEC, 0, P, launch_bicg_dir<T>(r, b, nullptr, n, sc, true, s));  // r = b
+        } else {
+            KRUN(K_RESID, 0, P, launch_stencil<T>(D, 1, b, x, r, nullptr, s));
+        }
+        first_outer = false;
+        KRUN(K_VEC, 0, P, nb = launch_dot<T>(r, r, n, pa, s));
+        KRUN(K_VEC, 0, P, launch_bicg_finalize(pa, nullptr, nb, sc, BICG_START, s));
+        CHK(read_bicg(H, &rr, nullptr, s));
+        if (bad(rr)) return fail(MG_ERR_NONFINITE, "non-finite residual");
+        if (rr0 < 0) rr0 = rr;
+        record(rr);
+        *its_out = its;
+        *rel_out = rel;
+        if (std::sqrt(rr) <= tol * bn) return MG_OK;
+        if (its >= maxit)
+            return fail(MG_ERR_NOT_CONVERGED, "not converged after %d iterations (rel %.3e)", its,
+                        rel);
+        if (rr > 1e6 * rr0) return fail(MG_ERR_DIVERGED, "residual grew to %.3e", rel);
+        KRUN(K_VEC, 0, P, launch_bicg_dir<T>(rh, r, nullptr, n, sc, true, s));  // rh = r
+        bool first = true;
+        while (its < maxit) {
+            ++its;
+            KRUN(K_VEC, 0, P, launch_bicg_dir<T>(p, r, v, n, sc, first, s));
+            first = false;
+            CHK(bicg_precond<T>(H, 1, p, ph, s));
+            KRUN(K_APPLY, 0, P, launch_stencil<T>(D, 0, nullptr, ph, v, nullptr, s));
+            KRUN(K_VEC, 0, P, nb = launch_dot<T>(rh, v, n, pa, s));
+            KRUN(K_VEC, 0, P, launch_bicg_finalize(pa, nullptr, nb, sc, BICG_ALPHA, s));
+            KRUN(K_VEC, 0, P, launch_bicg_s<T>(sv, r, v, n, sc, s));
+            CHK(bicg_precond<T>(H, 2, sv, sh, s));
+            KRUN(K_APPLY, 0, P, launch_stencil<T>(D, 0, nullptr, sh, t, nullptr, s));
+            KRUN(K_VEC, 0, P, nb = launch_dot2<T>(t, sv, n, pa, pb, s));
+            KRUN(K_VEC, 0, P, launch_bicg_finalize(pa, pb, nb, sc, BICG_OMEGA, s));
+            KRUN(K_VEC, 0, P,
+                 nb = launch_bicg_update<T>(x, r, ph, sh, sv, t, rh, n, sc, pa, pb, s));
+            KRUN(K_VEC, 0, P, launch_bicg_finalize(pa, pb, nb, sc, BICG_NEXT, s));
+            CHK(read_bicg(H, &rr, &brk, s));
+            if (bad(rr)) return fail(MG_ERR_NONFINITE, "non-finite residual");
+            if (std::sqrt(rr) <= tol * bn || its >= maxit || brk != 0.0) {
+                if (inner && brk == 0.0) {
+                    record(rr);
+                    *its_out = its;
+                    *rel_out = rel;
+                    return std::sqrt(rr) <= tol * bn ? MG_OK : MG_ERR_NOT_CONVERGED;
+                }
+                break;  // confirm with the true residual (restart on a breakdown)
+            }
+            record(rr);
+            if (rr > 1e6 * rr0) return fail(MG_ERR_DIVERGED, "residual grew to %.3e", rel);
+        }
+    }
+}
+
 // Conjugate gradients preconditioned by one V-cycle, or the stationary
-// iteration x <- x + V(b - H x) (Section 2).  Scalars in FP64.
+// iteration x <- x + V(b - H x) (Section 2), or BiCGStab (solve_bicgstab).
+// Scalars in FP64.
 // inner: the inner solve of the mixed-precision refinement: x enters as 0
 // (so r = b without a stencil) and the recursively updated residual decides
 // (the FP64 outer residual is the check), no confirming residual.
@@ -764,6 +912,9 @@ static int solve_impl(mg_handle *H, const T *b, T *x, double tol, int maxit, int
         CHK(read_scalar(H, S_RR, &bb, s));
     }
     if (bad(bb)) return fail(MG_ERR_NONFINITE, "non-finite right-hand side");
+    if (is_bicgstab(method))
+        return solve_bicgstab<T>(H, b, x, tol, maxit, hist, its_out, rel_out, s, inner,
+                                 inner || x_zero, bb);
     const double bn = std::sqrt(bb);
     constexpr int P = prec_of<T>();
     int its = 0;
@@ -771,6 +922,8 @@ static int solve_impl(mg_handle *H, const T *b, T *x, double tol, int maxit, int
     auto record = [&](double rr) {
         rel = bn > 0 ? std::sqrt(rr) / bn : 0.0;
         if (hist) hist->push_back(rel);
+        *its_out = its;
+        *rel_out = rel;
     };
     bool first = true;
     while (true) {
@@ -982,6 +1135,31 @@ extern "C" int mg_solve_mixed(mg_handle *H, const double *b, double *x, double t
         ++outer;
     }
     fill_stats(st, hist, outer, inner, rel);
+    return rc;
+}
+
+extern "C" int mg_solve_single(mg_handle *H, const float *b, float *x, double tol, mg_stats *st,
+                               void *stream)
+{
+    if (!H || !b || !x || b == x) return fail(MG_ERR_ARG, "bad solve buffers");
+    if (!H->p.mixed) return fail(MG_ERR_ARG, "handle built without the FP32 hierarchy (mixed=0)");
+    if (!(tol >= 0)) return fail(MG_ERR_ARG, "tol must be >= 0");
+    LevelHost &f = H->lev[0];
+    const CgVecs<float> &cg = H->cg32;
+    for (const void *q : {(const void *)cg.r, (const void *)cg.z, (const void *)cg.d0,
+                          (const void *)cg.d1, (const void *)cg.Ad, (const void *)cg.x,
+                          (const void *)cg.s, (const void *)cg.sh, (const void *)cg.t,
+                          (const void *)f.w32, (const void *)f.r32, (const void *)f.b32})
+        if (q && (q == b || q == x)) return fail(MG_ERR_ARG, "buffer aliases a solver vector");
+    cudaStream_t s = (cudaStream_t)stream;
+    // the FP32 hierarchy holds c H: solve (c H) y = b and return x = c y
+    KRUN(K_VEC, 0, 1, launch_scale<float>(x, 1.0 / H->scale32, f.n, s));
+    std::vector<double> hist;
+    int its = 0;
+    double rel = 0;
+    const int rc = solve_impl<float>(H, b, x, tol, H->p.maxit, H->p.method, &hist, &its, &rel, s);
+    KRUN(K_VEC, 0, 1, launch_scale<float>(x, H->scale32, f.n, s));
+    fill_stats(st, hist, its, 0, rel);
     return rc;
 }
 

@@ -320,8 +320,7 @@ __device__ __forceinline__ double bvec_chunk(T *__restrict__ a, T *__restrict__ 
         } else if (OP == BV_ADD) {
             a[i] += b[i];
         } else {
-            const double m = fabs((double)a[i]);
-            acc = (m > acc || m != m) ? m : acc;
+            acc = max_mag(acc, (double)a[i]);  // NaN propagates
         }
     }
     return OP == BV_MAXABS ? acc : (double)tacc;
@@ -412,7 +411,7 @@ k_bfinalize(const double *__restrict__ partial, const int *__restrict__ beg,
     const int p0 = beg[sys], p1 = end[sys];
     double v = 0;
     for (int c = p0 + threadIdx.x; c < p1; c += blockDim.x)
-        v = op == 3 ? ((partial[c] > v || partial[c] != partial[c]) ? partial[c] : v) : v + partial[c];
+        v = op == 3 ? max_mag(v, partial[c]) : v + partial[c];
     __shared__ double ws[8];
     v = op == 3 ? warp_reduce<1>(v) : warp_reduce<0>(v);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;

@@ -1100,6 +1100,9 @@ extern "C" int mg_batch_workspace_bytes(int n, const mg_grid *grids, const mg_pa
     if (n < 1 || !grids || !params || !bytes) return fail(MG_ERR_ARG, "bad batch arguments");
     if (params->coarse_method != MG_COARSE_JACOBI)
         return fail(MG_ERR_ARG, "batched solves take the block-Jacobi coarsest-level solve");
+    if (params->method != MG_METHOD_CG && params->method != MG_METHOD_STATIONARY)
+        return fail(MG_ERR_ARG, "batched solves take conjugate gradients or the stationary "
+                                "iteration");
     mg_batch *B = batch_new(n, grids, params);
     size_t total = 0;
     const int st = batch_layout(B, nullptr, &total);
@@ -1117,6 +1120,9 @@ extern "C" int mg_batch_setup(int n, const mg_grid *grids, const mg_coeffs *coef
     if (n < 1 || !grids || !coeffs || !params) return fail(MG_ERR_ARG, "bad batch arguments");
     if (params->coarse_method != MG_COARSE_JACOBI)
         return fail(MG_ERR_ARG, "batched solves take the block-Jacobi coarsest-level solve");
+    if (params->method != MG_METHOD_CG && params->method != MG_METHOD_STATIONARY)
+        return fail(MG_ERR_ARG, "batched solves take conjugate gradients or the stationary "
+                                "iteration");
     if (!workspace || (uintptr_t)workspace % 256)
         return fail(MG_ERR_WORKSPACE, "workspace null or not 256-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;

@@ -11,13 +11,25 @@
 namespace tpmg {
 
 // ------------------------------------------------------------------ reductions
-template <int OP>  // 0: sum, 1: max
+// Maximum of two magnitudes (values >= 0 or NaN): non-negative doubles order
+// as their bit patterns read as unsigned integers, and a NaN sorts above
+// +Inf, so the integer maximum of the sign-cleared patterns is the maximum
+// with NaN propagated, taken on the integer pipe instead of FP64 compares.
+__device__ __forceinline__ double max_mag(double a, double b)
+{
+    constexpr unsigned long long kAbs = 0x7fffffffffffffffULL;
+    const unsigned long long ia = (unsigned long long)__double_as_longlong(a) & kAbs;
+    const unsigned long long ib = (unsigned long long)__double_as_longlong(b) & kAbs;
+    return __longlong_as_double((long long)(ia > ib ? ia : ib));
+}
+
+template <int OP>  // 0: sum, 1: maximum magnitude (max_mag)
 __device__ __forceinline__ double warp_reduce(double v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         double w = __shfl_down_sync(0xffffffffu, v, o);
-        v = OP == 0 ? v + w : fmax(v, w);
+        v = OP == 0 ? v + w : max_mag(v, w);
     }
     return v;
 }

@@ -47,6 +47,7 @@ using tpmg::LinkHost;
 using tpmg::LevelDev;
 using tpmg::LinkDev;
 using tpmg::CgScalars;
+using tpmg::BicgScalars;
 
 // ------------------------------------------------------------------ handle
 struct LevelHost {
@@ -67,9 +68,14 @@ struct LevelHost {
     LinkDev linkdev{};
 };
 
+// Fine-level vectors of the outer iterations.  Conjugate gradients use r, z,
+// d0, d1, Ad (x: the FP32 inner solution of the mixed solve).  BiCGStab
+// (carved only for its methods) uses r, rh = Ad, p = d0, ph = z, v = d1 and
+// s, sh, t.
 template <typename T>
 struct CgVecs {
     T *r = nullptr, *z = nullptr, *d0 = nullptr, *d1 = nullptr, *Ad = nullptr, *x = nullptr;
+    T *s = nullptr, *sh = nullptr, *t = nullptr;
 };
 
 struct ProfRec {
@@ -101,8 +107,12 @@ struct mg_handle {
     void *batch_x = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
     bool capturing = false;
+    VGraph *cap_graph = nullptr;        // the graph being captured
     bool use_graphs = true;
-    VGraph vg[2];                       // [MG_PREC_FP64], [MG_PREC_FP32]
+    // V-cycles captured per precision [MG_PREC_FP64], [MG_PREC_FP32] and
+    // vector pair: 0 r -> z (conjugate gradients, stationary), 1 p -> ph and
+    // 2 s -> sh (BiCGStab)
+    VGraph vg[2][3];
     mg_grid grid{};
     mg_params p{};
     int L = 0;
@@ -112,6 +122,7 @@ struct mg_handle {
     double *partial = nullptr;
     CgScalars *sc = nullptr;
     CgScalars *sc_coarse = nullptr;  // scalars of the PCG coarse solve
+    BicgScalars *bsc = nullptr;      // scalars of BiCGStab
     int *flag = nullptr;
     double scale32 = 0.0;
 };
@@ -171,7 +182,7 @@ inline int run_k(mg_handle *H, int kind, int level, int prec, cudaStream_t s, F 
         CU(cudaEventRecord(a, s));
     }
     const cudaError_t e = f();
-    if (H->capturing) ++H->vg[prec].kernels;
+    if (H->capturing) ++H->cap_graph->kernels;
     else tpmg::g_launches.fetch_add(1, std::memory_order_relaxed);
     if (e != cudaSuccess)
         return tpmg::fail(MG_ERR_CUDA, "kernel launch (kind %d, level %d): %s", kind, level,

@@ -38,6 +38,12 @@ struct CgScalars {
     double rz, rz_new, dAd, rr, alpha, beta, maxabs, pad;
 };
 
+// Device-side scalars of a BiCGStab iteration (brk: a breakdown was met).
+struct BicgScalars {
+    double rho, alpha, omega, beta, rv, ts, tt, rr, brk, pad;
+};
+enum { BICG_START = 0, BICG_ALPHA = 1, BICG_OMEGA = 2, BICG_NEXT = 3 };
+
 constexpr int kBlock = 128;          // threads per block, one column per thread
 constexpr int kMaxLayers = 192;      // MG_MAX_NZ of the C ABI (checked in tpmg_api.cpp)
 constexpr int kMaxRestrictRows = 4;  // fine rows per coarse row of the restriction (checked at setup)
@@ -136,6 +142,33 @@ int launch_cg_update(T *x, T *r, const T *d, const T *Ad, size_t n, const CgScal
 template <typename T>
 cudaError_t launch_cg_direction(const T *z, const T *d_in, T *d_out, size_t n,
                                 const CgScalars *sc, bool beta_zero, cudaStream_t s);
+
+// Grid of the vector kernels for n elements (one wave of full occupancy).
+int vec_grid(size_t n);
+
+// ---- BiCGStab vector steps (tpmg_krylov.cu); scalars read from sc ----
+// p = r (first) or p = r + beta (p - omega v)
+template <typename T>
+cudaError_t launch_bicg_dir(T *p, const T *r, const T *v, size_t n, const BicgScalars *sc,
+                            bool first, cudaStream_t s);
+// s = r - alpha v
+template <typename T>
+cudaError_t launch_bicg_s(T *sv, const T *r, const T *v, size_t n, const BicgScalars *sc,
+                          cudaStream_t s);
+// per-block <t, s> into pa and <t, t> into pb; returns the number of blocks
+template <typename T>
+int launch_dot2(const T *t, const T *sv, size_t n, double *pa, double *pb, cudaStream_t s);
+// x += alpha ph + omega sh; r = s - omega t; per-block <r, r> (pa), <rh, r> (pb)
+template <typename T>
+int launch_bicg_update(T *x, T *r, const T *ph, const T *sh, const T *sv, const T *t,
+                       const T *rh, size_t n, const BicgScalars *sc, double *pa, double *pb,
+                       cudaStream_t s);
+// fixed-order sums of the partials and the scalar step op (BICG_*)
+cudaError_t launch_bicg_finalize(const double *pa, const double *pb, int n, BicgScalars *sc,
+                                 int op, cudaStream_t s);
+// x *= f
+template <typename T>
+cudaError_t launch_scale(T *x, double f, size_t n, cudaStream_t s);
 
 // x += e (same precision)
 template <typename T>

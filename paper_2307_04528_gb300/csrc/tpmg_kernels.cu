@@ -509,6 +509,8 @@ static inline int red_grid(size_t n)
     return (int)g;
 }
 
+int vec_grid(size_t n) { return red_grid(n); }
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_dot(const T *__restrict__ a, const T *__restrict__ b, size_t n, double *partial)
@@ -535,10 +537,8 @@ __global__ void __launch_bounds__(kBlock) k_maxabs(const T *__restrict__ a, size
     double m = 0;
 #pragma unroll 4
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
-         c += (size_t)gridDim.x * blockDim.x) {
-        const double v = fabs((double)a[c]);
-        m = v > m ? v : (v != v ? v : m);  // propagate NaN
-    }
+         c += (size_t)gridDim.x * blockDim.x)
+        m = max_mag(m, (double)a[c]);  // NaN propagates
     block_store<1>(m, partial);
 }
 
@@ -653,7 +653,7 @@ k_finalize(const double *__restrict__ partial, int n, CgScalars *sc, int which, 
     __shared__ double ws[32];
     double v = 0;
     for (int c = threadIdx.x; c < n; c += blockDim.x)
-        v = op == 3 ? (partial[c] > v || partial[c] != partial[c] ? partial[c] : v) : v + partial[c];
+        v = op == 3 ? max_mag(v, partial[c]) : v + partial[c];
     if (op == 3) v = warp_reduce<1>(v);
     else v = warp_reduce<0>(v);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;

@@ -37,7 +37,7 @@ class MGHandle:
     tx, ty, tz, h: CUDA float64 tensors (copied into the workspace at setup).
     params: keyword overrides of mg_params (levels, nu1, nu2, coarse_iters,
     method, mixed, maxit, inner_maxit, omega, alpha_c, inner_tol,
-    coarse_method).
+    coarse_method, line_sweeps).
     """
 
     @classmethod
@@ -141,6 +141,22 @@ class MGHandle:
     def solve_mixed(self, b, x=None, tol=1e-10, history_cap=512, raise_on_error=True):
         """FP32 multigrid inside FP64 refinement (needs mixed=1 at setup)."""
         return self._solve(self.lib.mg_solve_mixed, b, x, tol, history_cap, raise_on_error)
+
+    def solve_single(self, b, x=None, tol=1e-6, history_cap=4096, raise_on_error=True):
+        """The whole solve in FP32 (float32 b and x; needs mixed=1 at setup),
+        with the configured method; x is the initial guess, overwritten."""
+        _field(b, torch.float32, self.shape, "b")
+        x = torch.zeros_like(b) if x is None else x
+        _field(x, torch.float32, self.shape, "x")
+        hist = (ctypes.c_double * history_cap)()
+        st = L.mg_stats(0, 0, 0.0, hist, history_cap, 0)
+        status = self.lib.mg_solve_single(self._hh, _ptr(b), _ptr(x), float(tol),
+                                          ctypes.byref(st), _stream())
+        if raise_on_error:
+            L.check(status)
+        info = dict(status=status, iterations=st.iterations, rel_res=st.rel_res,
+                    history=[hist[i] for i in range(st.history_len)])
+        return x, info
 
     def coeff_grad(self, lam, x):
         outs = [torch.empty_like(x) for _ in range(4)]
