@@ -607,6 +607,7 @@ PROBE_KERNELS = {
     "presmooth_restrict32": (1, "presmooth_restrict", None),
     "prolong32": (1, "prolong", None),
     "coarse32": (1, "coarse", None),
+    "dir_apply32": (1, "dir_apply", 8),
     "vcycle32": (1, "vcycle", None),
     "smooth64": (0, "smooth", 8),
     "smooth64_zero": (0, "smooth0", 5),
@@ -682,6 +683,8 @@ def run_kernel(args):
             return H.vcycle(b, prec=prec)
         if op == "coeff_grad":
             return H.coeff_grad(b, u)
+        if op == "dir_apply":
+            return H.level_dir_apply(0, b, u, 0.5, prec=prec)
         if op == "solve_mixed":
             x64.zero_()
             return H.solve_mixed(b64, x64, tol=TOL)

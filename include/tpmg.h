@@ -250,6 +250,16 @@ int mg_level_relax(mg_handle *h, int level, int prec, int sweeps, const void *b,
 int mg_level_smooth_dot(mg_handle *h, int level, int prec, const void *b, const void *u_in,
                         void *u_out, double *dot, void *stream);
 
+/* The fused step of the conjugate-gradient iteration preconditioned by the
+ * V-cycle (Section 2's multigrid as a preconditioner) on level l:
+ *   d_new = z + beta d_old  (d_old == NULL: d_new = z),  q = H_l d_new,
+ * and *dot = <d_new, q> (host double; FP64 accumulation of per-block sums).
+ * z, d_old, d_new, q: device arrays of the level's shape and precision,
+ * d_new and q distinct from the inputs.  Uses the handle's scalar and
+ * partial-sum storage: calls on one handle must not overlap.  Synchronises. */
+int mg_level_dir_apply(mg_handle *h, int level, int prec, const void *z, const void *d_old,
+                       double beta, void *d_new, void *q, double *dot, void *stream);
+
 /* bc = R r: restriction from level l to l+1 (R = P^T; the coarse grid of
  * Section 2.2: longitude halved, latitude rows merged where the anisotropy
  * allows). */

@@ -90,6 +90,7 @@ def load() -> ctypes.CDLL:
         "mg_level_residual": (I, [H, I, I, P, P, P, P]),
         "mg_level_smooth": (I, [H, I, I, P, P, P, P]),
         "mg_level_smooth_dot": (I, [H, I, I, P, P, P, ctypes.POINTER(D), P]),
+        "mg_level_dir_apply": (I, [H, I, I, P, P, D, P, P, ctypes.POINTER(D), P]),
         "mg_level_relax": (I, [H, I, I, I, P, P, P]),
         "mg_coarse_solve": (I, [H, I, P, P, P]),
         "mg_level_residual_restrict": (I, [H, I, I, P, P, P, P]),

@@ -395,6 +395,7 @@ static int setup_impl(mg_handle *H, const mg_coeffs *co, void *ws, size_t ws_byt
         return fail(MG_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, need);
     carve(H, ws);
     CU(smooth_prepare());
+    CU(tma_prepare());
     {
         int dev = 0, lim = 0;
         CU(cudaGetDevice(&dev));
@@ -585,6 +586,16 @@ extern "C" int mg_profile_read(mg_handle *H, int kind, int level, int prec, int 
 extern "C" unsigned long long mg_launch_count(void) { return g_launches.load(); }
 
 static int level_check(mg_handle *H, int level, int prec, bool need_coarser);
+
+// A staged kernel that gave up waiting on its copies (tpmg_tma.cu) turns the
+// solve's status into MG_ERR_TIMEOUT.
+int tpmg::check_timeouts(int rc, cudaStream_t s)
+{
+    const int n = tma_timeouts(s, true);
+    if (n > 0) return fail(MG_ERR_TIMEOUT, "%d blocks gave up waiting on their copies", n);
+    if (n < 0) return fail(MG_ERR_CUDA, "reading the copy-timeout flag failed");
+    return rc;
+}
 
 // ------------------------------------------------------------------ V-cycle
 // Smoother sweeps from a zero guess, alternating between two buffers so that
@@ -1043,7 +1054,7 @@ extern "C" int mg_solve(mg_handle *H, const double *b, double *x, double tol, mg
     const int rc = solve_impl<double>(H, b, x, tol, H->p.maxit, H->p.method, &hist, &its, &rel,
                                       (cudaStream_t)stream, false, xmax == 0.0);
     fill_stats(st, hist, its, 0, rel);
-    return rc;
+    return check_timeouts(rc, (cudaStream_t)stream);
 }
 
 extern "C" int mg_solve_mixed(mg_handle *H, const double *b, double *x, double tol, mg_stats *st,
@@ -1135,7 +1146,7 @@ extern "C" int mg_solve_mixed(mg_handle *H, const double *b, double *x, double t
         ++outer;
     }
     fill_stats(st, hist, outer, inner, rel);
-    return rc;
+    return check_timeouts(rc, s);
 }
 
 extern "C" int mg_solve_single(mg_handle *H, const float *b, float *x, double tol, mg_stats *st,
@@ -1160,7 +1171,7 @@ extern "C" int mg_solve_single(mg_handle *H, const float *b, float *x, double to
     const int rc = solve_impl<float>(H, b, x, tol, H->p.maxit, H->p.method, &hist, &its, &rel, s);
     KRUN(K_VEC, 0, 1, launch_scale<float>(x, H->scale32, f.n, s));
     fill_stats(st, hist, its, 0, rel);
-    return rc;
+    return check_timeouts(rc, s);
 }
 
 // ------------------------------------------------------------------ C ABI: operators
@@ -1413,6 +1424,35 @@ extern "C" int mg_level_relax(mg_handle *H, int level, int prec, int sweeps, con
         return fail(MG_ERR_ARG, "buffer aliases the level scratch");
     return smooth_from_zero<float>(H, level, dev<float>(v), (const float *)b, (float *)out,
                                    Vec<float>::w(v), sweeps, H->p.omega, s);
+}
+
+template <typename T>
+static int level_dir_apply(mg_handle *H, int level, const T *z, const T *d_old, double beta,
+                           T *d_new, T *q, double *dot, cudaStream_t s)
+{
+    LevelHost &v = H->lev[level];
+    CU(cudaMemcpyAsync(&H->sc->beta, &beta, sizeof beta, cudaMemcpyHostToDevice, s));
+    int nb = 0;
+    KRUN(K_APPLY, level, prec_of<T>(),
+         nb = launch_dir_apply<T>(dev<T>(v), z, d_old, H->sc, d_new, q, H->partial, s));
+    KRUN(K_VEC, level, prec_of<T>(), launch_finalize(H->partial, nb, H->sc, S_DAD, 0, s));
+    return read_scalar(H, S_DAD, dot, s);  // also keeps beta alive until its copy ran
+}
+
+extern "C" int mg_level_dir_apply(mg_handle *H, int level, int prec, const void *z,
+                                  const void *d_old, double beta, void *d_new, void *q,
+                                  double *dot, void *stream)
+{
+    CHK(level_check(H, level, prec, false));
+    if (!z || !d_new || !q || !dot || d_new == z || d_new == d_old || q == z || q == d_old ||
+        q == d_new)
+        return fail(MG_ERR_ARG, "bad direction-update buffers");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == MG_PREC_FP64)
+        return level_dir_apply<double>(H, level, (const double *)z, (const double *)d_old, beta,
+                                       (double *)d_new, (double *)q, dot, s);
+    return level_dir_apply<float>(H, level, (const float *)z, (const float *)d_old, beta,
+                                  (float *)d_new, (float *)q, dot, s);
 }
 
 extern "C" int mg_level_smooth_dot(mg_handle *H, int level, int prec, const void *b,

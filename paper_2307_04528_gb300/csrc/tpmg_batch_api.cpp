@@ -409,10 +409,13 @@ void red_plan(mg_batch *B, RedPlan<T> &R, const T *(*a)(mg_handle *), const T *(
     }
     int next = (int)R.items.size();
     for (int s : R.big) {
+        // split plans run the direction update + apply: its own partial sums
+        const BOp<T> &op = R.ops[s];
+        const int nb = dir_apply_partials<T>(op.L, op.a, op.x, op.y, op.w);
         R.base.push_back(next);
         R.off[s] = next;
-        R.off[B->n + s] = next + R.ops[s].nblk;
-        next += R.ops[s].nblk;
+        R.off[B->n + s] = next + nb;
+        next += nb;
     }
 }
 
@@ -542,6 +545,7 @@ void carve_plan(Bump &b, PrecPlan<T> &P, size_t *max_items)
         const size_t cap = item_cap(st);
         carve_step(b, st, cap);
         *max_items = std::max(*max_items, cap);
+        for (int o : st.off) *max_items = std::max(*max_items, (size_t)o);  // big ranges
     }
     for (VecPlan<T> *V : {&P.dot_rz, &P.dot_bb, &P.update[0], &P.update[1], &P.dir[0], &P.dir[1],
                           &P.dir0, &P.add, &P.rcopy, &P.xmax}) {
@@ -552,6 +556,7 @@ void carve_plan(Bump &b, PrecPlan<T> &P, size_t *max_items)
                           &P.dirapply[1]}) {
         carve_red(b, *R);
         *max_items = std::max(*max_items, R->items.size());
+        for (int o : R->off) *max_items = std::max(*max_items, (size_t)o);  // big ranges
     }
 }
 
@@ -1366,5 +1371,5 @@ extern "C" int mg_batch_solve(mg_batch *B, const double *const *b, double *const
         if (first == MG_OK && st[i] != MG_OK) first = st[i];
     }
     if (first != MG_OK) return fail(first, "%d system(s) did not converge", (int)std::count_if(st.begin(), st.end(), [](int v) { return v != MG_OK; }));
-    return MG_OK;
+    return check_timeouts(MG_OK, s);
 }

@@ -21,6 +21,10 @@ int fail(int code, const char *fmt, ...);
 // Kernel launches issued by the library (all handles).
 extern std::atomic<unsigned long long> g_launches;
 
+// rc, or MG_ERR_TIMEOUT when a staged kernel gave up waiting on its copies
+// since the last check (synchronises s).
+int check_timeouts(int rc, cudaStream_t s);
+
 struct LinkHost {
     int nlat_c = 0;
     std::vector<int> cfirst, ccnt, j0, j1, rptr, rrow;

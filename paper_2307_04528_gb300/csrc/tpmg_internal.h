@@ -146,6 +146,29 @@ cudaError_t launch_cg_direction(const T *z, const T *d_in, T *d_out, size_t n,
 // Grid of the vector kernels for n elements (one wave of full occupancy).
 int vec_grid(size_t n);
 
+// ---- TMA-staged FP32 direction update + apply (tpmg_tma.cu) ---------------
+// Levels of at least kTmaMinColumns columns (and rows of whole 16-byte
+// groups, 16-byte aligned arrays) take the staged kernel; the launcher
+// returns -1 when a level or buffer does not suit it (the caller then runs
+// the register-pipeline kernel), else the number of blocks (and partial
+// sums) launched.
+constexpr long long kTmaMinColumns = 1LL << 18;
+int dir_apply_tma_grid(const LevelDev<float> &L, const void *z, const void *d_old,
+                       const void *d_new, const void *q);
+int launch_dir_apply_tma(const LevelDev<float> &L, const float *z, const float *d_old,
+                         const CgScalars *sc, float *d_new, float *q, double *partial,
+                         cudaStream_t s, const int *flag);
+// Shared-memory limits of the staged kernel (once per process and device,
+// before any stream capture).
+cudaError_t tma_prepare();
+// Threads of the staged kernel that gave up waiting on a copy since the
+// last reset (-1 if the flag could not be read).  Synchronises s.
+int tma_timeouts(cudaStream_t s, bool reset);
+// Partial sums launch_dir_apply writes for these arguments.
+template <typename T>
+int dir_apply_partials(const LevelDev<T> &L, const T *z, const T *d_old, const T *d_new,
+                       const T *q);
+
 // ---- BiCGStab vector steps (tpmg_krylov.cu); scalars read from sc ----
 // p = r (first) or p = r + beta (p - omega v)
 template <typename T>

@@ -60,6 +60,10 @@ template <typename T>
 int launch_dir_apply(const LevelDev<T> &L, const T *z, const T *d_old, const CgScalars *sc,
                      T *d_new, T *q, double *partial, cudaStream_t s, const int *flag)
 {
+    if constexpr (sizeof(T) == 4) {
+        const int g = launch_dir_apply_tma(L, z, d_old, sc, d_new, q, partial, s, flag);
+        if (g >= 0) return g;
+    }
     const int ncol = L.nlon * L.nlat;
     const int grid = (ncol + kBlock - 1) / kBlock;
     if (d_old == nullptr)
@@ -512,6 +516,17 @@ static inline int red_grid(size_t n)
 int vec_grid(size_t n) { return red_grid(n); }
 
 template <typename T>
+int dir_apply_partials(const LevelDev<T> &L, const T *z, const T *d_old, const T *d_new,
+                       const T *q)
+{
+    if constexpr (sizeof(T) == 4) {
+        const int g = dir_apply_tma_grid(L, z, d_old, d_new, q);
+        if (g >= 0) return g;
+    }
+    return (L.nlon * L.nlat + kBlock - 1) / kBlock;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_dot(const T *__restrict__ a, const T *__restrict__ b, size_t n, double *partial)
 {
@@ -867,7 +882,9 @@ cudaError_t launch_coeff_grad(int nlon, int nlat, int nz, const double *lam, con
     template cudaError_t launch_coarse_solve<T>(const LevelDev<T> &, const T *, T *, T *, double, \
                                                 int, cudaStream_t);                               \
     template int launch_dir_apply<T>(const LevelDev<T> &, const T *, const T *, const CgScalars *, \
-                                     T *, T *, double *, cudaStream_t, const int *);
+                                     T *, T *, double *, cudaStream_t, const int *);            \
+    template int dir_apply_partials<T>(const LevelDev<T> &, const T *, const T *, const T *,      \
+                                       const T *);
 
 TPMG_INST(double)
 TPMG_INST(float)

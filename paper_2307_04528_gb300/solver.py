@@ -236,6 +236,16 @@ class MGHandle:
                                              ctypes.byref(dot), _stream()))
         return out, dot.value
 
+    def level_dir_apply(self, level, z, d_old=None, beta=0.0, prec=L.MG_PREC_FP64):
+        """The fused CG step: d_new = z + beta d_old (d_old None: z), q = H d_new,
+        and <d_new, q>.  Returns (d_new, q, dot)."""
+        d_new, q = torch.empty_like(z), torch.empty_like(z)
+        dot = ctypes.c_double()
+        L.check(self.lib.mg_level_dir_apply(self._hh, level, prec, _ptr(z), _ptr(d_old),
+                                            float(beta), _ptr(d_new), _ptr(q), ctypes.byref(dot),
+                                            _stream()))
+        return d_new, q, dot.value
+
     def level_restrict(self, level, r, prec=L.MG_PREC_FP64):
         shp = self.level_shape(level + 1)
         bc = torch.empty(shp, dtype=r.dtype, device=r.device)

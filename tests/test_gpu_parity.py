@@ -276,6 +276,23 @@ def test_fp32_kernels(case):
             assert rel_inf(host(H.level_restrict(l, f32(x), prec=1)), O.restrict(ol, x)) <= 2e-5
 
 
+def test_dir_apply_every_level(case):
+    """The CG step d_new = z + beta d_old, q = H d_new, <d_new, q> (the
+    register-pipeline kernel at these sizes) against the oracle's apply."""
+    P, lev, p, H = case
+    rng = np.random.default_rng(9)
+    for l, ol in enumerate(lev):
+        z = rng.standard_normal(ol.shape)
+        d = rng.standard_normal(ol.shape)
+        dn, q, dot = H.level_dir_apply(l, dev(z), dev(d), 0.37)
+        dref = host(dn)
+        assert rel_inf(dref, z + 0.37 * d) <= 1e-15
+        assert rel_inf(host(q), O.apply(ol, dref)) <= 1e-13
+        assert abs(dot - O.dot(dref, host(q))) <= 1e-12 * O.norm2(dref) * O.norm2(host(q))
+        dn, q, _ = H.level_dir_apply(l, dev(z), None)
+        assert np.array_equal(host(dn), z) and rel_inf(host(q), O.apply(ol, z)) <= 1e-13
+
+
 # FP32 V-cycle against the oracle's float V-cycle: both run V(1,1) with the
 # same steps in FP32 but different rounding orders (fused multiply-adds, the
 # warp-scan column sweeps of the small levels); each step is good to ~1e-6
