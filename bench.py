@@ -265,7 +265,11 @@ PAPER_RUNS = [
     ("stationary_default_hierarchy_fp64", dict(method=1), False, 200),
     ("stationary_default_hierarchy_mixed", dict(method=1, inner_maxit=40), True, 40),
     ("stationary_4_levels_fp64", dict(method=1, levels=4), False, 60),
-    ("cg_4_levels_mixed", dict(levels=4, inner_maxit=200), True, 40),
+    ("cg_4_levels_mixed", dict(levels=4, inner_maxit=40), True, 40),
+    ("cg_4_levels_chebyshev24_mixed", dict(levels=4, inner_maxit=40, coarse_method=2,
+                                           coarse_iters=24), True, 40),
+    ("cg_4_levels_pcg24_mixed", dict(levels=4, inner_maxit=40, coarse_method=1,
+                                     coarse_iters=24), True, 40),
 ]
 
 

@@ -55,7 +55,7 @@ typedef enum {
 enum { MG_METHOD_CG = 0, MG_METHOD_STATIONARY = 1, MG_METHOD_BICGSTAB = 2,
        MG_METHOD_BICGSTAB_LINE = 3 };
 enum { MG_PREC_FP64 = 0, MG_PREC_FP32 = 1 };
-enum { MG_COARSE_JACOBI = 0, MG_COARSE_PCG = 1 };
+enum { MG_COARSE_JACOBI = 0, MG_COARSE_PCG = 1, MG_COARSE_CHEBYSHEV = 2 };
 
 typedef struct mg_handle mg_handle;
 
@@ -73,7 +73,10 @@ typedef struct {
 
 typedef struct {
     int levels;        /* 0: coarsen down to the coarsest level (nlon >= 4 there);
-                          4 is the shallow hierarchy of Section 2.3 */
+                          4 is the shallow hierarchy of Section 2.3; -1: coarsen until a
+                          level's largest (sum of horizontal couplings) / h is at most
+                          iso_ratio (at most as deep as 0; the workspace is sized for that
+                          depth; single systems only) */
     int nu1, nu2;      /* pre/post smoothing sweeps (V(1,1) default) */
     int coarse_iters;  /* block-Jacobi sweeps on the coarsest level (12) */
     int method;        /* outer iteration: MG_METHOD_CG (V-cycle-preconditioned CG,
@@ -95,10 +98,17 @@ typedef struct {
                           sweeps (default; V stays a fixed linear operator), or MG_COARSE_PCG,
                           coarse_iters iterations of CG preconditioned by the column solves
                           (for shallow hierarchies; V then depends nonlinearly on its input,
-                          which the stationary method tolerates; CG usually does).  Single
-                          systems only: mg_batch_setup rejects MG_COARSE_PCG. */
+                          which the stationary method tolerates; CG usually does), or
+                          MG_COARSE_CHEBYSHEV, coarse_iters Chebyshev steps on the
+                          column-solve preconditioner over [mu, 2], mu = min over the level
+                          of h / (h + the horizontal couplings), a bound of the spectrum of
+                          H_z^{-1} H (a fixed polynomial: V stays linear).  Single systems
+                          only: mg_batch_setup takes MG_COARSE_JACOBI alone. */
     int line_sweeps;   /* MG_METHOD_BICGSTAB_LINE: sweeps of Eq. (1) per preconditioner
                           application (1) */
+    double iso_ratio;  /* levels = -1: the largest (sum of the horizontal couplings) / h
+                          the coarsest level may keep (6.25: four faces at Section 2.3's
+                          nu^2 / 4^3 = 1.56) */
 } mg_params;
 
 typedef struct {

@@ -68,14 +68,18 @@ def num_threads() -> int:
 class MGParams:
     """Readings of what the paper leaves open (listed in the design notes)."""
     levels: int = 0            # 0: coarsen down to the coarsest level (nlon >= 4);
-    #                            Section 2.3's shallow hierarchy is levels=4
+    #                            Section 2.3's shallow hierarchy is levels=4; -1: stop at the
+    #                            first level whose couplings are within iso_ratio (below)
+    iso_ratio: float = 6.25    # levels=-1: largest (sum of horizontal couplings) / h allowed on
+    #                            the coarsest level (4 faces at Section 2.3's nu^2 / 4^3 = 1.56)
     nu1: int = 1               # pre-smoothing sweeps, V(1,1)
     nu2: int = 1               # post-smoothing sweeps
     omega: float = 0.85        # Eq. (1) relaxation factor (value not printed; tuned)
     coarse_iters: int = 12     # Section 2.3's simple coarsest-grid iteration: block-Jacobi sweeps
     #                            (count not printed; measured), or PCG iterations
-    coarse_method: str = "jacobi"  # coarsest-level solve: "jacobi" sweeps or "pcg" (CG
-    #                                preconditioned by the column solves), both from zero
+    coarse_method: str = "jacobi"  # coarsest-level solve: "jacobi" sweeps, "pcg" (CG
+    #                                preconditioned by the column solves) or "chebyshev"
+    #                                (Chebyshev steps on the column-solve preconditioner), from zero
     alpha_c: float = 0.6       # Section 2.2 anisotropy threshold (value not printed; tuned)
     method: str = "cg"         # outer iteration: "cg" (V-cycle-preconditioned CG), "stationary",
     #                            "bicgstab" (V-cycle-preconditioned) or "bicgstab_line" (BiCGStab
@@ -217,8 +221,19 @@ def lat_interpolation(fine_centres, coarse_centres, row_of):
     return j0, w0, j1, w1
 
 
+def horizontal_ratio(lev: Level) -> float:
+    """The largest (sum of the four horizontal couplings) / h over a level:
+    the square of the horizontal Courant number of Section 2.3 summed over
+    the faces, 1 / mu - 1 for mu of hz_interval."""
+    mu, _ = hz_interval(lev)
+    return 1.0 / mu - 1.0
+
+
 def build_hierarchy(tx, ty, tz, h, params: MGParams | None = None):
-    """Levels 0..L-1 with rediscretised coarse coefficients (Sections 2.1-2.3)."""
+    """Levels 0..L-1 with rediscretised coarse coefficients (Sections 2.1-2.3).
+    levels = -1: coarsen until a level's horizontal_ratio is at most
+    iso_ratio (the coarse problem is then well conditioned, the premise of
+    Section 2.3's shallow hierarchy), at most as deep as levels = 0."""
     p = params or MGParams()
     nz, nlat, nlon = h.shape
     L = p.levels if p.levels > 0 else auto_levels(nlon)
@@ -246,6 +261,8 @@ def build_hierarchy(tx, ty, tz, h, params: MGParams | None = None):
         lib.orc_coarsen_coeffs(f.nlon, f.nlat, nz, nlat_c, row_of, top, 0.5, sy,
                                f.tx, f.ty, f.tz, f.h, txc, tyc, tzc, hc)
         levels.append(Level(nlon_c, nlat_c, nz, txc, tyc, tzc, hc, cs, cn))
+        if p.levels < 0 and horizontal_ratio(levels[-1]) <= p.iso_ratio:
+            break
     return levels
 
 
@@ -367,11 +384,68 @@ def coarse_pcg(lev: Level, b, iters: int):
     return x
 
 
+def hz_interval(lev: Level):
+    """An interval [mu, 2] holding the spectrum of H_z^{-1} H.  2 H_z - H =
+    H_z - dH is diagonally dominant with a positive diagonal, so lambda < 2;
+    u' H u = sum h u^2 + (vertical and horizontal couplings, both >= 0) and
+    u' H_z u = sum (h + horizontal couplings) u^2 + (the same vertical
+    part), so lambda >= mu = min over cells of h / (h + the four horizontal
+    couplings).  Computed in FP64 from the level's coefficients (a FP32
+    level holds them scaled, which leaves the ratios unchanged)."""
+    h = lev.h.astype(np.float64)
+    tx = lev.tx.astype(np.float64)
+    ty = lev.ty.astype(np.float64)
+    hor = tx + np.roll(tx, 1, axis=2) + ty
+    hor[:, 1:, :] += ty[:, :-1, :]
+    return float(np.min(h / (h + hor))), 2.0
+
+
+def coarse_chebyshev(lev: Level, b, iters: int):
+    """Chebyshev iteration from a zero guess preconditioned by the column
+    solves (M = H_z), exactly `iters` steps, on the interval [mu, 2] of
+    hz_interval: a fixed polynomial in H_z^{-1} H, so the coarsest-level
+    solve (Section 2.3's simple iteration, here polynomially accelerated)
+    stays a fixed symmetric linear operator.  With theta = (2 + mu) / 2,
+    delta = (2 - mu) / 2, sigma = theta / delta (scalars in FP64):
+        r_0 = b, d_0 = M^{-1} r_0 / theta, rho_0 = 1 / sigma
+        x_{k+1} = x_k + d_k;  r_{k+1} = r_k - H d_k
+        rho_{k+1} = 1 / (2 sigma - rho_k)
+        d_{k+1} = rho_{k+1} rho_k d_k + (2 rho_{k+1} / delta) M^{-1} r_{k+1}
+    The error after m steps is T_m((theta - H_z^{-1} H) / delta) / T_m(sigma)
+    times the initial error (T_m the Chebyshev polynomial).  Vectors in b's
+    precision; the column solves are sweeps from zero with omega = 1."""
+    mu, lam = hz_interval(lev)
+    theta, delta = 0.5 * (lam + mu), 0.5 * (lam - mu)
+    sigma = theta / delta
+    dt = b.dtype.type
+    one = dt(1.0)
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = np.zeros_like(b)
+    smooth(lev, r, z, one)
+    d = (z * dt(1.0 / theta)).astype(b.dtype)
+    rho = 1.0 / sigma
+    for it in range(iters):
+        x += d
+        if it + 1 == iters:
+            break
+        r = residual(lev, r, d)             # r - H d
+        z = np.zeros_like(b)
+        smooth(lev, r, z, one)
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        d = (dt(rho_new * rho) * d + dt(2.0 * rho_new / delta) * z).astype(b.dtype)
+        rho = rho_new
+    return x
+
+
 def coarse_solve(lev: Level, b, p: MGParams):
     """The coarsest-level solve of the V-cycle from a zero guess (Section
-    2.3): coarse_iters block-Jacobi sweeps, or coarse_iters PCG iterations."""
+    2.3): coarse_iters block-Jacobi sweeps, PCG iterations or Chebyshev
+    steps."""
     if p.coarse_method == "pcg":
         return coarse_pcg(lev, b, p.coarse_iters)
+    if p.coarse_method == "chebyshev":
+        return coarse_chebyshev(lev, b, p.coarse_iters)
     om = np.float32(p.omega) if b.dtype == np.float32 else p.omega
     u = np.zeros_like(b)
     work = np.empty_like(b)

@@ -16,7 +16,7 @@ MG_OK, MG_ERR_ARG, MG_ERR_COEFF, MG_ERR_NONFINITE, MG_ERR_NOT_CONVERGED = 0, 1, 
 MG_ERR_DIVERGED, MG_ERR_TIMEOUT, MG_ERR_CUDA, MG_ERR_WORKSPACE = 5, 6, 7, 8
 MG_METHOD_CG, MG_METHOD_STATIONARY, MG_METHOD_BICGSTAB, MG_METHOD_BICGSTAB_LINE = 0, 1, 2, 3
 MG_PREC_FP64, MG_PREC_FP32 = 0, 1
-MG_COARSE_JACOBI, MG_COARSE_PCG = 0, 1
+MG_COARSE_JACOBI, MG_COARSE_PCG, MG_COARSE_CHEBYSHEV = 0, 1, 2
 # kernel classes of mg_profile_read
 K_SMOOTH, K_SMOOTH0, K_RESID, K_APPLY, K_RESTRICT, K_PROLONG, K_VEC = range(7)
 
@@ -46,7 +46,7 @@ class mg_params(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("inner_maxit", ctypes.c_int),
                 ("omega", ctypes.c_double), ("alpha_c", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("coarse_method", ctypes.c_int),
-                ("line_sweeps", ctypes.c_int)]
+                ("line_sweeps", ctypes.c_int), ("iso_ratio", ctypes.c_double)]
 
 
 class mg_stats(ctypes.Structure):

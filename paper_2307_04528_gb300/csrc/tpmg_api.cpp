@@ -183,13 +183,15 @@ static int check_grid(const mg_grid *g, const mg_params *p, int *L_out)
     if (L > 1 && (g->nlon % (1 << (L - 1)) || (g->nlon >> (L - 1)) < 2))
         return fail(MG_ERR_ARG, "nlon=%d not divisible by 2^(levels-1) = %d", g->nlon,
                     1 << (L - 1));
-    if (p->coarse_method != MG_COARSE_JACOBI && p->coarse_method != MG_COARSE_PCG)
+    if (p->coarse_method != MG_COARSE_JACOBI && p->coarse_method != MG_COARSE_PCG &&
+        p->coarse_method != MG_COARSE_CHEBYSHEV)
         return fail(MG_ERR_ARG, "coarse_method %d unknown", p->coarse_method);
     if (p->nu1 < 1 || p->nu2 < 0 || p->coarse_iters < 1 || p->maxit < 0 ||
         !(p->omega > 0.0 && p->omega < 2.0) ||
         (p->method != MG_METHOD_CG && p->method != MG_METHOD_STATIONARY &&
          !is_bicgstab(p->method)) ||
-        (p->method == MG_METHOD_BICGSTAB_LINE && (p->line_sweeps < 1 || p->line_sweeps > 100)))
+        (p->method == MG_METHOD_BICGSTAB_LINE && (p->line_sweeps < 1 || p->line_sweeps > 100)) ||
+        p->levels < -1 || (p->levels == -1 && !(p->iso_ratio > 0.0)))
         return fail(MG_ERR_ARG, "invalid multigrid parameters");
     if ((size_t)g->nlon * g->nlat > (size_t)kReduceSlots * kBlock)
         return fail(MG_ERR_ARG, "nlon*nlat=%zu exceeds %zu columns", (size_t)g->nlon * g->nlat,
@@ -244,7 +246,12 @@ static size_t carve(mg_handle *H, void *base)
         v.w = cv.take<double>(n);
         v.r = cv.take<double>(n);
         if (l > 0) v.b = cv.take<double>(n);
-        const bool pcg = l == H->L - 1 && H->p.coarse_method == MG_COARSE_PCG;
+        // the coarsest level's extra vectors (PCG: direction and its image;
+        // Chebyshev: step and residual ping-pong); with the isotropy rule any
+        // level below the finest may end up the coarsest
+        const bool pcg = (l == H->L - 1 || (H->p.levels < 0 && l > 0)) &&
+                         (H->p.coarse_method == MG_COARSE_PCG ||
+                          H->p.coarse_method == MG_COARSE_CHEBYSHEV);
         if (pcg) {
             v.cd = cv.take<double>(n);
             v.cq = cv.take<double>(n);
@@ -332,6 +339,7 @@ extern "C" void mg_default_params(mg_params *p)
     p->inner_tol = 5e-4;
     p->coarse_method = MG_COARSE_JACOBI;
     p->line_sweeps = 1;
+    p->iso_ratio = 6.25;
 }
 
 extern "C" const char *mg_last_error(void) { return g_last_error.c_str(); }
@@ -437,10 +445,32 @@ static int setup_impl(mg_handle *H, const mg_coeffs *co, void *ws, size_t ws_byt
             CHK(upload(K.sy, D.sy, s));
             LevelHost &c = H->lev[l + 1];
             KRUN(K_VEC, l, 0, launch_coarsen(dev<double>(v), D, 0.5, c.tx, c.ty, c.tz, c.h, s));
+            if (H->p.levels < 0) {  // coarsen until the couplings are within iso_ratio
+                int nb = 0;
+                KRUN(K_VEC, l + 1, 0, nb = launch_hz_ratio(dev<double>(c), H->partial, s));
+                KRUN(K_VEC, l + 1, 0, launch_finalize(H->partial, nb, H->sc, S_MAX, 3, s));
+                double ratio = 0;
+                CHK(read_scalar(H, S_MAX, &ratio, s));
+                if (!std::isfinite(ratio)) return fail(MG_ERR_COEFF, "bad coarse coefficients");
+                if (ratio - 1.0 <= H->p.iso_ratio) H->L = l + 2;  // level l+1 is the coarsest
+            }
         }
         KRUN(K_VEC, l, 0, launch_column_lu(dev<double>(v), v.m, v.dq, s));
         // the uploads above read pageable host vectors: finish before they go away
         CU(cudaStreamSynchronize(s));
+    }
+    if (H->p.coarse_method == MG_COARSE_CHEBYSHEV) {
+        // spectrum of H_z^{-1} H on the coarsest level in [mu, 2]:
+        // mu = 1 / max over cells of (h + horizontal couplings) / h
+        const LevelHost &c = H->lev[H->L - 1];
+        int nb = 0;
+        KRUN(K_VEC, H->L - 1, 0, nb = launch_hz_ratio(dev<double>(c), H->partial, s));
+        KRUN(K_VEC, H->L - 1, 0, launch_finalize(H->partial, nb, H->sc, S_MAX, 3, s));
+        double ratio = 0;
+        CHK(read_scalar(H, S_MAX, &ratio, s));
+        if (!(ratio >= 1.0) || !std::isfinite(ratio))
+            return fail(MG_ERR_COEFF, "coarsest level: bad Helmholtz ratio %g", ratio);
+        H->cheb_mu = 1.0 / ratio;
     }
     if (H->p.mixed) {
         double big = 0;
@@ -653,12 +683,54 @@ static int coarse_pcg(mg_handle *H, int l, const LevelDev<T> &D, const T *b, T *
     return MG_OK;
 }
 
+// The coarsest-level solve as coarse_iters Chebyshev steps from zero on the
+// column-solve preconditioner (M = H_z, z = M^{-1} r the sweep from zero with
+// omega = 1), on the interval [mu, 2] holding the spectrum of H_z^{-1} H (mu
+// from setup): a fixed polynomial, so the V-cycle stays a fixed linear
+// operator.  theta = (2 + mu) / 2, delta = (2 - mu) / 2, sigma = theta /
+// delta; d_0 = z_0 / theta, rho_0 = 1 / sigma; step k: x += d_k,
+// r_{k+1} = r_k - H d_k, d_{k+1} = rho_{k+1} rho_k d_k + 2 rho_{k+1} / delta
+// z_{k+1}, rho_{k+1} = 1 / (2 sigma - rho_k) (scalars on the host, passed to
+// the kernels).  Vectors: out = x, the level's r and cq alternate as the
+// residual, w = z, cd = d.
+template <typename T>
+static int coarse_chebyshev(mg_handle *H, int l, const LevelDev<T> &D, const T *b, T *out,
+                            cudaStream_t s)
+{
+    LevelHost &v = H->lev[l];
+    const size_t n = v.n;
+    constexpr int P = prec_of<T>();
+    T *r = Vec<T>::r(v), *r2 = Vec<T>::cq(v), *z = Vec<T>::w(v), *d = Vec<T>::cd(v);
+    if (!d || !r2) return fail(MG_ERR_ARG, "Chebyshev coarse solve without its vectors");
+    const double mu = H->cheb_mu, lam = 2.0;
+    const double theta = 0.5 * (lam + mu), delta = 0.5 * (lam - mu), sigma = theta / delta;
+    const int m = H->p.coarse_iters;
+    CU(cudaMemsetAsync(out, 0, n * sizeof(T), s));
+    KRUN(K_SMOOTH0, l, P, launch_smooth<T>(D, b, nullptr, z, 1.0, s));  // z_0 = M^{-1} b
+    KRUN(K_VEC, l, P, launch_cheb_step<T>(out, d, z, 0.0, 1.0 / theta, n, true, s));
+    const T *rk = b;
+    double rho = 1.0 / sigma;
+    for (int k = 0; k + 1 < m; ++k) {
+        T *rn = (rk == r) ? r2 : r;
+        KRUN(K_RESID, l, P, launch_stencil<T>(D, 1, rk, d, rn, nullptr, s));  // r - H d
+        rk = rn;
+        KRUN(K_SMOOTH0, l, P, launch_smooth<T>(D, rk, nullptr, z, 1.0, s));
+        const double rho_new = 1.0 / (2.0 * sigma - rho);
+        KRUN(K_VEC, l, P,
+             launch_cheb_step<T>(out, d, z, rho_new * rho, 2.0 * rho_new / delta, n, false, s));
+        rho = rho_new;
+    }
+    KRUN(K_VEC, l, P, launch_add<T>(out, d, n, s));  // the last x += d
+    return MG_OK;
+}
+
 // The V-cycle's coarsest-level solve from zero (Section 2.3).
 template <typename T>
 static int coarse_solve(mg_handle *H, int l, const LevelDev<T> &D, const T *b, T *out, T *scratch,
                         cudaStream_t s)
 {
     if (H->p.coarse_method == MG_COARSE_PCG) return coarse_pcg<T>(H, l, D, b, out, s);
+    if (H->p.coarse_method == MG_COARSE_CHEBYSHEV) return coarse_chebyshev<T>(H, l, D, b, out, s);
     return smooth_from_zero<T>(H, l, D, b, out, scratch, H->p.coarse_iters, H->p.omega, s);
 }
 

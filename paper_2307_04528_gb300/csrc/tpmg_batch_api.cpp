@@ -1103,6 +1103,8 @@ extern "C" int mg_batch_workspace_bytes(int n, const mg_grid *grids, const mg_pa
                                         size_t *bytes)
 {
     if (n < 1 || !grids || !params || !bytes) return fail(MG_ERR_ARG, "bad batch arguments");
+    if (params->levels < 0)
+        return fail(MG_ERR_ARG, "batched solves take a fixed number of levels");
     if (params->coarse_method != MG_COARSE_JACOBI)
         return fail(MG_ERR_ARG, "batched solves take the block-Jacobi coarsest-level solve");
     if (params->method != MG_METHOD_CG && params->method != MG_METHOD_STATIONARY)
@@ -1123,6 +1125,8 @@ extern "C" int mg_batch_setup(int n, const mg_grid *grids, const mg_coeffs *coef
     if (!out) return fail(MG_ERR_ARG, "null out");
     *out = nullptr;
     if (n < 1 || !grids || !coeffs || !params) return fail(MG_ERR_ARG, "bad batch arguments");
+    if (params->levels < 0)
+        return fail(MG_ERR_ARG, "batched solves take a fixed number of levels");
     if (params->coarse_method != MG_COARSE_JACOBI)
         return fail(MG_ERR_ARG, "batched solves take the block-Jacobi coarsest-level solve");
     if (params->method != MG_METHOD_CG && params->method != MG_METHOD_STATIONARY)

@@ -129,6 +129,7 @@ struct mg_handle {
     BicgScalars *bsc = nullptr;      // scalars of BiCGStab
     int *flag = nullptr;
     double scale32 = 0.0;
+    double cheb_mu = 0.0;  // Chebyshev coarse solve: lower end of the spectrum of H_z^{-1} H
 };
 
 template <typename T>

@@ -192,6 +192,12 @@ cudaError_t launch_bicg_finalize(const double *pa, const double *pb, int n, Bicg
 // x *= f
 template <typename T>
 cudaError_t launch_scale(T *x, double f, size_t n, cudaStream_t s);
+// per-block maxima of (h + horizontal couplings) / h over the level
+int launch_hz_ratio(const LevelDev<double> &L, double *partial, cudaStream_t s);
+// Chebyshev step: x += d, d = c1 d + c2 z (first: d = c2 z)
+template <typename T>
+cudaError_t launch_cheb_step(T *x, T *d, const T *z, double c1, double c2, size_t n, bool first,
+                             cudaStream_t s);
 
 // x += e (same precision)
 template <typename T>

@@ -203,6 +203,62 @@ cudaError_t launch_scale(T *x, double f, size_t n, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Per-block maxima of (h + the four horizontal couplings) / h: its inverse
+// over the level bounds the spectrum of H_z^{-1} H from below.
+__global__ void __launch_bounds__(kBlock) k_hz_ratio(LevelDev<double> L, double *partial)
+{
+    const int nlon = L.nlon, nlat = L.nlat;
+    const size_t plane = (size_t)nlon * nlat, n = plane * L.nz;
+    double m = 0;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+         c += (size_t)gridDim.x * blockDim.x) {
+        const size_t col = c % plane;
+        const int j = (int)(col / nlon), i = (int)(col - (size_t)j * nlon);
+        const size_t iw = (i == 0) ? c + nlon - 1 : c - 1;
+        double hor = L.tx[c] + L.tx[iw];
+        if (j + 1 < nlat) hor += L.ty[c];
+        if (j > 0) hor += L.ty[c - nlon];
+        m = max_mag(m, (L.h[c] + hor) / L.h[c]);
+    }
+    block_store<1>(m, partial);
+}
+
+int launch_hz_ratio(const LevelDev<double> &L, double *partial, cudaStream_t s)
+{
+    const int g = vec_grid((size_t)L.nlon * L.nlat * L.nz);
+    k_hz_ratio<<<g, kBlock, 0, s>>>(L, partial);
+    return g;
+}
+
+// One Chebyshev step of the coarsest-level solve: x += d, then
+// d = c1 d + c2 z (first: d = c2 z, x untouched).
+template <typename T, bool FIRST>
+__global__ void __launch_bounds__(kBlock)
+k_cheb_step(T *__restrict__ x, T *__restrict__ d, const T *__restrict__ z, T c1, T c2, size_t n)
+{
+#pragma unroll 4
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
+         c += (size_t)gridDim.x * blockDim.x) {
+        if (FIRST) {
+            d[c] = c2 * z[c];
+        } else {
+            const T dv = d[c];
+            x[c] += dv;
+            d[c] = fma(c1, dv, c2 * z[c]);
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_cheb_step(T *x, T *d, const T *z, double c1, double c2, size_t n, bool first,
+                             cudaStream_t s)
+{
+    const int g = vec_grid(n);
+    if (first) k_cheb_step<T, true><<<g, kBlock, 0, s>>>(x, d, z, (T)c1, (T)c2, n);
+    else k_cheb_step<T, false><<<g, kBlock, 0, s>>>(x, d, z, (T)c1, (T)c2, n);
+    return cudaGetLastError();
+}
+
 #define TPMG_KRYLOV_INST(T)                                                                     \
     template cudaError_t launch_bicg_dir<T>(T *, const T *, const T *, size_t,                  \
                                             const BicgScalars *, bool, cudaStream_t);           \
@@ -212,7 +268,9 @@ cudaError_t launch_scale(T *x, double f, size_t n, cudaStream_t s)
     template int launch_bicg_update<T>(T *, T *, const T *, const T *, const T *, const T *,     \
                                        const T *, size_t, const BicgScalars *, double *,         \
                                        double *, cudaStream_t);                                  \
-    template cudaError_t launch_scale<T>(T *, double, size_t, cudaStream_t);
+    template cudaError_t launch_scale<T>(T *, double, size_t, cudaStream_t);                   \
+    template cudaError_t launch_cheb_step<T>(T *, T *, const T *, double, double, size_t, bool, \
+                                             cudaStream_t);
 
 TPMG_KRYLOV_INST(double)
 TPMG_KRYLOV_INST(float)

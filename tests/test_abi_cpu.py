@@ -75,7 +75,9 @@ def test_workspace_sizing(lib):
                                       ((48, 32, 4), {"levels": 6}),  # 48 not divisible by 32
                                       ((64, 32, 4), {"omega": 2.5}),
                                       ((64, 32, 4), {"nu1": 0}),
-                                      ((64, 32, 4), {"coarse_method": 2})])
+                                      ((64, 32, 4), {"coarse_method": 3}),
+                                      ((64, 32, 4), {"method": 4}),
+                                      ((64, 32, 4), {"method": 3, "line_sweeps": 0})])
 def test_bad_arguments_rejected_on_host(lib, shape, kw):
     st, _ = _bytes(lib, *shape, **kw)
     assert st == 1
@@ -113,3 +115,11 @@ def test_batch_workspace_covers_every_system(lib):
     assert n.value > singles
     bad = (L.mg_grid * 1)(L.mg_grid(64, 31, 8))
     assert lib.mg_batch_workspace_bytes(1, bad, ctypes.byref(p), ctypes.byref(n)) == 1
+
+
+def test_isotropy_rule_sized_for_full_depth(lib):
+    st0, n0 = _bytes(lib, 64, 32, 16)
+    st1, n1 = _bytes(lib, 64, 32, 16, levels=-1)
+    assert st0 == st1 == 0 and n1 >= n0
+    st, _ = _bytes(lib, 64, 32, 16, levels=-1, iso_ratio=0.0)
+    assert st == 1

@@ -86,5 +86,5 @@ def test_workspace_and_argument_errors():
                                           ctypes.c_void_p(b.data_ptr()),
                                           ctypes.c_void_p(b.data_ptr()), s) == L.MG_ERR_ARG
     assert lib.mg_coarse_solve(H._hh, 0, ptr(b), ptr(b), s) == L.MG_ERR_ARG
-    _raises(L.MG_ERR_ARG, lambda: handle_for(P, coarse_method=2))
+    _raises(L.MG_ERR_ARG, lambda: handle_for(P, coarse_method=3))
 

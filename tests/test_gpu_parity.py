@@ -156,6 +156,54 @@ def test_coarse_pcg(shape, levels):
             assert rel_2(host(x), xr) <= 1e-9
 
 
+@pytest.mark.parametrize("shape,levels", [((64, 32, 16), 3), ((96, 46, 9), 2), ((64, 32, 16), 0)])
+def test_coarse_chebyshev(shape, levels):
+    """coarse_method = Chebyshev: the coarsest-level solve against the
+    oracle's coarse_chebyshev (a fixed polynomial: FP64 1e-11, FP32 2e-5),
+    the FP64 V-cycle against the oracle's (1e-10), and a 3-level FP64 and
+    mixed solve to 1e-10 against the oracle's FP64 solution (1e-9)."""
+    P = problem(*shape, sigma=0.2, seed=sum(shape) + 2 * levels)
+    lev, p = oracle_levels(P, levels=levels, coarse_method="chebyshev")
+    H = handle_for(P, levels=levels, coarse_method=2)
+    assert H.num_levels == len(lev)
+    l32 = O.float_levels(lev)
+    rng = np.random.default_rng(17)
+    b = rng.standard_normal(lev[-1].shape)
+    got = host(H.coarse_solve(dev(b)))
+    assert rel_inf(got, O.coarse_chebyshev(lev[-1], b, p.coarse_iters)) <= 1e-11
+    b32 = b.astype(np.float32)
+    got = host(H.coarse_solve(dev(b32, torch.float32), prec=1))
+    assert rel_inf(got, O.coarse_chebyshev(l32[-1], b32, p.coarse_iters)) <= 2e-5
+    r = rng.standard_normal(lev[0].shape)
+    assert rel_inf(host(H.vcycle(dev(r))), O.vcycle(lev, r, p)) <= 1e-10
+    if levels == 3:
+        xr, _, sr = O.solve(lev, P["b"], 1e-11, params=p)
+        assert sr == O.OK
+        for fn in (H.solve, H.solve_mixed):
+            x, info = fn(dev(P["b"]), tol=1e-10)
+            assert info["status"] == 0 and info["rel_res"] <= 1e-10
+            assert rel_2(host(x), xr) <= 1e-9
+
+
+def test_isotropy_stopping_rule():
+    """levels = -1 (coarsen until the couplings are within iso_ratio): the
+    same depth and shapes as the oracle's rule, on a system with a large
+    Helmholtz term (stops early) and on the lat-lon workload (full depth),
+    and the solve against the oracle's solution."""
+    for hscale, shape in ((1e4, (64, 32, 16)), (1.0, (96, 46, 9))):
+        P = problem(*shape, sigma=0.2, seed=61)
+        P = dict(P, h=P["h"] * hscale)
+        lev, p = oracle_levels(P, levels=-1)
+        H = handle_for(P, levels=-1)
+        assert H.num_levels == len(lev)
+        for l, ol in enumerate(lev):
+            assert H.level_shape(l) == ol.shape
+        xr, _, sr = O.solve(lev, P["b"], 1e-11, params=p)
+        assert sr == O.OK
+        x, info = H.solve_mixed(dev(P["b"]), tol=1e-10)
+        assert info["status"] == 0 and rel_2(host(x), xr) <= 1e-9
+
+
 def test_coarsest_solve_beyond_shared_memory():
     """A shallow hierarchy whose coarsest level (40 x 30 x 32 cells) exceeds
     one block's shared memory: the FP32 coarsest-level solve runs from

@@ -171,3 +171,27 @@ def test_vcycle_1_1_rate_is_set_by_the_smoother():
     print("two-grid stationary rates V(1,1), V(2,2):", rates)
     assert 0.35 <= rates[0] <= 0.6
     assert rates[1] <= 1.2 * rates[0] ** 2
+
+
+def test_isotropy_stopping_rule():
+    """levels = -1 stops at the first level whose largest (sum of horizontal
+    couplings) / h is within iso_ratio (Section 2.3's premise for stopping:
+    the coarse problem is well conditioned).  On the lat-lon sphere the pole
+    rows never get there before the depth limit (their ratio falls 4x per
+    level from ~850: 849, 213, 56, 15, 0.65 even with a Helmholtz term 100
+    times larger); with one 10^4 times larger it stops after one
+    coarsening."""
+    P = make_problem(64, 32, 16, 0.1, 1000)
+    deep = O.build_hierarchy(P["tx"], P["ty"], P["tz"], P["h"], O.MGParams())
+    iso = O.build_hierarchy(P["tx"], P["ty"], P["tz"], P["h"], O.MGParams(levels=-1))
+    assert len(iso) == len(deep)
+    assert all(O.horizontal_ratio(L) > 6.25 for L in iso)
+    h = P["h"] * 1e4
+    p = O.MGParams(levels=-1)
+    lev = O.build_hierarchy(P["tx"], P["ty"], P["tz"], h, p)
+    ratios = [O.horizontal_ratio(L) for L in lev]
+    print("ratios per level with h x 1e4:", ratios)
+    assert 1 < len(lev) < len(deep)
+    assert ratios[-1] <= p.iso_ratio and all(r > p.iso_ratio for r in ratios[:-1])
+    x, hist, st = O.solve(lev, P["b"], 1e-10, params=p)
+    assert st == O.OK
