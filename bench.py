@@ -236,9 +236,9 @@ KERNEL_WORDS = {
 # 512x384x70: 397.3 MB read + 34.8 MB written for 13,762,560 cells)
 SMOOTH_DOT_DRAM_BYTES_PER_CELL = (397.266944e6 + 34.799616e6) / (512 * 384 * 70)
 # DRAM bytes per fine cell of one k_resid_restrict<float> launch in its
-# presmoothing form on the finest level (ncu capture at 512x384x70: 227.5 MB
-# read + 13.3 MB written for 13,762,560 fine cells)
-RESID_RESTRICT_PRE_DRAM_BYTES_PER_CELL = (227.481344e6 + 13.346048e6) / (512 * 384 * 70)
+# presmoothing form on the finest level (ncu capture at 512x384x70: 232.6 MB
+# read + 16.1 MB written for 13,762,560 fine cells)
+RESID_RESTRICT_PRE_DRAM_BYTES_PER_CELL = (232.561408e6 + 16.097536e6) / (512 * 384 * 70)
 
 
 def kernel_table(H, L, N):

@@ -1031,13 +1031,43 @@ __device__ __forceinline__ void resid_restrict_band(const LevelDev<T> &F, const 
     P2 Us = jfirst > 0 ? ld_pair(uk + (size_t)(jfirst - 1) * nf) : zero;
     P2 Tys = jfirst > 0 ? ld_pair(tyk + (size_t)(jfirst - 1) * nf) : zero;
     P2 Uc = ld_pair(uk + (size_t)jfirst * nf);
+    // The FP32 PRE form has little arithmetic per row to cover its loads, so
+    // it issues the next row's loads (u and t_y one row north, b and t_x on
+    // the row) before combining this one: two rows in flight per thread.  The
+    // full residual, and FP64 (ALU-bound), keep one row.
+    constexpr bool kAhead = PRE && sizeof(T) == 4;
+    P2 nUn = zero, nB = zero, nTX = zero, nTYN = zero;
+    if (kAhead) {
+        const size_t o0 = (size_t)jfirst * nf;
+        nUn = jfirst + 1 < nlat ? ld_pair(uk + o0 + nf) : zero;
+        nB = ld_pair(bk + o0);
+        nTX = ld_pair(txk + o0);
+        nTYN = jfirst + 1 < nlat ? ld_pair(tyk + o0) : zero;
+    }
 #pragma unroll 1
     for (int j = jfirst; j <= jlast; ++j) {
         const bool hasN = j + 1 < nlat, hasS = j > 0;
         const size_t oj = (size_t)j * nf;
-        const P2 Un = hasN ? ld_pair(uk + oj + nf) : zero;
-        const P2 B = ld_pair(bk + oj), TX = ld_pair(txk + oj);
-        const P2 TYN = hasN ? ld_pair(tyk + oj) : zero;
+        P2 Un, B, TX, TYN;
+        if (kAhead) {
+            Un = nUn;
+            B = nB;
+            TX = nTX;
+            TYN = nTYN;
+            if (j < jlast) {
+                const size_t o1 = oj + nf;
+                const bool n1 = j + 2 < nlat;
+                nUn = n1 ? ld_pair(uk + o1 + nf) : zero;
+                nB = ld_pair(bk + o1);
+                nTX = ld_pair(txk + o1);
+                nTYN = n1 ? ld_pair(tyk + o1) : zero;
+            }
+        } else {
+            Un = hasN ? ld_pair(uk + oj + nf) : zero;
+            B = ld_pair(bk + oj);
+            TX = ld_pair(txk + oj);
+            TYN = hasN ? ld_pair(tyk + oj) : zero;
+        }
         const T uw = __shfl_up_sync(kAll, Uc.y, 1);    // u[2I-1]
         const T ue = __shfl_down_sync(kAll, Uc.x, 1);  // u[2I+2]
         const T txw = __shfl_up_sync(kAll, TX.y, 1);   // t_x[2I-1], west face of 2I

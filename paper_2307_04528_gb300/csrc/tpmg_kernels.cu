@@ -413,8 +413,10 @@ k_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ r, T *__restrict__ bc
 // L2 (bands before layers: 0.662 instead of 0.614 ms at 1536 x 1152 x 70).
 // PRE: u is the sweep from zero (the residual's presmoothing form).  band0:
 // first band of this launch (more than 65535 bands take several launches).
+// The FP32 PRE form runs at 12 blocks per SM (40 registers): its band walk
+// is latency-bound, and the extra resident warps outweigh a few spilled bytes.
 template <typename T, bool PRE>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, (PRE && sizeof(T) == 4) ? 12 : 0)
 k_resid_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ b, const T *__restrict__ u,
                  T *__restrict__ bc, T om1, int band0, const int *__restrict__ flag)
 {
