@@ -8,6 +8,7 @@ take as inputs; it holds none of the multigrid method's arithmetic
 """
 from .latlon import (  # noqa: F401
     ShellGrid,
+    make_ns_problem,
     make_problem,
     box_filter_3pt,
     WORKLOADS,

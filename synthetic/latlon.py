@@ -219,3 +219,61 @@ def workload_seed(name: str, member: int = 0) -> int:
     if name == "ensemble":
         return ENSEMBLE_SEED_BASE + member
     return WORKLOADS[name]["seed_base"] + member
+
+
+def make_ns_problem(nlon: int, nlat: int, nz: int, sigma: float, seed: int, pe: float = 0.3,
+                    **kw) -> dict:
+    """A nonsymmetric system: make_problem's operator plus upwind transport by
+    a seeded divergence-free flow (a model of the advective terms that make
+    the operational Helmholtz problem nonsymmetric).
+
+    Face volume fluxes come from two stream functions on cell corners, one in
+    the lon-lat plane (psi1 [nz, nlat+1, nlon], zero on the pole corners) and
+    one in the lon-height plane (psi2 [nz+1, nlat, nlon], zero at the surface
+    and the top):
+      Fx[k,j,i] = psi1[k,j+1,i] - psi1[k,j,i] + psi2[k+1,j,i] - psi2[k,j,i]  (east face)
+      Fy[k,j,i] = -(psi1[k,j+1,i] - psi1[k,j+1,i-1])                          (north face)
+      Fz[k,j,i] = -(psi2[k+1,j,i] - psi2[k+1,j,i-1])                          (upper face)
+    so every cell's net outflow vanishes and the pole, surface and top faces
+    carry none.  psi1 = pe * s_k * cos(theta_face) * g1 and psi2 = pe * s_k *
+    cos(theta_j) * g2, with g1, g2 box-filtered N(0,1) fields (as in
+    make_problem) and s_k the median longitude coupling of layer k, so the
+    transport is a fraction ~pe of the horizontal diffusion on every layer
+    and latitude.  Upwinding adds |F| to the coupling of the downstream row:
+    F > 0 (towards +i, +j, +k) to txr / tyr / tzr, F < 0 to tx / ty / tz.
+    h is unchanged, and with a divergence-free flow it is both the row and
+    the column sum of the transport-free part's mass.
+
+    Returns make_problem's dict with tx, ty, tz replaced by the directed
+    couplings, txr, tyr, tzr added, and the fluxes fx, fy, fz."""
+    P = make_problem(nlon, nlat, nz, sigma, seed, **kw)
+    grid = P["grid"]
+    rng = np.random.default_rng(seed + 7919)
+    g1 = rng.standard_normal((nz, nlat + 1, nlon))
+    g2 = rng.standard_normal((nz + 1, nlat, nlon))
+    for g in (g1, g2):
+        g[:] = box_filter_3pt(g, axis=2, periodic=True)
+        g[:] = box_filter_3pt(g, axis=1, periodic=False)
+        g[:] = box_filter_3pt(g, axis=0, periodic=False)
+    s = np.median(P["tx"].reshape(nz, -1), axis=1)              # [nz]
+    cos_f = grid._cos_lat_faces()                               # [nlat+1]
+    cos_c = np.cos(grid.lat_centres())                          # [nlat]
+    psi1 = pe * s[:, None, None] * cos_f[None, :, None] * g1
+    psi1[:, 0, :] = 0.0
+    psi1[:, nlat, :] = 0.0
+    s2 = np.concatenate([s[:1], s])                             # [nz+1]
+    psi2 = pe * s2[:, None, None] * cos_c[None, :, None] * g2
+    psi2[0] = 0.0
+    psi2[nz] = 0.0
+    fx = (psi1[:, 1:, :] - psi1[:, :-1, :]) + (psi2[1:] - psi2[:-1])
+    fy = -(psi1[:, 1:, :] - np.roll(psi1[:, 1:, :], 1, axis=2))
+    fz = -(psi2[1:] - np.roll(psi2[1:], 1, axis=2))
+    fy[:, nlat - 1, :] = 0.0
+    fz[nz - 1] = 0.0
+    out = dict(P)
+    for name, f in (("x", fx), ("y", fy), ("z", fz)):
+        t = P["t" + name]
+        out["t" + name] = t + np.maximum(-f, 0.0)
+        out["t" + name + "r"] = t + np.maximum(f, 0.0)
+        out["f" + name] = f
+    return out
