@@ -337,6 +337,94 @@ int mg_batch_solve(mg_batch *b, const double *const *bs, double *const *xs, doub
  * count and the summed event time in ms (synchronises on the events).
  * kind: 0 smoother (non-zero guess), 1 smoother (zero guess), 2 residual,
  * 3 apply, 4 restriction, 5 prolongation, 6 vector/reduction kernels. */
+/* ---- nonsymmetric operator (directed couplings) and its transpose.
+ * Section 1 names BiCGStab as the solver of the operational Helmholtz
+ * problem, which is nonsymmetric.  In this form every face carries two
+ * couplings, one for each row it enters:
+ *   tx[c]: row c's coupling to its east neighbour E;  txr[c]: row E's coupling to c
+ *   ty[c], tyr[c]: the same across c's north face;    tz[c], tzr[c]: across c's upper face
+ *   (H u)_c = h_c u_c + tx[c](u_c - u_E) + txr[W](u_c - u_W) + ty[c](u_c - u_N)
+ *             + tyr[S](u_c - u_S) + tz[c](u_c - u_U) + tzr[D](u_c - u_D)
+ * with W, S, D the west, south and lower neighbours.  h is H's row sum.
+ * H^T has the two couplings of every face swapped and the column sums
+ *   h^T_c = h_c + sum over c's six faces of (row coupling - column coupling)
+ * as its mass.  txr = tx, tyr = ty, tzr = tz is mg_setup's symmetric
+ * operator.  Requirements (else MG_ERR_COEFF): h > 0 and h^T > 0 (H
+ * diagonally dominant by rows and by columns), couplings finite and >= 0,
+ * pole and top faces 0 in all six coupling arrays.
+ * Hierarchy: Section 2.2's grid hierarchy (depends on the grid only), each
+ * of a face's two couplings coarsened by mg_setup's rule, masses summed;
+ * H^T's hierarchy is built by the same rule from H^T (its couplings are
+ * H's swapped, its masses the sums of the fine column sums).  A call with
+ * transpose = 1 works on H^T's hierarchy; its sweeps solve the transposed
+ * column systems.
+ * FP64 throughout.  params: method MG_METHOD_STATIONARY or
+ * MG_METHOD_BICGSTAB (V-cycle-preconditioned; CG and the line-relaxed
+ * BiCGStab are rejected), coarse_method MG_COARSE_JACOBI, mixed 0,
+ * levels >= 0; the other fields as for mg_setup (MG_ERR_ARG otherwise). */
+typedef struct mg_ns_handle mg_ns_handle;
+
+typedef struct {
+    const double *h, *tx, *ty, *tz, *txr, *tyr, *tzr;   /* device, [nz][nlat][nlon], FP64 */
+} mg_ns_coeffs;
+
+/* Workspace bytes mg_ns_setup needs (256-byte aligned start). */
+int mg_ns_workspace_bytes(const mg_grid *grid, const mg_params *params, size_t *bytes);
+
+/* Copy the seven arrays into the workspace, validate them, build both
+ * hierarchies and factor every column system of both.  Synchronises
+ * `stream`.  On failure *out is NULL. */
+int mg_ns_setup(const mg_grid *grid, const mg_ns_coeffs *coeffs, const mg_params *params,
+                void *workspace, size_t ws_bytes, void *stream, mg_ns_handle **out);
+
+/* Release the handle (host memory only). */
+void mg_ns_destroy(mg_ns_handle *h);
+
+/* y = H x (transpose 0) or y = H^T x (transpose 1) on the fine level; the
+ * transposed apply reads H's own arrays at the transposed positions (the
+ * couplings into c from its neighbours' rows) with h^T as its mass.  x, y:
+ * distinct device FP64 fields. */
+int mg_ns_apply(mg_ns_handle *h, int transpose, const double *x, double *y, void *stream);
+
+/* e = V r: one V(nu1, nu2) cycle from zero of H or of H^T (Section 2).  r, e:
+ * distinct device FP64 fine-level fields; r is not modified.  Uses the
+ * handle's level vectors: calls on one handle must not overlap. */
+int mg_ns_vcycle(mg_ns_handle *h, int transpose, const double *r, double *e, void *stream);
+
+/* Solve H x = b (transpose 0) or H^T x = b (transpose 1) to
+ * ||b - A x||_2 <= tol ||b||_2 with the configured method.  x: in =
+ * initial guess, out = solution.  Returns as mg_solve. */
+int mg_ns_solve(mg_ns_handle *h, int transpose, const double *b, double *x, double tol,
+                mg_stats *stats, void *stream);
+
+/* Gradient of a loss L(x) through H x = b with respect to the seven arrays,
+ * given x and lambda = H^{-T} dL/dx (mg_ns_solve with transpose = 1):
+ * dL/dtheta = -lambda^T (dH/dtheta) x, i.e.
+ *   gh = -lambda_c x_c,  gtx = -lambda_c (x_c - x_E),  gtxr = -lambda_E (x_E - x_c)
+ * and likewise north and up; 0 on the pole and top faces.  Device FP64
+ * fields; any output may be NULL. */
+int mg_ns_coeff_grad(mg_ns_handle *h, const double *lambda, const double *x, double *gh,
+                     double *gtx, double *gty, double *gtz, double *gtxr, double *gtyr,
+                     double *gtzr, void *stream);
+
+/* Levels and their shapes (as mg_num_levels / mg_level_shape). */
+int mg_ns_num_levels(const mg_ns_handle *h);
+int mg_ns_level_shape(const mg_ns_handle *h, int level, int *nlon, int *nlat, int *nz);
+
+/* Copies of level `level`'s arrays of H (transpose 0) or of H^T
+ * (transpose 1: h^T and the couplings as H^T sees them) into device FP64
+ * fields of the level's shape; a NULL output is skipped. */
+int mg_ns_level_coeffs(mg_ns_handle *h, int level, int transpose, double *h_out, double *tx,
+                       double *ty, double *tz, double *txr, double *tyr, double *tzr,
+                       void *stream);
+
+/* One sweep of Eq. (1) on a level of H or H^T:
+ * u_out = (1 - omega) u_in + omega A_z^{-1} (b - dA u_in), u_in NULL = zero
+ * guess.  Device FP64 fields of the level's shape; u_out distinct from
+ * u_in and b. */
+int mg_ns_level_smooth(mg_ns_handle *h, int level, int transpose, const double *b,
+                       const double *u_in, double *u_out, void *stream);
+
 int mg_profile_enable(mg_handle *h, int on);
 int mg_profile_read(mg_handle *h, int kind, int level, int prec, int *launches, double *ms);
 

@@ -17,7 +17,8 @@ from ._lib import (  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("MGHandle", "MGBatch", "MGSolveFn", "mg_solve_fn"):
+    if name in ("MGHandle", "MGBatch", "MGSolveFn", "mg_solve_fn", "NSHandle", "NSSolveFn",
+                "ns_solve_fn"):
         from . import solver
         return getattr(solver, name)
     raise AttributeError(name)

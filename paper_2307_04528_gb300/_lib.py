@@ -40,6 +40,10 @@ class mg_coeffs(ctypes.Structure):
                 ("h", ctypes.c_void_p)]
 
 
+class mg_ns_coeffs(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("h", "tx", "ty", "tz", "txr", "tyr", "tzr")]
+
+
 class mg_params(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("coarse_iters", ctypes.c_int), ("method", ctypes.c_int), ("mixed", ctypes.c_int),
@@ -114,6 +118,20 @@ def load() -> ctypes.CDLL:
                                 ctypes.POINTER(I)]),
         "mg_batch_solve": (I, [H, ctypes.POINTER(P), ctypes.POINTER(P), D, I,
                                ctypes.POINTER(mg_stats), ctypes.POINTER(I), P]),
+        "mg_ns_workspace_bytes": (I, [ctypes.POINTER(mg_grid), ctypes.POINTER(mg_params),
+                                      ctypes.POINTER(S)]),
+        "mg_ns_setup": (I, [ctypes.POINTER(mg_grid), ctypes.POINTER(mg_ns_coeffs),
+                            ctypes.POINTER(mg_params), P, S, P, ctypes.POINTER(H)]),
+        "mg_ns_destroy": (None, [H]),
+        "mg_ns_apply": (I, [H, I, P, P, P]),
+        "mg_ns_vcycle": (I, [H, I, P, P, P]),
+        "mg_ns_solve": (I, [H, I, P, P, D, ctypes.POINTER(mg_stats), P]),
+        "mg_ns_coeff_grad": (I, [H, P, P, P, P, P, P, P, P, P, P]),
+        "mg_ns_num_levels": (I, [H]),
+        "mg_ns_level_shape": (I, [H, I, ctypes.POINTER(I), ctypes.POINTER(I),
+                                  ctypes.POINTER(I)]),
+        "mg_ns_level_coeffs": (I, [H, I, I, P, P, P, P, P, P, P, P]),
+        "mg_ns_level_smooth": (I, [H, I, I, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -18,8 +18,8 @@ LIB = os.path.join(LIB_DIR, "libtpmg.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 KERNEL_SOURCES = ["tpmg_kernels.cu", "tpmg_noalloc.cu", "tpmg_batch.cu", "tpmg_krylov.cu",
-                  "tpmg_tma.cu"]
-HOST_SOURCES = ["tpmg_api.cpp", "tpmg_batch_api.cpp"]
+                  "tpmg_tma.cu", "tpmg_ns.cu"]
+HOST_SOURCES = ["tpmg_api.cpp", "tpmg_batch_api.cpp", "tpmg_ns_api.cpp"]
 HEADERS = ["tpmg_internal.h", "tpmg_handle.h", "tpmg_device.cuh"]
 
 

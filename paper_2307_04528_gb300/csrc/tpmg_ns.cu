@@ -1,0 +1,399 @@
+// Kernels of the nonsymmetric (directed-coupling) operator, FP64.
+//
+// Every face carries two couplings, one for each row it enters (the row's
+// own coupling to its east / north / upper neighbour, and the neighbour
+// row's coupling back).  A kernel sees one operator through an NsView: H
+// reads (h, tx, ty, tz, txr, tyr, tzr), H^T the same arrays swapped with the
+// column sums h^T as mass, so one set of kernels applies, smooths and
+// coarsens both, and the transposed apply is a transposed-stencil read of
+// H's own arrays.  Layout and traversal as the symmetric kernels: fields
+// [nz][nlat][nlon], one thread per column walking the layers (the column
+// solve of Eq. (1) is sequential in k), longitude fastest so that a warp's
+// loads of one layer are one coalesced segment.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "tpmg_internal.h"
+
+namespace tpmg {
+namespace {
+
+// Columns per block of the sweep: its forward values wait in shared memory
+// (nz x 64 doubles, 98 KB at the largest nz).
+constexpr int kNsSmoothBlock = 64;
+constexpr int kNsCellBlock = 256;
+
+struct Col {
+    int j, i, ie, iw;
+    bool hasN, hasS;
+};
+
+__device__ __forceinline__ Col col_of(int col, int nlon, int nlat)
+{
+    Col c;
+    c.j = col / nlon;
+    c.i = col - c.j * nlon;
+    c.ie = (c.i + 1 == nlon) ? col - c.i : col + 1;
+    c.iw = (c.i == 0) ? col + nlon - 1 : col - 1;
+    c.hasN = c.j + 1 < nlat;
+    c.hasS = c.j > 0;
+    return c;
+}
+
+// (A x)_c = h x_c + e (x_c - x_E) + w[W] (x_c - x_W) + n (x_c - x_N)
+//           + s[S] (x_c - x_S) + u (x_c - x_U) + d[D] (x_c - x_D)
+template <int MODE>
+__global__ void __launch_bounds__(kBlock)
+k_ns_stencil(NsView V, const double *__restrict__ b, const double *__restrict__ x,
+             double *__restrict__ y)
+{
+    const int nlon = V.nlon, nlat = V.nlat, nz = V.nz, ncol = nlon * nlat;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol) return;
+    const Col c = col_of(col, nlon, nlat);
+    const size_t plane = (size_t)ncol;
+    double xc = __ldg(x + col), xdn = 0.0, ddn = 0.0;
+    for (int k = 0; k < nz; ++k) {
+        const size_t o = (size_t)k * plane;
+        const double xup = (k + 1 < nz) ? __ldg(x + o + plane + col) : 0.0;
+        double v = __ldg(V.h + o + col) * xc;
+        v = fma(__ldg(V.e + o + col), xc - __ldg(x + o + c.ie), v);
+        v = fma(__ldg(V.w + o + c.iw), xc - __ldg(x + o + c.iw), v);
+        if (c.hasN) v = fma(__ldg(V.n + o + col), xc - __ldg(x + o + col + nlon), v);
+        if (c.hasS) v = fma(__ldg(V.s + o + col - nlon), xc - __ldg(x + o + col - nlon), v);
+        if (k + 1 < nz) v = fma(__ldg(V.u + o + col), xc - xup, v);
+        if (k > 0) v = fma(ddn, xc - xdn, v);
+        y[o + col] = MODE ? __ldg(b + o + col) - v : v;
+        ddn = __ldg(V.d + o + col);  // coupling of the row above back to this layer
+        xdn = xc;
+        xc = xup;
+    }
+}
+
+// r = (1 - omega) b + e u_E + w[W] u_W + n u_N + s[S] u_S
+__global__ void __launch_bounds__(kBlock)
+k_ns_presmooth_resid(NsView V, const double *__restrict__ b, const double *__restrict__ u,
+                     double om1, double *__restrict__ r)
+{
+    const int nlon = V.nlon, nlat = V.nlat, ncol = nlon * nlat;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol) return;
+    const Col c = col_of(col, nlon, nlat);
+    const size_t plane = (size_t)ncol;
+    for (int k = 0; k < V.nz; ++k) {
+        const size_t o = (size_t)k * plane;
+        double v = om1 * __ldg(b + o + col);
+        v = fma(__ldg(V.e + o + col), __ldg(u + o + c.ie), v);
+        v = fma(__ldg(V.w + o + c.iw), __ldg(u + o + c.iw), v);
+        if (c.hasN) v = fma(__ldg(V.n + o + col), __ldg(u + o + col + nlon), v);
+        if (c.hasS) v = fma(__ldg(V.s + o + col - nlon), __ldg(u + o + col - nlon), v);
+        r[o + col] = v;
+    }
+}
+
+// One sweep of Eq. (1) on a column: forward y_k = (v_k + l_k y_{k-1}) / p_k
+// with l_k = d[k-1] (the row's coupling to the layer below) and v = b plus the
+// horizontal couplings of u_in; backward x_k = x_{k+1} + (y_k - (q_k/p_k)
+// x_{k+1}); u_out = (1 - omega) u_in + omega x.  No block barrier: a thread
+// past the last column returns at once.
+template <bool ZERO>
+__global__ void __launch_bounds__(kNsSmoothBlock)
+k_ns_smooth(NsView V, const double *__restrict__ b, const double *__restrict__ uin,
+            double *__restrict__ uout, double omega)
+{
+    extern __shared__ double ns_ys[];
+    const int nlon = V.nlon, nlat = V.nlat, nz = V.nz, ncol = nlon * nlat;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol) return;
+    const int bd = blockDim.x, tid = threadIdx.x;
+    const Col c = col_of(col, nlon, nlat);
+    const size_t plane = (size_t)ncol;
+    double yprev = 0.0, ldn = 0.0;
+    for (int k = 0; k < nz; ++k) {
+        const size_t o = (size_t)k * plane;
+        double v = __ldg(b + o + col);
+        if (!ZERO) {
+            v = fma(__ldg(V.e + o + col), __ldg(uin + o + c.ie), v);
+            v = fma(__ldg(V.w + o + c.iw), __ldg(uin + o + c.iw), v);
+            if (c.hasN) v = fma(__ldg(V.n + o + col), __ldg(uin + o + col + nlon), v);
+            if (c.hasS) v = fma(__ldg(V.s + o + col - nlon), __ldg(uin + o + col - nlon), v);
+        }
+        const double y = fma(ldn, yprev, v) * __ldg(V.m + o + col);
+        ns_ys[(size_t)k * bd + tid] = y;
+        yprev = y;
+        ldn = __ldg(V.d + o + col);
+    }
+    const double om1 = 1.0 - omega;
+    double xk = yprev;
+    for (int k = nz - 1; k >= 0; --k) {
+        const size_t o = (size_t)k * plane + col;
+        if (k < nz - 1) xk = xk + fma(-__ldg(V.dq + o), xk, ns_ys[(size_t)k * bd + tid]);
+        uout[o] = ZERO ? omega * xk : fma(om1, __ldg(uin + o), omega * xk);
+    }
+}
+
+// Column factors: s = h + e + w[W] + n + s[S]; q_0 = s_0, q_k = s_k + l_k
+// q_{k-1} / p_{k-1} (l_k = d[k-1]), p_k = q_k + u_k; m = 1/p, dq = q/p.
+__global__ void __launch_bounds__(kBlock)
+k_ns_column_lu(NsView V, double *__restrict__ m, double *__restrict__ dq)
+{
+    const int nlon = V.nlon, nlat = V.nlat, ncol = nlon * nlat;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol) return;
+    const Col c = col_of(col, nlon, nlat);
+    const size_t plane = (size_t)ncol;
+    double qp = 0.0, pp = 1.0, ldn = 0.0;
+    for (int k = 0; k < V.nz; ++k) {
+        const size_t o = (size_t)k * plane;
+        double sv = V.h[o + col] + V.e[o + col] + V.w[o + c.iw] + V.n[o + col];
+        if (c.hasS) sv += V.s[o + col - nlon];
+        const double q = (k == 0) ? sv : sv + ldn * qp / pp;
+        const double p = q + V.u[o + col];
+        m[o + col] = 1.0 / p;
+        dq[o + col] = q / p;
+        qp = q;
+        pp = p;
+        ldn = V.d[o + col];
+    }
+}
+
+// h^T = h + (e - w) + (w[W] - e[W]) + (n - s) + (s[S] - n[S]) + (u - d) + (d[D] - u[D])
+// of the forward view (e, n, u = tx, ty, tz; w, s, d = txr, tyr, tzr).
+__global__ void __launch_bounds__(kNsCellBlock)
+k_ns_colmass(NsView V, double *__restrict__ hT)
+{
+    const int nlon = V.nlon, nlat = V.nlat, ncol = nlon * nlat;
+    const size_t n = (size_t)ncol * V.nz;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const int k = (int)(idx / ncol), col = (int)(idx - (size_t)k * ncol);
+    const Col c = col_of(col, nlon, nlat);
+    const size_t o = (size_t)k * ncol;
+    double v = V.h[idx] + (V.e[idx] - V.w[idx]);
+    v = v + (V.w[o + c.iw] - V.e[o + c.iw]);
+    v = v + (V.n[idx] - V.s[idx]);
+    if (c.hasS) v = v + (V.s[idx - nlon] - V.n[idx - nlon]);
+    v = v + (V.u[idx] - V.d[idx]);
+    if (k > 0) v = v + (V.d[idx - ncol] - V.u[idx - ncol]);
+    hT[idx] = v;
+}
+
+// One thread per coarse column walks the layers: sums over the 2 x cnt
+// children, the east faces of the odd fine columns, the top child row's
+// north faces; lon faces x sx, lat faces x sy[J] (0 on the last row).
+__global__ void __launch_bounds__(kBlock)
+k_ns_coarsen(NsView F, LinkDev K, double sx, double *__restrict__ hc, double *__restrict__ ec,
+             double *__restrict__ nc_, double *__restrict__ uc, double *__restrict__ wc,
+             double *__restrict__ sc, double *__restrict__ dc)
+{
+    const int nf = F.nlon, nci = nf / 2;
+    const int ncol_c = nci * K.nlat_c;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol_c) return;
+    const int J = col / nci, I = col - J * nci;
+    const int j0 = K.cfirst[J], cnt = K.ccnt[J], top = j0 + cnt - 1;
+    const size_t plane_f = (size_t)nf * F.nlat, plane_c = (size_t)ncol_c;
+    const bool last = J == K.nlat_c - 1;
+    const double sy = last ? 0.0 : K.sy[J];
+    for (int k = 0; k < F.nz; ++k) {
+        const size_t of = (size_t)k * plane_f;
+        double hs = 0, us = 0, ds = 0, es = 0, ws = 0;
+        for (int j = j0; j <= top; ++j) {
+            const size_t a = of + (size_t)j * nf + 2 * I;
+            hs += F.h[a];
+            hs += F.h[a + 1];
+            if (uc) {
+                us += F.u[a];
+                us += F.u[a + 1];
+                ds += F.d[a];
+                ds += F.d[a + 1];
+                es += F.e[a + 1];
+                ws += F.w[a + 1];
+            }
+        }
+        const size_t oc = (size_t)k * plane_c + col;
+        hc[oc] = hs;
+        if (!uc) continue;
+        const size_t t = of + (size_t)top * nf + 2 * I;
+        double ns = 0, ss = 0;
+        ns += F.n[t];
+        ns += F.n[t + 1];
+        ss += F.s[t];
+        ss += F.s[t + 1];
+        uc[oc] = us;
+        dc[oc] = ds;
+        ec[oc] = es * sx;
+        wc[oc] = ws * sx;
+        nc_[oc] = last ? 0.0 : ns * sy;
+        sc[oc] = last ? 0.0 : ss * sy;
+    }
+}
+
+__device__ __forceinline__ bool ok_coupling(double t) { return t >= 0.0 && isfinite(t); }
+
+// bits: 1 h <= 0 or non-finite, 2 a coupling < 0 or non-finite, 4 a non-zero
+// pole or top face
+__global__ void __launch_bounds__(kNsCellBlock)
+k_ns_validate(NsView V, int *__restrict__ flag)
+{
+    const int ncol = V.nlon * V.nlat;
+    const size_t n = (size_t)ncol * V.nz;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const int k = (int)(idx / ncol), col = (int)(idx - (size_t)k * ncol);
+    const int j = col / V.nlon;
+    int bits = 0;
+    const double h = V.h[idx];
+    if (!(h > 0.0) || !isfinite(h)) bits |= 1;
+    const double e = V.e[idx], nn = V.n[idx], u = V.u[idx];
+    const double w = V.w[idx], s = V.s[idx], d = V.d[idx];
+    if (!ok_coupling(e) || !ok_coupling(nn) || !ok_coupling(u) || !ok_coupling(w) ||
+        !ok_coupling(s) || !ok_coupling(d))
+        bits |= 2;
+    if (j == V.nlat - 1 && (nn != 0.0 || s != 0.0)) bits |= 4;
+    if (k == V.nz - 1 && (u != 0.0 || d != 0.0)) bits |= 4;
+    if (bits) atomicOr(flag, bits);
+}
+
+__global__ void __launch_bounds__(kNsCellBlock)
+k_ns_positive(const double *__restrict__ a, size_t n, int *__restrict__ flag)
+{
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const double v = a[idx];
+    if (!(v > 0.0) || !isfinite(v)) atomicOr(flag, 8);
+}
+
+// dL/dtheta = -lam^T (dH/dtheta) x per array entry
+__global__ void __launch_bounds__(kNsCellBlock)
+k_ns_coeff_grad(int nlon, int nlat, int nz, const double *__restrict__ lam,
+                const double *__restrict__ x, double *__restrict__ gh, double *__restrict__ gtx,
+                double *__restrict__ gty, double *__restrict__ gtz, double *__restrict__ gtxr,
+                double *__restrict__ gtyr, double *__restrict__ gtzr)
+{
+    const int ncol = nlon * nlat;
+    const size_t n = (size_t)ncol * nz;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const int k = (int)(idx / ncol), col = (int)(idx - (size_t)k * ncol);
+    const Col c = col_of(col, nlon, nlat);
+    const size_t o = (size_t)k * ncol;
+    const double lc = lam[idx], xc = x[idx];
+    if (gh) gh[idx] = -lc * xc;
+    const double le = lam[o + c.ie], xe = x[o + c.ie];
+    if (gtx) gtx[idx] = -lc * (xc - xe);
+    if (gtxr) gtxr[idx] = -le * (xe - xc);
+    if (c.hasN) {
+        const double ln = lam[idx + nlon], xn = x[idx + nlon];
+        if (gty) gty[idx] = -lc * (xc - xn);
+        if (gtyr) gtyr[idx] = -ln * (xn - xc);
+    } else {
+        if (gty) gty[idx] = 0.0;
+        if (gtyr) gtyr[idx] = 0.0;
+    }
+    if (k + 1 < nz) {
+        const double lu = lam[idx + ncol], xu = x[idx + ncol];
+        if (gtz) gtz[idx] = -lc * (xc - xu);
+        if (gtzr) gtzr[idx] = -lu * (xu - xc);
+    } else {
+        if (gtz) gtz[idx] = 0.0;
+        if (gtzr) gtzr[idx] = 0.0;
+    }
+}
+
+int col_blocks(const NsView &V, int block) { return (V.nlon * V.nlat + block - 1) / block; }
+
+unsigned cell_blocks(size_t n) { return (unsigned)((n + kNsCellBlock - 1) / kNsCellBlock); }
+
+}  // namespace
+
+size_t ns_smooth_smem_bytes(int nz) { return (size_t)nz * kNsSmoothBlock * sizeof(double); }
+
+cudaError_t ns_prepare()
+{
+    const int bytes = (int)ns_smooth_smem_bytes(kMaxLayers);
+    cudaError_t e = cudaFuncSetAttribute(k_ns_smooth<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_ns_smooth<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                bytes);
+}
+
+cudaError_t launch_ns_stencil(const NsView &V, int mode, const double *b, const double *x,
+                              double *y, cudaStream_t s)
+{
+    if (mode)
+        k_ns_stencil<1><<<col_blocks(V, kBlock), kBlock, 0, s>>>(V, b, x, y);
+    else
+        k_ns_stencil<0><<<col_blocks(V, kBlock), kBlock, 0, s>>>(V, b, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ns_presmooth_resid(const NsView &V, const double *b, const double *u,
+                                      double omega, double *r, cudaStream_t s)
+{
+    k_ns_presmooth_resid<<<col_blocks(V, kBlock), kBlock, 0, s>>>(V, b, u, 1.0 - omega, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ns_smooth(const NsView &V, const double *b, const double *u_in,
+                             double *u_out, double omega, cudaStream_t s)
+{
+    const size_t smem = ns_smooth_smem_bytes(V.nz);
+    const int grid = col_blocks(V, kNsSmoothBlock);
+    if (u_in)
+        k_ns_smooth<false><<<grid, kNsSmoothBlock, smem, s>>>(V, b, u_in, u_out, omega);
+    else
+        k_ns_smooth<true><<<grid, kNsSmoothBlock, smem, s>>>(V, b, nullptr, u_out, omega);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ns_column_lu(const NsView &V, double *m, double *dq, cudaStream_t s)
+{
+    k_ns_column_lu<<<col_blocks(V, kBlock), kBlock, 0, s>>>(V, m, dq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ns_colmass(const NsView &V, double *hT, cudaStream_t s)
+{
+    const size_t n = (size_t)V.nlon * V.nlat * V.nz;
+    k_ns_colmass<<<cell_blocks(n), kNsCellBlock, 0, s>>>(V, hT);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ns_coarsen(const NsView &F, const LinkDev &K, double sx, double *h,
+                              double *e, double *n, double *u, double *w, double *sv, double *d,
+                              cudaStream_t s)
+{
+    const int ncol_c = (F.nlon / 2) * K.nlat_c;
+    k_ns_coarsen<<<(ncol_c + kBlock - 1) / kBlock, kBlock, 0, s>>>(F, K, sx, h, e, n, u, w, sv,
+                                                                   d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ns_validate(const NsView &V, int *flag, cudaStream_t s)
+{
+    const size_t n = (size_t)V.nlon * V.nlat * V.nz;
+    k_ns_validate<<<cell_blocks(n), kNsCellBlock, 0, s>>>(V, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ns_positive(const double *a, size_t n, int *flag, cudaStream_t s)
+{
+    k_ns_positive<<<cell_blocks(n), kNsCellBlock, 0, s>>>(a, n, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ns_coeff_grad(int nlon, int nlat, int nz, const double *lam, const double *x,
+                                 double *gh, double *gtx, double *gty, double *gtz,
+                                 double *gtxr, double *gtyr, double *gtzr, cudaStream_t s)
+{
+    const size_t n = (size_t)nlon * nlat * nz;
+    k_ns_coeff_grad<<<cell_blocks(n), kNsCellBlock, 0, s>>>(nlon, nlat, nz, lam, x, gh, gtx, gty,
+                                                            gtz, gtxr, gtyr, gtzr);
+    return cudaGetLastError();
+}
+
+}  // namespace tpmg

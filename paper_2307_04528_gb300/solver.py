@@ -262,14 +262,14 @@ class MGFloorWarning(RuntimeWarning):
     caller's floor_accept, and its solution was used."""
 
 
-def _solve_checked(handle, b, tol, floor_accept=None):
+def _solve_checked(handle, b, tol, floor_accept=None, **solve_kw):
     """Solve and raise on any failure, except that a solve stopping on maxit
     with rel_res <= floor_accept is accepted with an MGFloorWarning.  The
     FP64 rounding floor of the residual (rounding of x times the vertical
     couplings: ~1e-12..1e-10 relative, higher for smooth right-hand sides
     such as an adjoint dL/dx) can sit above a tight tol while the solution
     is accurate; floor_accept=None (the default) accepts nothing."""
-    x, info = handle.solve(b, tol=tol, raise_on_error=False)
+    x, info = handle.solve(b, tol=tol, raise_on_error=False, **solve_kw)
     st = info["status"]
     if st == L.MG_OK:
         return x, info
@@ -391,3 +391,136 @@ class MGSolveFn(torch.autograd.Function):
 def mg_solve_fn(b, h, tx, ty, tz, tol=1e-11, floor_accept=None, **params):
     """Differentiable solve (MGSolveFn); params: mg_params overrides."""
     return MGSolveFn.apply(b, h, tx, ty, tz, tol, params, floor_accept)
+
+
+_NS_ARRAYS = ("h", "tx", "ty", "tz", "txr", "tyr", "tzr")
+
+
+class NSHandle:
+    """Multigrid hierarchies of a nonsymmetric operator H (directed couplings,
+    mg_ns_* in include/tpmg.h) and of its transpose.
+
+    h, tx, ty, tz, txr, tyr, tzr: CUDA float64 tensors [nz, nlat, nlon]
+    (tx[c]: row c's coupling to its east neighbour; txr[c]: that neighbour's
+    row's coupling back to c; likewise north and up; h: the row sums).
+    params: mg_params overrides; method MG_METHOD_BICGSTAB (default here) or
+    MG_METHOD_STATIONARY.  Every call takes transpose=False (H) or True (H^T).
+    """
+
+    def __init__(self, h, tx, ty, tz, txr, tyr, tzr, stream=None, **params):
+        self.lib = L.load()
+        nz, nlat, nlon = h.shape
+        self.shape = (nz, nlat, nlon)
+        arrays = (h, tx, ty, tz, txr, tyr, tzr)
+        for name, t in zip(_NS_ARRAYS, arrays):
+            _field(t, torch.float64, self.shape, name)
+        self.device = h.device
+        self.grid = L.mg_grid(nlon, nlat, nz)
+        params.setdefault("method", L.MG_METHOD_BICGSTAB)
+        self.params = L.default_params(**params)
+        nbytes = ctypes.c_size_t(0)
+        L.check(self.lib.mg_ns_workspace_bytes(ctypes.byref(self.grid),
+                                               ctypes.byref(self.params), ctypes.byref(nbytes)))
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        co = L.mg_ns_coeffs(*(t.data_ptr() for t in arrays))
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            L.check(self.lib.mg_ns_setup(ctypes.byref(self.grid), ctypes.byref(co),
+                                         ctypes.byref(self.params), _ptr(self.workspace),
+                                         nbytes, _stream(stream), ctypes.byref(self._h)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self.lib.mg_ns_destroy(h)
+            self._h = None
+
+    @property
+    def num_levels(self) -> int:
+        return int(self.lib.mg_ns_num_levels(self._h))
+
+    def level_shape(self, level: int):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        L.check(self.lib.mg_ns_level_shape(self._h, level, ctypes.byref(a), ctypes.byref(b),
+                                           ctypes.byref(c)))
+        return (c.value, b.value, a.value)
+
+    def level_coeffs(self, level: int, transpose=False):
+        """The level's (h, tx, ty, tz, txr, tyr, tzr) of H, or of H^T."""
+        shp = self.level_shape(level)
+        out = [torch.empty(shp, dtype=torch.float64, device=self.device) for _ in range(7)]
+        L.check(self.lib.mg_ns_level_coeffs(self._h, level, int(transpose), *map(_ptr, out),
+                                            _stream()))
+        return out
+
+    def apply(self, x, transpose=False, y=None):
+        _field(x, torch.float64, self.shape, "x")
+        y = torch.empty_like(x) if y is None else y
+        L.check(self.lib.mg_ns_apply(self._h, int(transpose), _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def vcycle(self, r, transpose=False, e=None):
+        _field(r, torch.float64, self.shape, "r")
+        e = torch.empty_like(r) if e is None else e
+        L.check(self.lib.mg_ns_vcycle(self._h, int(transpose), _ptr(r), _ptr(e), _stream()))
+        return e
+
+    def level_smooth(self, level, b, u_in=None, transpose=False):
+        out = torch.empty_like(b)
+        L.check(self.lib.mg_ns_level_smooth(self._h, level, int(transpose), _ptr(b), _ptr(u_in),
+                                            _ptr(out), _stream()))
+        return out
+
+    def solve(self, b, x=None, tol=1e-10, transpose=False, history_cap=512,
+              raise_on_error=True):
+        """Solve H x = b (or H^T x = b); x is the initial guess, overwritten."""
+        _field(b, torch.float64, self.shape, "b")
+        x = torch.zeros_like(b) if x is None else x
+        _field(x, torch.float64, self.shape, "x")
+        hist = (ctypes.c_double * history_cap)()
+        st = L.mg_stats(0, 0, 0.0, hist, history_cap, 0)
+        status = self.lib.mg_ns_solve(self._h, int(transpose), _ptr(b), _ptr(x), float(tol),
+                                      ctypes.byref(st), _stream())
+        if raise_on_error:
+            L.check(status)
+        info = dict(status=status, iterations=st.iterations, rel_res=st.rel_res,
+                    history=[hist[i] for i in range(st.history_len)])
+        return x, info
+
+    def coeff_grad(self, lam, x):
+        """(gh, gtx, gty, gtz, gtxr, gtyr, gtzr) = -lam^T (dH/dtheta) x."""
+        out = [torch.empty_like(x) for _ in range(7)]
+        L.check(self.lib.mg_ns_coeff_grad(self._h, _ptr(lam), _ptr(x), *map(_ptr, out),
+                                          _stream()))
+        return out
+
+
+class NSSolveFn(torch.autograd.Function):
+    """x = H^{-1} b for the nonsymmetric operator, differentiable in b and the
+    seven arrays.  Backward solves the adjoint system H^T lambda = dL/dx on
+    the transposed hierarchy (a different operator from H now) and forms
+    the seven gradients in one kernel; statuses in ctx.infos."""
+
+    @staticmethod
+    def forward(ctx, b, h, tx, ty, tz, txr, tyr, tzr, tol=1e-10, params=None,
+                floor_accept=None):
+        arrays = [t.detach().contiguous() for t in (h, tx, ty, tz, txr, tyr, tzr)]
+        handle = NSHandle(*arrays, **dict(params or {}))
+        x, info = _solve_checked(handle, b.detach().contiguous(), tol, floor_accept)
+        ctx.handle, ctx.tol, ctx.floor_accept, ctx.infos = handle, tol, floor_accept, [info]
+        ctx.save_for_backward(x)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        lam, info = _solve_checked(ctx.handle, gx.contiguous(), ctx.tol, ctx.floor_accept,
+                                   transpose=True)
+        ctx.infos.append(info)
+        grads = ctx.handle.coeff_grad(lam, x)
+        return (lam, *grads, None, None, None)
+
+
+def ns_solve_fn(b, h, tx, ty, tz, txr, tyr, tzr, tol=1e-10, floor_accept=None, **params):
+    """Differentiable nonsymmetric solve (NSSolveFn); params: mg_params overrides."""
+    return NSSolveFn.apply(b, h, tx, ty, tz, txr, tyr, tzr, tol, params, floor_accept)

@@ -123,3 +123,38 @@ def test_isotropy_rule_sized_for_full_depth(lib):
     assert st0 == st1 == 0 and n1 >= n0
     st, _ = _bytes(lib, 64, 32, 16, levels=-1, iso_ratio=0.0)
     assert st == 1
+
+
+def _ns_bytes(lib, nlon, nlat, nz, **kw):
+    from paper_2307_04528_gb300 import _lib as L
+    kw.setdefault("method", L.MG_METHOD_BICGSTAB)
+    g = L.mg_grid(nlon, nlat, nz)
+    p = L.default_params(**kw)
+    n = ctypes.c_size_t(0)
+    st = lib.mg_ns_workspace_bytes(ctypes.byref(g), ctypes.byref(p), ctypes.byref(n))
+    return st, n.value
+
+
+def test_nonsymmetric_workspace_and_parameter_checks(lib):
+    """The nonsymmetric hierarchy holds 15 level fields (seven arrays, the
+    column sums, two factor pairs, three vectors) plus the right-hand side on
+    coarse levels and nine fine solver vectors; it takes the stationary
+    iteration or BiCGStab, the sweep coarse solve, FP64, a fixed depth."""
+    from paper_2307_04528_gb300 import _lib as L
+    st, n = _ns_bytes(lib, 64, 32, 16)
+    assert st == 0 and n >= 64 * 32 * 16 * 8 * (15 + 9)
+    st2, n2 = _ns_bytes(lib, 64, 32, 16, method=L.MG_METHOD_STATIONARY)
+    assert st2 == 0 and n2 == n
+    for kw in ({"method": L.MG_METHOD_CG}, {"method": L.MG_METHOD_BICGSTAB_LINE},
+               {"coarse_method": L.MG_COARSE_PCG}, {"mixed": 1}, {"levels": -1},
+               {"omega": 2.5}):
+        st, _ = _ns_bytes(lib, 64, 32, 16, **kw)
+        assert st == L.MG_ERR_ARG, kw
+        assert lib.mg_last_error()
+    g = L.mg_grid(64, 32, 16)
+    p = L.default_params(method=L.MG_METHOD_BICGSTAB)
+    h = ctypes.c_void_p()
+    co = L.mg_ns_coeffs(0, 0, 0, 0, 0, 0, 0)
+    assert lib.mg_ns_setup(ctypes.byref(g), ctypes.byref(co), ctypes.byref(p), None, 0, None,
+                           ctypes.byref(h)) == L.MG_ERR_ARG and not h.value
+    assert lib.mg_ns_num_levels(None) == 0
