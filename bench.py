@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-from synthetic import WORKLOADS, make_problem, workload_seed  # noqa: E402
+from synthetic import WORKLOADS, make_ns_problem, make_problem, workload_seed  # noqa: E402
 from synthetic.latlon import ENSEMBLE_MEMBERS  # noqa: E402
 
 METRIC = "ms to 1e-10 rel residual, 1536x1152x70: FP32-MG+FP64 refine vs FP64 MG; HBM %"
@@ -628,6 +628,17 @@ PROBE_KERNELS = {
     # and latitude), FP32 multigrid in FP64 refinement to 1e-8 (the batched
     # persistent kernels)
     "batch_mixed": (1, "batch", None),
+    # the nonsymmetric operator (synthetic transport, pe 0.3), FP64: the
+    # apply of H and the transposed-stencil apply of H^T (h, 6 couplings, x ->
+    # y), the sweep (b u e w n s d m dq -> u) and the sweep from zero (b d m dq
+    # -> u), the V-cycle and BiCGStab solves of H and H^T
+    "ns_apply64": (0, "ns_apply", 9),
+    "ns_apply64_T": (0, "ns_apply_T", 9),
+    "ns_smooth64": (0, "ns_smooth", 10),
+    "ns_smooth64_zero": (0, "ns_smooth0", 5),
+    "ns_vcycle64": (0, "ns_vcycle", None),
+    "ns_solve64": (0, "ns_solve", None),
+    "ns_solve64_T": (0, "ns_solve_T", None),
 }
 
 
@@ -642,10 +653,15 @@ def run_kernel(args):
     from paper_2307_04528_gb300.solver import MGHandle
 
     nlon, nlat, nz = args.shape
-    P = make_problem(nlon, nlat, nz, args.sigma, 3000)
-    d = lambda a, dt=torch.float64: torch.as_tensor(a).to("cuda", dt)
-    H = MGHandle(d(P["tx"]), d(P["ty"]), d(P["tz"]), d(P["h"]), mixed=1)
     prec, op, words = PROBE_KERNELS[args.kernel]
+    d = lambda a, dt=torch.float64: torch.as_tensor(a).to("cuda", dt)
+    if op.startswith("ns_"):
+        from paper_2307_04528_gb300.solver import NSHandle
+        P = make_ns_problem(nlon, nlat, nz, args.sigma, 3000)
+        H = NSHandle(*(d(P[k]) for k in ("h", "tx", "ty", "tz", "txr", "tyr", "tzr")))
+    else:
+        P = make_problem(nlon, nlat, nz, args.sigma, 3000)
+        H = MGHandle(d(P["tx"]), d(P["ty"]), d(P["tz"]), d(P["h"]), mixed=1)
     if op == "batch":
         from paper_2307_04528_gb300.solver import MGBatch
         probs = [P] + [make_problem(nlon // f, nlat // f, nz, args.sigma, 3000 + f) for f in (2, 4)]
@@ -665,6 +681,17 @@ def run_kernel(args):
     x64 = torch.zeros_like(b64)
 
     def run():
+        if op in ("ns_apply", "ns_apply_T"):
+            return H.apply(u, transpose=op.endswith("_T"))
+        if op == "ns_smooth":
+            return H.level_smooth(0, b, u)
+        if op == "ns_smooth0":
+            return H.level_smooth(0, b, None)
+        if op == "ns_vcycle":
+            return H.vcycle(b)
+        if op in ("ns_solve", "ns_solve_T"):
+            x64.zero_()
+            return H.solve(b64, x64, tol=TOL, transpose=op.endswith("_T"))
         if op == "smooth":
             return H.level_smooth(0, b, u, prec=prec)
         if op == "smooth_dot":
@@ -823,6 +850,82 @@ def run_krylov(args):
     print(json.dumps(out))
 
 
+def run_ns(args):
+    """The nonsymmetric operator (the transport-augmented 1536 x 1152 x 70
+    system, pe 0.3): FP64 BiCGStab preconditioned by the V-cycle to 1e-10 for
+    H and for H^T (the adjoint solve of a differentiable nonsymmetric solve),
+    beside the same method on the symmetric operator without the transport,
+    and the event times of the nonsymmetric fine-level kernels."""
+    import torch
+
+    from paper_2307_04528_gb300 import _lib as L
+    from paper_2307_04528_gb300.solver import MGHandle, NSHandle
+
+    w = WORKLOADS["latlon_1536x1152x70"]
+    seed = workload_seed("latlon_1536x1152x70")
+    P = make_ns_problem(w["nlon"], w["nlat"], w["nz"], w["sigma"], seed, pe=0.3)
+    d = lambda a: torch.as_tensor(a, dtype=torch.float64).cuda()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    b = d(P["b"])
+    H = NSHandle(*(d(P[k]) for k in ("h", "tx", "ty", "tz", "txr", "tyr", "tzr")),
+                 method=L.MG_METHOD_BICGSTAB)
+    out = {"metric": "ms to 1e-10 rel residual, nonsymmetric 1536x1152x70 (transport pe 0.3), "
+                     "FP64 BiCGStab + V-cycle: H and H^T", "unit": "ms", "n_gpus": 1,
+           "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "latlon_1536x1152x70_transport", "unknowns": int(b.numel()),
+                      "tol": TOL, "levels": H.num_levels}}
+    x = torch.zeros_like(b)
+    for tr in (False, True):
+        def solve():
+            x.zero_()
+            return H.solve(b, x, tol=TOL, transpose=tr, raise_on_error=False)
+        ms, (_, info) = timed(solve, args.steps)
+        out["transpose" if tr else "forward"] = {
+            "ms": ms, "status": info["status"], "iterations": info["iterations"],
+            "rel_res": info["rel_res"]}
+    out["value"] = out["forward"]["ms"]
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    u = torch.randn(b.shape, generator=gen, device="cuda", dtype=torch.float64)
+    n = b.numel()
+    kern = []
+    for name, fn, words in (("k_ns_stencil (H x)", lambda: H.apply(u), 9),
+                            ("k_ns_stencil (H^T x, transposed stencil)",
+                             lambda: H.apply(u, transpose=True), 9),
+                            ("k_ns_smooth (sweep)", lambda: H.level_smooth(0, b, u), 10),
+                            ("k_ns_smooth (from zero)", lambda: H.level_smooth(0, b, None), 5)):
+        ms, _ = timed(fn, 10)
+        kern.append({"kernel": name, "avg_ms": ms, "alg_bytes": 8.0 * words * n,
+                     "gbs": 8.0 * words * n / (ms * 1e-3) / 1e9})
+    out["kernels_fine_level"] = kern
+    del H, x, u
+    torch.cuda.empty_cache()
+    S = make_problem(w["nlon"], w["nlat"], w["nz"], w["sigma"], seed)
+    Hs = MGHandle(*(d(S[k]) for k in ("tx", "ty", "tz", "h")), method=L.MG_METHOD_BICGSTAB)
+    bs = d(S["b"])
+    xs = torch.zeros_like(bs)
+
+    def solve_sym():
+        xs.zero_()
+        return Hs.solve(bs, xs, tol=TOL, raise_on_error=False)
+    ms, (_, info) = timed(solve_sym, args.steps)
+    out["symmetric_same_method"] = {"ms": ms, "status": info["status"],
+                                    "iterations": info["iterations"]}
+    out["steps"] = args.steps
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.kernel:
@@ -833,6 +936,9 @@ def main():
         return
     if args.workload == "ensemble":
         run_ensemble(args)
+        return
+    if args.workload == "ns":
+        run_ns(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -371,9 +371,6 @@ cudaError_t launch_ns_presmooth_resid(const NsView &V, const double *b, const do
 // (u_in == nullptr: zero guess).
 cudaError_t launch_ns_smooth(const NsView &V, const double *b, const double *u_in,
                              double *u_out, double omega, cudaStream_t s);
-// Dynamic shared memory of the sweep (forward values of a block's columns).
-size_t ns_smooth_smem_bytes(int nz);
-cudaError_t ns_prepare();
 // Column factors of a view.
 cudaError_t launch_ns_column_lu(const NsView &V, double *m, double *dq, cudaStream_t s);
 // h^T = h + sum over the six faces of (row coupling - column coupling) of H

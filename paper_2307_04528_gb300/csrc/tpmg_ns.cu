@@ -20,8 +20,7 @@
 namespace tpmg {
 namespace {
 
-// Columns per block of the sweep: its forward values wait in shared memory
-// (nz x 64 doubles, 98 KB at the largest nz).
+// Columns per block of the sweep.
 constexpr int kNsSmoothBlock = 64;
 constexpr int kNsCellBlock = 256;
 
@@ -44,6 +43,34 @@ __device__ __forceinline__ Col col_of(int col, int nlon, int nlat)
 
 // (A x)_c = h x_c + e (x_c - x_E) + w[W] (x_c - x_W) + n (x_c - x_N)
 //           + s[S] (x_c - x_S) + u (x_c - x_U) + d[D] (x_c - x_D)
+// The loads of layers k+1 .. k+kStDepth-1 are in flight while layer k is
+// combined (a register pipeline, as the symmetric stencil's).
+constexpr int kStDepth = 2;
+
+struct StLoads {
+    double xc, h, e, w, n, s, u, d, xe, xw, xn, xs, b;
+};
+
+template <int MODE>
+__device__ __forceinline__ void st_load(StLoads &L, const NsView &V, const double *__restrict__ b,
+                                        const double *__restrict__ x, size_t o, int col,
+                                        const Col &c, int nlon)
+{
+    L.xc = __ldg(x + o + col);
+    L.h = __ldg(V.h + o + col);
+    L.e = __ldg(V.e + o + col);
+    L.w = __ldg(V.w + o + c.iw);
+    L.u = __ldg(V.u + o + col);
+    L.d = __ldg(V.d + o + col);
+    L.xe = __ldg(x + o + c.ie);
+    L.xw = __ldg(x + o + c.iw);
+    L.n = c.hasN ? __ldg(V.n + o + col) : 0.0;
+    L.xn = c.hasN ? __ldg(x + o + col + nlon) : 0.0;
+    L.s = c.hasS ? __ldg(V.s + o + col - nlon) : 0.0;
+    L.xs = c.hasS ? __ldg(x + o + col - nlon) : 0.0;
+    if (MODE) L.b = __ldg(b + o + col);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kBlock)
 k_ns_stencil(NsView V, const double *__restrict__ b, const double *__restrict__ x,
@@ -54,21 +81,32 @@ k_ns_stencil(NsView V, const double *__restrict__ b, const double *__restrict__ 
     if (col >= ncol) return;
     const Col c = col_of(col, nlon, nlat);
     const size_t plane = (size_t)ncol;
-    double xc = __ldg(x + col), xdn = 0.0, ddn = 0.0;
-    for (int k = 0; k < nz; ++k) {
-        const size_t o = (size_t)k * plane;
-        const double xup = (k + 1 < nz) ? __ldg(x + o + plane + col) : 0.0;
-        double v = __ldg(V.h + o + col) * xc;
-        v = fma(__ldg(V.e + o + col), xc - __ldg(x + o + c.ie), v);
-        v = fma(__ldg(V.w + o + c.iw), xc - __ldg(x + o + c.iw), v);
-        if (c.hasN) v = fma(__ldg(V.n + o + col), xc - __ldg(x + o + col + nlon), v);
-        if (c.hasS) v = fma(__ldg(V.s + o + col - nlon), xc - __ldg(x + o + col - nlon), v);
-        if (k + 1 < nz) v = fma(__ldg(V.u + o + col), xc - xup, v);
-        if (k > 0) v = fma(ddn, xc - xdn, v);
-        y[o + col] = MODE ? __ldg(b + o + col) - v : v;
-        ddn = __ldg(V.d + o + col);  // coupling of the row above back to this layer
-        xdn = xc;
-        xc = xup;
+    StLoads st[kStDepth];
+#pragma unroll
+    for (int q = 0; q < kStDepth; ++q)
+        if (q < nz) st_load<MODE>(st[q], V, b, x, (size_t)q * plane, col, c, nlon);
+    double xdn = 0.0, ddn = 0.0;
+    for (int k0 = 0; k0 < nz; k0 += kStDepth) {
+#pragma unroll
+        for (int q = 0; q < kStDepth; ++q) {
+            const int k = k0 + q;
+            if (k < nz) {
+                const StLoads &L = st[q];
+                const double xc = L.xc;
+                double v = L.h * xc;
+                v = fma(L.e, xc - L.xe, v);
+                v = fma(L.w, xc - L.xw, v);
+                if (c.hasN) v = fma(L.n, xc - L.xn, v);
+                if (c.hasS) v = fma(L.s, xc - L.xs, v);
+                if (k + 1 < nz) v = fma(L.u, xc - st[(q + 1) % kStDepth].xc, v);
+                if (k > 0) v = fma(ddn, xc - xdn, v);
+                y[(size_t)k * plane + col] = MODE ? L.b - v : v;
+                ddn = L.d;  // coupling of the row above back to this layer
+                xdn = xc;
+                if (k + kStDepth < nz)
+                    st_load<MODE>(st[q], V, b, x, (size_t)(k + kStDepth) * plane, col, c, nlon);
+            }
+        }
     }
 }
 
@@ -96,41 +134,124 @@ k_ns_presmooth_resid(NsView V, const double *__restrict__ b, const double *__res
 // One sweep of Eq. (1) on a column: forward y_k = (v_k + l_k y_{k-1}) / p_k
 // with l_k = d[k-1] (the row's coupling to the layer below) and v = b plus the
 // horizontal couplings of u_in; backward x_k = x_{k+1} + (y_k - (q_k/p_k)
-// x_{k+1}); u_out = (1 - omega) u_in + omega x.  No block barrier: a thread
-// past the last column returns at once.
-template <bool ZERO>
+// x_{k+1}); u_out = (1 - omega) u_in + omega x.  With a guess, register
+// pipelines of kFwdDepth layers forward and kBackDepth backward (3.61 -> 2.53
+// ms at 1536x1152x70).  The forward values wait in the thread's own column
+// of u_out, which the backward pass overwrites (the reads hit L2): without a
+// shared-memory buffer the block count is no longer capped at 6 per SM
+// (1536x1152x70: 2.53 -> 2.33 ms with a guess, 1.60 -> 1.18 ms from zero).
+// No block barrier: a thread past the last column returns at once.
+constexpr int kFwdDepth = 3;
+constexpr int kBackDepth = 4;
+
+struct SmLoads {
+    double b, e, w, n, s, ue, uw, un, us, m, d;
+};
+
+__device__ __forceinline__ void sm_load(SmLoads &L, const NsView &V, const double *__restrict__ b,
+                                        const double *__restrict__ uin, size_t o, int col,
+                                        const Col &c, int nlon)
+{
+    L.b = __ldg(b + o + col);
+    L.m = __ldg(V.m + o + col);
+    L.d = __ldg(V.d + o + col);
+    L.e = __ldg(V.e + o + col);
+    L.w = __ldg(V.w + o + c.iw);
+    L.ue = __ldg(uin + o + c.ie);
+    L.uw = __ldg(uin + o + c.iw);
+    L.n = c.hasN ? __ldg(V.n + o + col) : 0.0;
+    L.un = c.hasN ? __ldg(uin + o + col + nlon) : 0.0;
+    L.s = c.hasS ? __ldg(V.s + o + col - nlon) : 0.0;
+    L.us = c.hasS ? __ldg(uin + o + col - nlon) : 0.0;
+}
+
+// The sweep from zero (3 loads per layer) as a plain walk: with the forward
+// values in shared memory it ran 1.59 ms at 1536x1152x70 against 1.82-1.94
+// ms with 4-12 layers of loads in flight.
+__global__ void __launch_bounds__(kNsSmoothBlock)
+k_ns_smooth0(NsView V, const double *__restrict__ b, double *__restrict__ uout, double omega)
+{
+    const int ncol = V.nlon * V.nlat, nz = V.nz;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol) return;
+    const size_t plane = (size_t)ncol;
+    double yprev = 0.0, ldn = 0.0;
+    for (int k = 0; k < nz; ++k) {
+        const size_t o = (size_t)k * plane + col;
+        const double y = fma(ldn, yprev, __ldg(b + o)) * __ldg(V.m + o);
+        uout[o] = y;  // forward value, overwritten on the way back
+        yprev = y;
+        ldn = __ldg(V.d + o);
+    }
+    double xk = yprev;
+    for (int k = nz - 1; k >= 0; --k) {
+        const size_t o = (size_t)k * plane + col;
+        if (k < nz - 1) xk = xk + fma(-__ldg(V.dq + o), xk, uout[o]);
+        uout[o] = omega * xk;
+    }
+}
+
 __global__ void __launch_bounds__(kNsSmoothBlock)
 k_ns_smooth(NsView V, const double *__restrict__ b, const double *__restrict__ uin,
             double *__restrict__ uout, double omega)
 {
-    extern __shared__ double ns_ys[];
     const int nlon = V.nlon, nlat = V.nlat, nz = V.nz, ncol = nlon * nlat;
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= ncol) return;
-    const int bd = blockDim.x, tid = threadIdx.x;
     const Col c = col_of(col, nlon, nlat);
     const size_t plane = (size_t)ncol;
+    SmLoads st[kFwdDepth];
+#pragma unroll
+    for (int q = 0; q < kFwdDepth; ++q)
+        if (q < nz) sm_load(st[q], V, b, uin, (size_t)q * plane, col, c, nlon);
     double yprev = 0.0, ldn = 0.0;
-    for (int k = 0; k < nz; ++k) {
-        const size_t o = (size_t)k * plane;
-        double v = __ldg(b + o + col);
-        if (!ZERO) {
-            v = fma(__ldg(V.e + o + col), __ldg(uin + o + c.ie), v);
-            v = fma(__ldg(V.w + o + c.iw), __ldg(uin + o + c.iw), v);
-            if (c.hasN) v = fma(__ldg(V.n + o + col), __ldg(uin + o + col + nlon), v);
-            if (c.hasS) v = fma(__ldg(V.s + o + col - nlon), __ldg(uin + o + col - nlon), v);
+    for (int k0 = 0; k0 < nz; k0 += kFwdDepth) {
+#pragma unroll
+        for (int q = 0; q < kFwdDepth; ++q) {
+            const int k = k0 + q;
+            if (k < nz) {
+                const SmLoads &L = st[q];
+                double v = L.b;
+                v = fma(L.e, L.ue, v);
+                v = fma(L.w, L.uw, v);
+                v = fma(L.n, L.un, v);
+                v = fma(L.s, L.us, v);
+                const double y = fma(ldn, yprev, v) * L.m;
+                uout[(size_t)k * plane + col] = y;  // forward value
+                yprev = y;
+                ldn = L.d;
+                if (k + kFwdDepth < nz)
+                    sm_load(st[q], V, b, uin, (size_t)(k + kFwdDepth) * plane, col, c, nlon);
+            }
         }
-        const double y = fma(ldn, yprev, v) * __ldg(V.m + o + col);
-        ns_ys[(size_t)k * bd + tid] = y;
-        yprev = y;
-        ldn = __ldg(V.d + o + col);
     }
     const double om1 = 1.0 - omega;
     double xk = yprev;
-    for (int k = nz - 1; k >= 0; --k) {
-        const size_t o = (size_t)k * plane + col;
-        if (k < nz - 1) xk = xk + fma(-__ldg(V.dq + o), xk, ns_ys[(size_t)k * bd + tid]);
-        uout[o] = ZERO ? omega * xk : fma(om1, __ldg(uin + o), omega * xk);
+    double dqp[kBackDepth], up[kBackDepth];
+#pragma unroll
+    for (int q = 0; q < kBackDepth; ++q) {
+        const int k = nz - 1 - q;
+        if (k >= 0) {
+            dqp[q] = __ldg(V.dq + (size_t)k * plane + col);
+            up[q] = __ldg(uin + (size_t)k * plane + col);
+        }
+    }
+    for (int k0 = nz - 1; k0 >= 0; k0 -= kBackDepth) {
+#pragma unroll
+        for (int q = 0; q < kBackDepth; ++q) {
+            const int k = k0 - q;
+            if (k >= 0) {
+                const size_t o = (size_t)k * plane + col;
+                if (k < nz - 1) xk = xk + fma(-dqp[q], xk, uout[o]);
+                uout[o] = fma(om1, up[q], omega * xk);
+                const int kn = k - kBackDepth;
+                if (kn >= 0) {
+                    const size_t on = (size_t)kn * plane + col;
+                    dqp[q] = __ldg(V.dq + on);
+                    up[q] = __ldg(uin + on);
+                }
+            }
+        }
     }
 }
 
@@ -309,18 +430,6 @@ unsigned cell_blocks(size_t n) { return (unsigned)((n + kNsCellBlock - 1) / kNsC
 
 }  // namespace
 
-size_t ns_smooth_smem_bytes(int nz) { return (size_t)nz * kNsSmoothBlock * sizeof(double); }
-
-cudaError_t ns_prepare()
-{
-    const int bytes = (int)ns_smooth_smem_bytes(kMaxLayers);
-    cudaError_t e = cudaFuncSetAttribute(k_ns_smooth<true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_ns_smooth<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                bytes);
-}
-
 cudaError_t launch_ns_stencil(const NsView &V, int mode, const double *b, const double *x,
                               double *y, cudaStream_t s)
 {
@@ -341,12 +450,11 @@ cudaError_t launch_ns_presmooth_resid(const NsView &V, const double *b, const do
 cudaError_t launch_ns_smooth(const NsView &V, const double *b, const double *u_in,
                              double *u_out, double omega, cudaStream_t s)
 {
-    const size_t smem = ns_smooth_smem_bytes(V.nz);
     const int grid = col_blocks(V, kNsSmoothBlock);
     if (u_in)
-        k_ns_smooth<false><<<grid, kNsSmoothBlock, smem, s>>>(V, b, u_in, u_out, omega);
+        k_ns_smooth<<<grid, kNsSmoothBlock, 0, s>>>(V, b, u_in, u_out, omega);
     else
-        k_ns_smooth<true><<<grid, kNsSmoothBlock, smem, s>>>(V, b, nullptr, u_out, omega);
+        k_ns_smooth0<<<grid, kNsSmoothBlock, 0, s>>>(V, b, u_out, omega);
     return cudaGetLastError();
 }
 

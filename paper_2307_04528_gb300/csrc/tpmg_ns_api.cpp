@@ -176,15 +176,6 @@ int ns_setup(mg_ns_handle *H, const mg_ns_coeffs *co, void *ws, size_t ws_bytes,
     if (ws_bytes < need)
         return fail(MG_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, need);
     ns_carve(H, ws);
-    CU(ns_prepare());
-    {
-        int dev = 0, lim = 0;
-        CU(cudaGetDevice(&dev));
-        CU(cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        if (ns_smooth_smem_bytes(H->grid.nz) > (size_t)lim)
-            return fail(MG_ERR_ARG, "nz = %d needs more shared memory per block than the device "
-                                    "has", H->grid.nz);
-    }
     NsLevel &f = H->lev[0];
     const size_t bytes0 = f.n * sizeof(double);
     const double *src[7] = {co->h, co->tx, co->ty, co->tz, co->txr, co->tyr, co->tzr};
