@@ -47,7 +47,7 @@ typedef enum {
     MG_ERR_NONFINITE = 3,      /* NaN/Inf met in a right-hand side or residual */
     MG_ERR_NOT_CONVERGED = 4,  /* maxit reached before the tolerance */
     MG_ERR_DIVERGED = 5,       /* residual grew beyond 1e3 x its start */
-    MG_ERR_TIMEOUT = 6,        /* reserved: a bounded device wait gave up */
+    MG_ERR_TIMEOUT = 6,        /* a bounded device wait (TMA-staged kernel) gave up */
     MG_ERR_CUDA = 7,           /* a CUDA runtime call failed */
     MG_ERR_WORKSPACE = 8       /* workspace too small or misaligned */
 } mg_status;
