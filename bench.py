@@ -880,8 +880,9 @@ def ns_measure(steps):
     """The nonsymmetric operator (the transport-augmented 1536 x 1152 x 70
     system, pe 0.3): FP64 BiCGStab preconditioned by the V-cycle to 1e-10 for
     H and for H^T (the adjoint solve of a differentiable nonsymmetric solve),
-    beside the same method on the symmetric operator without the transport,
-    and the event times of the nonsymmetric fine-level kernels."""
+    the same with FP32 multigrid inside FP64 refinement, beside FP64
+    BiCGStab on the symmetric operator without the transport, and the event
+    times of the nonsymmetric fine-level kernels."""
     import torch
 
     from paper_2307_04528_gb300 import _lib as L
@@ -906,9 +907,10 @@ def ns_measure(steps):
 
     b = d(P["b"])
     H = NSHandle(*(d(P[k]) for k in ("h", "tx", "ty", "tz", "txr", "tyr", "tzr")),
-                 method=L.MG_METHOD_BICGSTAB)
+                 method=L.MG_METHOD_BICGSTAB, mixed=1)
     out = {"metric": "ms to 1e-10 rel residual, nonsymmetric 1536x1152x70 (transport pe 0.3), "
-                     "FP64 BiCGStab + V-cycle: H and H^T", "unit": "ms", "n_gpus": 1,
+                     "FP64 BiCGStab + V-cycle: H and H^T (mixed_*: FP32 multigrid in FP64 "
+                     "refinement)", "unit": "ms", "n_gpus": 1,
            "higher_is_better": False, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "latlon_1536x1152x70_transport", "unknowns": int(b.numel()),
                       "tol": TOL, "levels": H.num_levels}}
@@ -921,6 +923,15 @@ def ns_measure(steps):
         out["transpose" if tr else "forward"] = {
             "ms": ms, "status": info["status"], "iterations": info["iterations"],
             "rel_res": info["rel_res"]}
+    # FP32 multigrid (BiCGStab + V-cycle) inside FP64 refinement, H and H^T
+    for tr in (False, True):
+        def solve_mixed():
+            x.zero_()
+            return H.solve_mixed(b, x, tol=TOL, transpose=tr, raise_on_error=False)
+        ms, (_, info) = timed(solve_mixed, steps)
+        out["mixed_transpose" if tr else "mixed_forward"] = {
+            "ms": ms, "status": info["status"], "refinement_steps": info["iterations"],
+            "fp32_iterations": info["inner_iterations"], "rel_res": info["rel_res"]}
     out["value"] = out["forward"]["ms"]
     gen = torch.Generator(device="cuda").manual_seed(0)
     u = torch.randn(b.shape, generator=gen, device="cuda", dtype=torch.float64)

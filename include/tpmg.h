@@ -358,10 +358,11 @@ int mg_batch_solve(mg_batch *b, const double *const *bs, double *const *xs, doub
  * H's swapped, its masses the sums of the fine column sums).  A call with
  * transpose = 1 works on H^T's hierarchy; its sweeps solve the transposed
  * column systems.
- * FP64 throughout.  params: method MG_METHOD_STATIONARY or
+ * FP64, and with params->mixed = 1 also an FP32 copy of both hierarchies
+ * for mg_ns_solve_mixed.  params: method MG_METHOD_STATIONARY or
  * MG_METHOD_BICGSTAB (V-cycle-preconditioned; CG and the line-relaxed
- * BiCGStab are rejected), coarse_method MG_COARSE_JACOBI, mixed 0,
- * levels >= 0; the other fields as for mg_setup (MG_ERR_ARG otherwise). */
+ * BiCGStab are rejected), coarse_method MG_COARSE_JACOBI, levels >= 0; the
+ * other fields as for mg_setup (MG_ERR_ARG otherwise). */
 typedef struct mg_ns_handle mg_ns_handle;
 
 typedef struct {
@@ -396,6 +397,27 @@ int mg_ns_vcycle(mg_ns_handle *h, int transpose, const double *r, double *e, voi
  * initial guess, out = solution.  Returns as mg_solve. */
 int mg_ns_solve(mg_ns_handle *h, int transpose, const double *b, double *x, double tol,
                 mg_stats *stats, void *stream);
+
+/* The same solves with FP32 multigrid inside FP64 iterative refinement
+ * (Section 1's single-precision solves, as mg_solve_mixed): FP64 residual
+ * b - A x, norms and update; the configured method (stationary or BiCGStab
+ * with the V-cycle) in FP32 on the FP32 copy of H's or H^T's hierarchy
+ * (params->mixed = 1 at setup, else MG_ERR_ARG; its arrays are the FP64 ones
+ * scaled by mg_ns_fp32_scale) for at most params->inner_maxit iterations per
+ * refinement step.  x: in = initial guess, out = solution.  Returns as
+ * mg_solve; stats->inner_iterations counts the FP32 iterations. */
+int mg_ns_solve_mixed(mg_ns_handle *h, int transpose, const double *b, double *x, double tol,
+                      mg_stats *stats, void *stream);
+
+/* e = V r of H or H^T in either precision: prec MG_PREC_FP64 (as
+ * mg_ns_vcycle) or MG_PREC_FP32 (the FP32 hierarchy; e approximates
+ * (c A)^{-1} r, c = mg_ns_fp32_scale).  r, e: distinct device fields of that
+ * precision; calls on one handle must not overlap. */
+int mg_ns_vcycle_prec(mg_ns_handle *h, int transpose, int prec, const void *r, void *e,
+                      void *stream);
+
+/* The power of two the FP32 arrays are scaled by (0 without them). */
+double mg_ns_fp32_scale(const mg_ns_handle *h);
 
 /* Gradient of a loss L(x) through H x = b with respect to the seven arrays,
  * given x and lambda = H^{-T} dL/dx (mg_ns_solve with transpose = 1):

@@ -126,6 +126,9 @@ def load() -> ctypes.CDLL:
         "mg_ns_apply": (I, [H, I, P, P, P]),
         "mg_ns_vcycle": (I, [H, I, P, P, P]),
         "mg_ns_solve": (I, [H, I, P, P, D, ctypes.POINTER(mg_stats), P]),
+        "mg_ns_solve_mixed": (I, [H, I, P, P, D, ctypes.POINTER(mg_stats), P]),
+        "mg_ns_vcycle_prec": (I, [H, I, I, P, P, P]),
+        "mg_ns_fp32_scale": (D, [H]),
         "mg_ns_coeff_grad": (I, [H, P, P, P, P, P, P, P, P, P, P]),
         "mg_ns_num_levels": (I, [H]),
         "mg_ns_level_shape": (I, [H, I, ctypes.POINTER(I), ctypes.POINTER(I),

@@ -353,37 +353,42 @@ bool coarse_sh_fits(int ncol, int nz, size_t value_bytes);
 // (e, n, u, read at the cell) and the coupling of the row beyond the face
 // back to the cell (w, s, d, read at the west / south / lower neighbour's
 // face index).  H: (h, tx, ty, tz, txr, tyr, tzr); H^T: (h^T, txr, tyr,
-// tzr, tx, ty, tz).  m, dq: the view's column factors 1/p and q/p.
+// tzr, tx, ty, tz).  m, dq: the view's column factors 1/p and q/p.  FP32
+// views hold the FP64 arrays scaled by one power of two (m by its inverse).
+template <typename T>
 struct NsView {
     int nlon, nlat, nz;
-    const double *h, *e, *n, *u, *w, *s, *d;
-    const double *m, *dq;
+    const T *h, *e, *n, *u, *w, *s, *d;
+    const T *m, *dq;
 };
 
 // y = A x (mode 0) or b - A x (mode 1) in the directed flux form.
-cudaError_t launch_ns_stencil(const NsView &V, int mode, const double *b, const double *x,
-                              double *y, cudaStream_t s);
+template <typename T>
+cudaError_t launch_ns_stencil(const NsView<T> &V, int mode, const T *b, const T *x, T *y,
+                              cudaStream_t s);
 // r = (1 - omega) b plus the four horizontal couplings of u (the residual
 // after one sweep from zero, u = omega A_z^{-1} b).
-cudaError_t launch_ns_presmooth_resid(const NsView &V, const double *b, const double *u,
-                                      double omega, double *r, cudaStream_t s);
+template <typename T>
+cudaError_t launch_ns_presmooth_resid(const NsView<T> &V, const T *b, const T *u, double omega,
+                                      T *r, cudaStream_t s);
 // One sweep of Eq. (1), u_out = (1 - omega) u_in + omega A_z^{-1}(b - dA u_in)
 // (u_in == nullptr: zero guess).
-cudaError_t launch_ns_smooth(const NsView &V, const double *b, const double *u_in,
-                             double *u_out, double omega, cudaStream_t s);
-// Column factors of a view.
-cudaError_t launch_ns_column_lu(const NsView &V, double *m, double *dq, cudaStream_t s);
+template <typename T>
+cudaError_t launch_ns_smooth(const NsView<T> &V, const T *b, const T *u_in, T *u_out,
+                             double omega, cudaStream_t s);
+// Column factors of a view (FP64).
+cudaError_t launch_ns_column_lu(const NsView<double> &V, double *m, double *dq, cudaStream_t s);
 // h^T = h + sum over the six faces of (row coupling - column coupling) of H
 // (the forward view).
-cudaError_t launch_ns_colmass(const NsView &V, double *hT, cudaStream_t s);
+cudaError_t launch_ns_colmass(const NsView<double> &V, double *hT, cudaStream_t s);
 // Coarse arrays of the next level from a fine view (R10 for both couplings
 // of a face, masses summed); null outputs are skipped.
-cudaError_t launch_ns_coarsen(const NsView &F, const LinkDev &K, double sx, double *h,
+cudaError_t launch_ns_coarsen(const NsView<double> &F, const LinkDev &K, double sx, double *h,
                               double *e, double *n, double *u, double *w, double *sv, double *d,
                               cudaStream_t s);
 // Validation of the fine arrays (bits as launch_validate) and of a mass
 // array (bit 8: h^T <= 0 or non-finite).
-cudaError_t launch_ns_validate(const NsView &V, int *flag, cudaStream_t s);
+cudaError_t launch_ns_validate(const NsView<double> &V, int *flag, cudaStream_t s);
 cudaError_t launch_ns_positive(const double *a, size_t n, int *flag, cudaStream_t s);
 // Gradient of the seven arrays (outputs may be null).
 cudaError_t launch_ns_coeff_grad(int nlon, int nlat, int nz, const double *lam, const double *x,

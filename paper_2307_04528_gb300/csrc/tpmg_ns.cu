@@ -47,14 +47,15 @@ __device__ __forceinline__ Col col_of(int col, int nlon, int nlat)
 // combined (a register pipeline, as the symmetric stencil's).
 constexpr int kStDepth = 2;
 
+template <typename T>
 struct StLoads {
-    double xc, h, e, w, n, s, u, d, xe, xw, xn, xs, b;
+    T xc, h, e, w, n, s, u, d, xe, xw, xn, xs, b;
 };
 
-template <int MODE>
-__device__ __forceinline__ void st_load(StLoads &L, const NsView &V, const double *__restrict__ b,
-                                        const double *__restrict__ x, size_t o, int col,
-                                        const Col &c, int nlon)
+template <typename T, int MODE>
+__device__ __forceinline__ void st_load(StLoads<T> &L, const NsView<T> &V, const T *__restrict__ b,
+                                        const T *__restrict__ x, size_t o, int col, const Col &c,
+                                        int nlon)
 {
     L.xc = __ldg(x + o + col);
     L.h = __ldg(V.h + o + col);
@@ -64,36 +65,35 @@ __device__ __forceinline__ void st_load(StLoads &L, const NsView &V, const doubl
     L.d = __ldg(V.d + o + col);
     L.xe = __ldg(x + o + c.ie);
     L.xw = __ldg(x + o + c.iw);
-    L.n = c.hasN ? __ldg(V.n + o + col) : 0.0;
-    L.xn = c.hasN ? __ldg(x + o + col + nlon) : 0.0;
-    L.s = c.hasS ? __ldg(V.s + o + col - nlon) : 0.0;
-    L.xs = c.hasS ? __ldg(x + o + col - nlon) : 0.0;
+    L.n = c.hasN ? __ldg(V.n + o + col) : T(0);
+    L.xn = c.hasN ? __ldg(x + o + col + nlon) : T(0);
+    L.s = c.hasS ? __ldg(V.s + o + col - nlon) : T(0);
+    L.xs = c.hasS ? __ldg(x + o + col - nlon) : T(0);
     if (MODE) L.b = __ldg(b + o + col);
 }
 
-template <int MODE>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kBlock)
-k_ns_stencil(NsView V, const double *__restrict__ b, const double *__restrict__ x,
-             double *__restrict__ y)
+k_ns_stencil(NsView<T> V, const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ y)
 {
     const int nlon = V.nlon, nlat = V.nlat, nz = V.nz, ncol = nlon * nlat;
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= ncol) return;
     const Col c = col_of(col, nlon, nlat);
     const size_t plane = (size_t)ncol;
-    StLoads st[kStDepth];
+    StLoads<T> st[kStDepth];
 #pragma unroll
     for (int q = 0; q < kStDepth; ++q)
-        if (q < nz) st_load<MODE>(st[q], V, b, x, (size_t)q * plane, col, c, nlon);
-    double xdn = 0.0, ddn = 0.0;
+        if (q < nz) st_load<T, MODE>(st[q], V, b, x, (size_t)q * plane, col, c, nlon);
+    T xdn = 0, ddn = 0;
     for (int k0 = 0; k0 < nz; k0 += kStDepth) {
 #pragma unroll
         for (int q = 0; q < kStDepth; ++q) {
             const int k = k0 + q;
             if (k < nz) {
-                const StLoads &L = st[q];
-                const double xc = L.xc;
-                double v = L.h * xc;
+                const StLoads<T> &L = st[q];
+                const T xc = L.xc;
+                T v = L.h * xc;
                 v = fma(L.e, xc - L.xe, v);
                 v = fma(L.w, xc - L.xw, v);
                 if (c.hasN) v = fma(L.n, xc - L.xn, v);
@@ -104,16 +104,17 @@ k_ns_stencil(NsView V, const double *__restrict__ b, const double *__restrict__ 
                 ddn = L.d;  // coupling of the row above back to this layer
                 xdn = xc;
                 if (k + kStDepth < nz)
-                    st_load<MODE>(st[q], V, b, x, (size_t)(k + kStDepth) * plane, col, c, nlon);
+                    st_load<T, MODE>(st[q], V, b, x, (size_t)(k + kStDepth) * plane, col, c, nlon);
             }
         }
     }
 }
 
 // r = (1 - omega) b + e u_E + w[W] u_W + n u_N + s[S] u_S
+template <typename T>
 __global__ void __launch_bounds__(kBlock)
-k_ns_presmooth_resid(NsView V, const double *__restrict__ b, const double *__restrict__ u,
-                     double om1, double *__restrict__ r)
+k_ns_presmooth_resid(NsView<T> V, const T *__restrict__ b, const T *__restrict__ u, T om1,
+                     T *__restrict__ r)
 {
     const int nlon = V.nlon, nlat = V.nlat, ncol = nlon * nlat;
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
@@ -122,7 +123,7 @@ k_ns_presmooth_resid(NsView V, const double *__restrict__ b, const double *__res
     const size_t plane = (size_t)ncol;
     for (int k = 0; k < V.nz; ++k) {
         const size_t o = (size_t)k * plane;
-        double v = om1 * __ldg(b + o + col);
+        T v = om1 * __ldg(b + o + col);
         v = fma(__ldg(V.e + o + col), __ldg(u + o + c.ie), v);
         v = fma(__ldg(V.w + o + c.iw), __ldg(u + o + c.iw), v);
         if (c.hasN) v = fma(__ldg(V.n + o + col), __ldg(u + o + col + nlon), v);
@@ -144,12 +145,14 @@ k_ns_presmooth_resid(NsView V, const double *__restrict__ b, const double *__res
 constexpr int kFwdDepth = 3;
 constexpr int kBackDepth = 4;
 
+template <typename T>
 struct SmLoads {
-    double b, e, w, n, s, ue, uw, un, us, m, d;
+    T b, e, w, n, s, ue, uw, un, us, m, d;
 };
 
-__device__ __forceinline__ void sm_load(SmLoads &L, const NsView &V, const double *__restrict__ b,
-                                        const double *__restrict__ uin, size_t o, int col,
+template <typename T>
+__device__ __forceinline__ void sm_load(SmLoads<T> &L, const NsView<T> &V, const T *__restrict__ b,
+                                        const T *__restrict__ uin, size_t o, int col,
                                         const Col &c, int nlon)
 {
     L.b = __ldg(b + o + col);
@@ -159,31 +162,32 @@ __device__ __forceinline__ void sm_load(SmLoads &L, const NsView &V, const doubl
     L.w = __ldg(V.w + o + c.iw);
     L.ue = __ldg(uin + o + c.ie);
     L.uw = __ldg(uin + o + c.iw);
-    L.n = c.hasN ? __ldg(V.n + o + col) : 0.0;
-    L.un = c.hasN ? __ldg(uin + o + col + nlon) : 0.0;
-    L.s = c.hasS ? __ldg(V.s + o + col - nlon) : 0.0;
-    L.us = c.hasS ? __ldg(uin + o + col - nlon) : 0.0;
+    L.n = c.hasN ? __ldg(V.n + o + col) : T(0);
+    L.un = c.hasN ? __ldg(uin + o + col + nlon) : T(0);
+    L.s = c.hasS ? __ldg(V.s + o + col - nlon) : T(0);
+    L.us = c.hasS ? __ldg(uin + o + col - nlon) : T(0);
 }
 
 // The sweep from zero (3 loads per layer) as a plain walk: with the forward
 // values in shared memory it ran 1.59 ms at 1536x1152x70 against 1.82-1.94
-// ms with 4-12 layers of loads in flight.
+// ms with 4-12 layers of loads in flight (FP64).
+template <typename T>
 __global__ void __launch_bounds__(kNsSmoothBlock)
-k_ns_smooth0(NsView V, const double *__restrict__ b, double *__restrict__ uout, double omega)
+k_ns_smooth0(NsView<T> V, const T *__restrict__ b, T *__restrict__ uout, T omega)
 {
     const int ncol = V.nlon * V.nlat, nz = V.nz;
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= ncol) return;
     const size_t plane = (size_t)ncol;
-    double yprev = 0.0, ldn = 0.0;
+    T yprev = 0, ldn = 0;
     for (int k = 0; k < nz; ++k) {
         const size_t o = (size_t)k * plane + col;
-        const double y = fma(ldn, yprev, __ldg(b + o)) * __ldg(V.m + o);
+        const T y = fma(ldn, yprev, __ldg(b + o)) * __ldg(V.m + o);
         uout[o] = y;  // forward value, overwritten on the way back
         yprev = y;
         ldn = __ldg(V.d + o);
     }
-    double xk = yprev;
+    T xk = yprev;
     for (int k = nz - 1; k >= 0; --k) {
         const size_t o = (size_t)k * plane + col;
         if (k < nz - 1) xk = xk + fma(-__ldg(V.dq + o), xk, uout[o]);
@@ -191,43 +195,44 @@ k_ns_smooth0(NsView V, const double *__restrict__ b, double *__restrict__ uout, 
     }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kNsSmoothBlock)
-k_ns_smooth(NsView V, const double *__restrict__ b, const double *__restrict__ uin,
-            double *__restrict__ uout, double omega)
+k_ns_smooth(NsView<T> V, const T *__restrict__ b, const T *__restrict__ uin, T *__restrict__ uout,
+            T omega)
 {
     const int nlon = V.nlon, nlat = V.nlat, nz = V.nz, ncol = nlon * nlat;
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= ncol) return;
     const Col c = col_of(col, nlon, nlat);
     const size_t plane = (size_t)ncol;
-    SmLoads st[kFwdDepth];
+    SmLoads<T> st[kFwdDepth];
 #pragma unroll
     for (int q = 0; q < kFwdDepth; ++q)
-        if (q < nz) sm_load(st[q], V, b, uin, (size_t)q * plane, col, c, nlon);
-    double yprev = 0.0, ldn = 0.0;
+        if (q < nz) sm_load<T>(st[q], V, b, uin, (size_t)q * plane, col, c, nlon);
+    T yprev = 0, ldn = 0;
     for (int k0 = 0; k0 < nz; k0 += kFwdDepth) {
 #pragma unroll
         for (int q = 0; q < kFwdDepth; ++q) {
             const int k = k0 + q;
             if (k < nz) {
-                const SmLoads &L = st[q];
-                double v = L.b;
+                const SmLoads<T> &L = st[q];
+                T v = L.b;
                 v = fma(L.e, L.ue, v);
                 v = fma(L.w, L.uw, v);
                 v = fma(L.n, L.un, v);
                 v = fma(L.s, L.us, v);
-                const double y = fma(ldn, yprev, v) * L.m;
+                const T y = fma(ldn, yprev, v) * L.m;
                 uout[(size_t)k * plane + col] = y;  // forward value
                 yprev = y;
                 ldn = L.d;
                 if (k + kFwdDepth < nz)
-                    sm_load(st[q], V, b, uin, (size_t)(k + kFwdDepth) * plane, col, c, nlon);
+                    sm_load<T>(st[q], V, b, uin, (size_t)(k + kFwdDepth) * plane, col, c, nlon);
             }
         }
     }
-    const double om1 = 1.0 - omega;
-    double xk = yprev;
-    double dqp[kBackDepth], up[kBackDepth];
+    const T om1 = T(1) - omega;
+    T xk = yprev;
+    T dqp[kBackDepth], up[kBackDepth];
 #pragma unroll
     for (int q = 0; q < kBackDepth; ++q) {
         const int k = nz - 1 - q;
@@ -258,7 +263,7 @@ k_ns_smooth(NsView V, const double *__restrict__ b, const double *__restrict__ u
 // Column factors: s = h + e + w[W] + n + s[S]; q_0 = s_0, q_k = s_k + l_k
 // q_{k-1} / p_{k-1} (l_k = d[k-1]), p_k = q_k + u_k; m = 1/p, dq = q/p.
 __global__ void __launch_bounds__(kBlock)
-k_ns_column_lu(NsView V, double *__restrict__ m, double *__restrict__ dq)
+k_ns_column_lu(NsView<double> V, double *__restrict__ m, double *__restrict__ dq)
 {
     const int nlon = V.nlon, nlat = V.nlat, ncol = nlon * nlat;
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
@@ -283,7 +288,7 @@ k_ns_column_lu(NsView V, double *__restrict__ m, double *__restrict__ dq)
 // h^T = h + (e - w) + (w[W] - e[W]) + (n - s) + (s[S] - n[S]) + (u - d) + (d[D] - u[D])
 // of the forward view (e, n, u = tx, ty, tz; w, s, d = txr, tyr, tzr).
 __global__ void __launch_bounds__(kNsCellBlock)
-k_ns_colmass(NsView V, double *__restrict__ hT)
+k_ns_colmass(NsView<double> V, double *__restrict__ hT)
 {
     const int nlon = V.nlon, nlat = V.nlat, ncol = nlon * nlat;
     const size_t n = (size_t)ncol * V.nz;
@@ -305,7 +310,7 @@ k_ns_colmass(NsView V, double *__restrict__ hT)
 // children, the east faces of the odd fine columns, the top child row's
 // north faces; lon faces x sx, lat faces x sy[J] (0 on the last row).
 __global__ void __launch_bounds__(kBlock)
-k_ns_coarsen(NsView F, LinkDev K, double sx, double *__restrict__ hc, double *__restrict__ ec,
+k_ns_coarsen(NsView<double> F, LinkDev K, double sx, double *__restrict__ hc, double *__restrict__ ec,
              double *__restrict__ nc_, double *__restrict__ uc, double *__restrict__ wc,
              double *__restrict__ sc, double *__restrict__ dc)
 {
@@ -357,7 +362,7 @@ __device__ __forceinline__ bool ok_coupling(double t) { return t >= 0.0 && isfin
 // bits: 1 h <= 0 or non-finite, 2 a coupling < 0 or non-finite, 4 a non-zero
 // pole or top face
 __global__ void __launch_bounds__(kNsCellBlock)
-k_ns_validate(NsView V, int *__restrict__ flag)
+k_ns_validate(NsView<double> V, int *__restrict__ flag)
 {
     const int ncol = V.nlon * V.nlat;
     const size_t n = (size_t)ncol * V.nz;
@@ -424,54 +429,72 @@ k_ns_coeff_grad(int nlon, int nlat, int nz, const double *__restrict__ lam,
     }
 }
 
-int col_blocks(const NsView &V, int block) { return (V.nlon * V.nlat + block - 1) / block; }
+template <typename T>
+int col_blocks(const NsView<T> &V, int block)
+{
+    return (V.nlon * V.nlat + block - 1) / block;
+}
 
 unsigned cell_blocks(size_t n) { return (unsigned)((n + kNsCellBlock - 1) / kNsCellBlock); }
 
 }  // namespace
 
-cudaError_t launch_ns_stencil(const NsView &V, int mode, const double *b, const double *x,
-                              double *y, cudaStream_t s)
+template <typename T>
+cudaError_t launch_ns_stencil(const NsView<T> &V, int mode, const T *b, const T *x, T *y,
+                              cudaStream_t s)
 {
     if (mode)
-        k_ns_stencil<1><<<col_blocks(V, kBlock), kBlock, 0, s>>>(V, b, x, y);
+        k_ns_stencil<T, 1><<<col_blocks(V, kBlock), kBlock, 0, s>>>(V, b, x, y);
     else
-        k_ns_stencil<0><<<col_blocks(V, kBlock), kBlock, 0, s>>>(V, b, x, y);
+        k_ns_stencil<T, 0><<<col_blocks(V, kBlock), kBlock, 0, s>>>(V, b, x, y);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ns_presmooth_resid(const NsView &V, const double *b, const double *u,
-                                      double omega, double *r, cudaStream_t s)
+template <typename T>
+cudaError_t launch_ns_presmooth_resid(const NsView<T> &V, const T *b, const T *u, double omega,
+                                      T *r, cudaStream_t s)
 {
-    k_ns_presmooth_resid<<<col_blocks(V, kBlock), kBlock, 0, s>>>(V, b, u, 1.0 - omega, r);
+    k_ns_presmooth_resid<T><<<col_blocks(V, kBlock), kBlock, 0, s>>>(V, b, u, T(1.0 - omega), r);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ns_smooth(const NsView &V, const double *b, const double *u_in,
-                             double *u_out, double omega, cudaStream_t s)
+template <typename T>
+cudaError_t launch_ns_smooth(const NsView<T> &V, const T *b, const T *u_in, T *u_out,
+                             double omega, cudaStream_t s)
 {
     const int grid = col_blocks(V, kNsSmoothBlock);
     if (u_in)
-        k_ns_smooth<<<grid, kNsSmoothBlock, 0, s>>>(V, b, u_in, u_out, omega);
+        k_ns_smooth<T><<<grid, kNsSmoothBlock, 0, s>>>(V, b, u_in, u_out, (T)omega);
     else
-        k_ns_smooth0<<<grid, kNsSmoothBlock, 0, s>>>(V, b, u_out, omega);
+        k_ns_smooth0<T><<<grid, kNsSmoothBlock, 0, s>>>(V, b, u_out, (T)omega);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ns_column_lu(const NsView &V, double *m, double *dq, cudaStream_t s)
+#define TPMG_NS_INSTANTIATE(T)                                                                \
+    template cudaError_t launch_ns_stencil<T>(const NsView<T> &, int, const T *, const T *, T *, \
+                                              cudaStream_t);                                  \
+    template cudaError_t launch_ns_presmooth_resid<T>(const NsView<T> &, const T *, const T *, \
+                                                      double, T *, cudaStream_t);             \
+    template cudaError_t launch_ns_smooth<T>(const NsView<T> &, const T *, const T *, T *,     \
+                                             double, cudaStream_t);
+TPMG_NS_INSTANTIATE(double)
+TPMG_NS_INSTANTIATE(float)
+#undef TPMG_NS_INSTANTIATE
+
+cudaError_t launch_ns_column_lu(const NsView<double> &V, double *m, double *dq, cudaStream_t s)
 {
     k_ns_column_lu<<<col_blocks(V, kBlock), kBlock, 0, s>>>(V, m, dq);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ns_colmass(const NsView &V, double *hT, cudaStream_t s)
+cudaError_t launch_ns_colmass(const NsView<double> &V, double *hT, cudaStream_t s)
 {
     const size_t n = (size_t)V.nlon * V.nlat * V.nz;
     k_ns_colmass<<<cell_blocks(n), kNsCellBlock, 0, s>>>(V, hT);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ns_coarsen(const NsView &F, const LinkDev &K, double sx, double *h,
+cudaError_t launch_ns_coarsen(const NsView<double> &F, const LinkDev &K, double sx, double *h,
                               double *e, double *n, double *u, double *w, double *sv, double *d,
                               cudaStream_t s)
 {
@@ -481,7 +504,7 @@ cudaError_t launch_ns_coarsen(const NsView &F, const LinkDev &K, double sx, doub
     return cudaGetLastError();
 }
 
-cudaError_t launch_ns_validate(const NsView &V, int *flag, cudaStream_t s)
+cudaError_t launch_ns_validate(const NsView<double> &V, int *flag, cudaStream_t s)
 {
     const size_t n = (size_t)V.nlon * V.nlat * V.nz;
     k_ns_validate<<<cell_blocks(n), kNsCellBlock, 0, s>>>(V, flag);

@@ -459,10 +459,18 @@ class NSHandle:
         L.check(self.lib.mg_ns_apply(self._h, int(transpose), _ptr(x), _ptr(y), _stream()))
         return y
 
-    def vcycle(self, r, transpose=False, e=None):
-        _field(r, torch.float64, self.shape, "r")
+    @property
+    def fp32_scale(self) -> float:
+        return float(self.lib.mg_ns_fp32_scale(self._h))
+
+    def vcycle(self, r, transpose=False, e=None, prec=L.MG_PREC_FP64):
+        """e = V r of H (or H^T); prec MG_PREC_FP32 runs the FP32 hierarchy
+        (scaled arrays, see fp32_scale) on float32 r."""
+        dt = torch.float64 if prec == L.MG_PREC_FP64 else torch.float32
+        _field(r, dt, self.shape, "r")
         e = torch.empty_like(r) if e is None else e
-        L.check(self.lib.mg_ns_vcycle(self._h, int(transpose), _ptr(r), _ptr(e), _stream()))
+        L.check(self.lib.mg_ns_vcycle_prec(self._h, int(transpose), prec, _ptr(r), _ptr(e),
+                                           _stream()))
         return e
 
     def level_smooth(self, level, b, u_in=None, transpose=False):
@@ -471,21 +479,31 @@ class NSHandle:
                                             _ptr(out), _stream()))
         return out
 
-    def solve(self, b, x=None, tol=1e-10, transpose=False, history_cap=512,
-              raise_on_error=True):
-        """Solve H x = b (or H^T x = b); x is the initial guess, overwritten."""
+    def _solve(self, fn, b, x, tol, transpose, history_cap, raise_on):
         _field(b, torch.float64, self.shape, "b")
         x = torch.zeros_like(b) if x is None else x
         _field(x, torch.float64, self.shape, "x")
         hist = (ctypes.c_double * history_cap)()
         st = L.mg_stats(0, 0, 0.0, hist, history_cap, 0)
-        status = self.lib.mg_ns_solve(self._h, int(transpose), _ptr(b), _ptr(x), float(tol),
-                                      ctypes.byref(st), _stream())
-        if raise_on_error:
+        status = fn(self._h, int(transpose), _ptr(b), _ptr(x), float(tol), ctypes.byref(st),
+                    _stream())
+        if raise_on:
             L.check(status)
-        info = dict(status=status, iterations=st.iterations, rel_res=st.rel_res,
-                    history=[hist[i] for i in range(st.history_len)])
+        info = dict(status=status, iterations=st.iterations, inner_iterations=st.inner_iterations,
+                    rel_res=st.rel_res, history=[hist[i] for i in range(st.history_len)])
         return x, info
+
+    def solve(self, b, x=None, tol=1e-10, transpose=False, history_cap=512,
+              raise_on_error=True):
+        """Solve H x = b (or H^T x = b) in FP64; x is the initial guess, overwritten."""
+        return self._solve(self.lib.mg_ns_solve, b, x, tol, transpose, history_cap,
+                           raise_on_error)
+
+    def solve_mixed(self, b, x=None, tol=1e-10, transpose=False, history_cap=512,
+                    raise_on_error=True):
+        """The same solve with FP32 multigrid inside FP64 refinement (mixed=1)."""
+        return self._solve(self.lib.mg_ns_solve_mixed, b, x, tol, transpose, history_cap,
+                           raise_on_error)
 
     def coeff_grad(self, lam, x):
         """(gh, gtx, gty, gtz, gtxr, gtyr, gtzr) = -lam^T (dH/dtheta) x."""

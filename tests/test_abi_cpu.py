@@ -138,16 +138,20 @@ def _ns_bytes(lib, nlon, nlat, nz, **kw):
 def test_nonsymmetric_workspace_and_parameter_checks(lib):
     """The nonsymmetric hierarchy holds 15 level fields (seven arrays, the
     column sums, two factor pairs, three vectors) plus the right-hand side on
-    coarse levels and nine fine solver vectors; it takes the stationary
-    iteration or BiCGStab, the sweep coarse solve, FP64, a fixed depth."""
+    coarse levels and ten fine solver vectors, and with mixed = 1 their FP32
+    copies; it takes the stationary iteration or BiCGStab, the sweep coarse
+    solve and a fixed depth."""
     from paper_2307_04528_gb300 import _lib as L
     st, n = _ns_bytes(lib, 64, 32, 16)
-    assert st == 0 and n >= 64 * 32 * 16 * 8 * (15 + 9)
+    assert st == 0 and n >= 64 * 32 * 16 * 8 * (15 + 10)
     st2, n2 = _ns_bytes(lib, 64, 32, 16, method=L.MG_METHOD_STATIONARY)
     assert st2 == 0 and n2 == n
+    # mixed precision adds the FP32 copies: 12 arrays and 4 vectors per level, 10 fine vectors
+    st3, n3 = _ns_bytes(lib, 64, 32, 16, mixed=1)
+    assert st3 == 0 and n3 - n >= 64 * 32 * 16 * 4 * (16 + 10)
     for kw in ({"method": L.MG_METHOD_CG}, {"method": L.MG_METHOD_BICGSTAB_LINE},
-               {"coarse_method": L.MG_COARSE_PCG}, {"mixed": 1}, {"levels": -1},
-               {"omega": 2.5}):
+               {"coarse_method": L.MG_COARSE_PCG}, {"levels": -1}, {"omega": 2.5},
+               {"mixed": 1, "inner_maxit": 0}):
         st, _ = _ns_bytes(lib, 64, 32, 16, **kw)
         assert st == L.MG_ERR_ARG, kw
         assert lib.mg_last_error()

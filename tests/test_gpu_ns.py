@@ -224,3 +224,73 @@ def test_operational_size_properties():
         assert info["iterations"] <= 25, (tr, info)
         r = b - H.apply(xs, transpose=tr)
         assert float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(b)) <= 1.5e-10
+
+
+# ----------------------------------------------------------------- mixed precision
+def _ns_float(levels, scale):
+    """The oracle's levels in FP32: every array scaled by the handle's power of
+    two and rounded, as the library builds its FP32 hierarchy from FP64."""
+    out = []
+    for L in levels:
+        arrs = [np.ascontiguousarray(a * scale, dtype=np.float32) for a in L.arrays()]
+        out.append(N.NSLevel(*arrs, L.geo))
+    return out
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fp32_vcycles_of_h_and_its_transpose(shape):
+    """The FP32 V-cycle of H and of H^T element by element against the oracle
+    run in float32 on the same scaled levels (the symmetric FP32 cycle's
+    tolerances: 1e-4 max-norm, 2e-5 2-norm), and against the FP64 cycle / c."""
+    from paper_2307_04528_gb300 import _lib as L_
+    P = _ns_problem(*shape)
+    H = _handle(P, mixed=1)
+    L, T, p = _oracle(P)
+    c = H.fp32_scale
+    _, ex = np.frexp(max(float(np.max(np.abs(a))) for lv in L + T for a in lv.arrays()))
+    assert c == float(np.ldexp(1.0, -int(ex)))
+    r = np.random.default_rng(40).standard_normal(P["h"].shape).astype(np.float32)
+    for tr, levs in ((False, L), (True, T)):
+        got = host(H.vcycle(dev(r, torch.float32), transpose=tr, prec=L_.MG_PREC_FP32))
+        ref = N.vcycle(_ns_float(levs, c), r, p)
+        assert ref.dtype == np.float32
+        assert rel_inf(got, ref) <= 1e-4, tr
+        assert rel_2(got, ref) <= 2e-5, tr
+        e64 = host(H.vcycle(dev(r.astype(np.float64)), transpose=tr))
+        assert rel_2(got * c, e64) <= 1e-4, tr
+
+
+@pytest.mark.parametrize("method", ["stationary", "bicgstab"])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_mixed_solves_reach_the_fp64_solution(method, transpose):
+    """FP32 multigrid inside FP64 refinement reaches 1e-10 for H and H^T and
+    the oracle's FP64 solution."""
+    from paper_2307_04528_gb300 import _lib as L_
+    P = _ns_problem(96, 46, 12)
+    code = L_.MG_METHOD_STATIONARY if method == "stationary" else L_.MG_METHOD_BICGSTAB
+    H = _handle(P, method=code, mixed=1)
+    L, T, _ = _oracle(P)
+    x, info = H.solve_mixed(dev(P["b"]), tol=1e-10, transpose=transpose)
+    xo, _, st = N.solve(T if transpose else L, P["b"], 1e-11, O.MGParams(method=method))
+    assert st == N.OK and info["status"] == 0
+    assert info["rel_res"] <= 1e-10 and info["iterations"] <= 6
+    assert rel_2(host(x), xo) <= 1e-8
+    A = T[0] if transpose else L[0]
+    true = np.linalg.norm(N.residual(A, P["b"], host(x))) / np.linalg.norm(P["b"])
+    assert true <= 1.5e-10
+
+
+def test_mixed_operational_size():
+    """1536 x 1152 x 70 with transport: the mixed solves of H and H^T reach
+    1e-10 in a few refinement steps, and their solutions agree with the FP64
+    solves' to the tolerance's order."""
+    P = _ns_problem(1536, 1152, 70, seed=24, sigma=0.2)
+    H = _handle(P, mixed=1)
+    del P["fx"], P["fy"], P["fz"]
+    b = dev(P["b"])
+    for tr in (False, True):
+        xm, im = H.solve_mixed(b, tol=1e-10, transpose=tr)
+        assert im["status"] == 0 and im["rel_res"] <= 1e-10 and im["iterations"] <= 6, (tr, im)
+        x64, i64 = H.solve(b, tol=1e-10, transpose=tr)
+        diff = float(torch.linalg.vector_norm(xm - x64) / torch.linalg.vector_norm(x64))
+        assert diff <= 1e-7, (tr, diff)
