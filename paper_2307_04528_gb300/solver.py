@@ -262,14 +262,16 @@ class MGFloorWarning(RuntimeWarning):
     caller's floor_accept, and its solution was used."""
 
 
-def _solve_checked(handle, b, tol, floor_accept=None, **solve_kw):
+def _solve_checked(handle, b, tol, floor_accept=None, mixed=False, **solve_kw):
     """Solve and raise on any failure, except that a solve stopping on maxit
     with rel_res <= floor_accept is accepted with an MGFloorWarning.  The
     FP64 rounding floor of the residual (rounding of x times the vertical
     couplings: ~1e-12..1e-10 relative, higher for smooth right-hand sides
     such as an adjoint dL/dx) can sit above a tight tol while the solution
-    is accurate; floor_accept=None (the default) accepts nothing."""
-    x, info = handle.solve(b, tol=tol, raise_on_error=False, **solve_kw)
+    is accurate; floor_accept=None (the default) accepts nothing.  mixed: FP32
+    multigrid inside FP64 refinement (the handle needs mixed=1)."""
+    fn = handle.solve_mixed if mixed else handle.solve
+    x, info = fn(b, tol=tol, raise_on_error=False, **solve_kw)
     st = info["status"]
     if st == L.MG_OK:
         return x, info
@@ -367,14 +369,17 @@ class MGSolveFn(torch.autograd.Function):
     are kept in ctx.infos (forward, then adjoint)."""
 
     @staticmethod
-    def forward(ctx, b, h, tx, ty, tz, tol=1e-11, params=None, floor_accept=None):
+    def forward(ctx, b, h, tx, ty, tz, tol=1e-11, params=None, floor_accept=None, mixed=False):
         params = dict(params or {})
+        if mixed:
+            params["mixed"] = 1
         handle = MGHandle(tx.detach().contiguous(), ty.detach().contiguous(),
                           tz.detach().contiguous(), h.detach().contiguous(), **params)
-        x, info = _solve_checked(handle, b.detach().contiguous(), tol, floor_accept)
+        x, info = _solve_checked(handle, b.detach().contiguous(), tol, floor_accept, mixed)
         ctx.handle = handle
         ctx.tol = tol
         ctx.floor_accept = floor_accept
+        ctx.mixed = mixed
         ctx.infos = [info]
         ctx.save_for_backward(x)
         return x
@@ -382,15 +387,17 @@ class MGSolveFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
-        lam, info = _solve_checked(ctx.handle, gx.contiguous(), ctx.tol, ctx.floor_accept)
+        lam, info = _solve_checked(ctx.handle, gx.contiguous(), ctx.tol, ctx.floor_accept,
+                                   ctx.mixed)
         ctx.infos.append(info)
         gh, gtx, gty, gtz = ctx.handle.coeff_grad(lam, x)
-        return lam, gh, gtx, gty, gtz, None, None, None
+        return lam, gh, gtx, gty, gtz, None, None, None, None
 
 
-def mg_solve_fn(b, h, tx, ty, tz, tol=1e-11, floor_accept=None, **params):
-    """Differentiable solve (MGSolveFn); params: mg_params overrides."""
-    return MGSolveFn.apply(b, h, tx, ty, tz, tol, params, floor_accept)
+def mg_solve_fn(b, h, tx, ty, tz, tol=1e-11, floor_accept=None, mixed=False, **params):
+    """Differentiable solve (MGSolveFn); params: mg_params overrides; mixed:
+    both solves with FP32 multigrid inside FP64 refinement."""
+    return MGSolveFn.apply(b, h, tx, ty, tz, tol, params, floor_accept, mixed)
 
 
 _NS_ARRAYS = ("h", "tx", "ty", "tz", "txr", "tyr", "tzr")
@@ -521,11 +528,15 @@ class NSSolveFn(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, b, h, tx, ty, tz, txr, tyr, tzr, tol=1e-10, params=None,
-                floor_accept=None):
+                floor_accept=None, mixed=False):
         arrays = [t.detach().contiguous() for t in (h, tx, ty, tz, txr, tyr, tzr)]
-        handle = NSHandle(*arrays, **dict(params or {}))
-        x, info = _solve_checked(handle, b.detach().contiguous(), tol, floor_accept)
+        params = dict(params or {})
+        if mixed:
+            params["mixed"] = 1
+        handle = NSHandle(*arrays, **params)
+        x, info = _solve_checked(handle, b.detach().contiguous(), tol, floor_accept, mixed)
         ctx.handle, ctx.tol, ctx.floor_accept, ctx.infos = handle, tol, floor_accept, [info]
+        ctx.mixed = mixed
         ctx.save_for_backward(x)
         return x
 
@@ -533,12 +544,14 @@ class NSSolveFn(torch.autograd.Function):
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
         lam, info = _solve_checked(ctx.handle, gx.contiguous(), ctx.tol, ctx.floor_accept,
-                                   transpose=True)
+                                   ctx.mixed, transpose=True)
         ctx.infos.append(info)
         grads = ctx.handle.coeff_grad(lam, x)
-        return (lam, *grads, None, None, None)
+        return (lam, *grads, None, None, None, None)
 
 
-def ns_solve_fn(b, h, tx, ty, tz, txr, tyr, tzr, tol=1e-10, floor_accept=None, **params):
-    """Differentiable nonsymmetric solve (NSSolveFn); params: mg_params overrides."""
-    return NSSolveFn.apply(b, h, tx, ty, tz, txr, tyr, tzr, tol, params, floor_accept)
+def ns_solve_fn(b, h, tx, ty, tz, txr, tyr, tzr, tol=1e-10, floor_accept=None, mixed=False,
+                **params):
+    """Differentiable nonsymmetric solve (NSSolveFn); params: mg_params
+    overrides; mixed: both solves with FP32 multigrid inside FP64 refinement."""
+    return NSSolveFn.apply(b, h, tx, ty, tz, txr, tyr, tzr, tol, params, floor_accept, mixed)

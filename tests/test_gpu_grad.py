@@ -13,22 +13,25 @@ from test_oracle_pins import _dense_solve
 pytestmark = pytest.mark.gpu
 
 
-def _grads(P, W, tol=1e-12):
+def _grads(P, W, tol=1e-12, mixed=False):
     from paper_2307_04528_gb300.solver import mg_solve_fn
     b, h, tx, ty, tz = (dev(P[k]).requires_grad_(True) for k in ("b", "h", "tx", "ty", "tz"))
     # the adjoint's smooth right-hand side floors near 6e-11: accepted below 1e-8
-    x = mg_solve_fn(b, h, tx, ty, tz, tol=tol, floor_accept=1e-8)
+    x = mg_solve_fn(b, h, tx, ty, tz, tol=tol, floor_accept=1e-8, mixed=mixed)
     loss = 0.5 * torch.sum((dev(W) * x) ** 2)
     loss.backward()
     return x, {k: host(t.grad) for k, t in zip(("b", "h", "tx", "ty", "tz"), (b, h, tx, ty, tz))}
 
 
-def test_gradient_matches_dense_lu_8x4x4():
+@pytest.mark.parametrize("mixed", [False, True])
+def test_gradient_matches_dense_lu_8x4x4(mixed):
+    """FP64 solves, or both solves with FP32 multigrid inside FP64
+    refinement (mixed): the same gradient to the same bounds."""
     P = problem(8, 4, 4, sigma=0.1, seed=21)
     W = np.random.default_rng(22).uniform(0, 1, P["h"].shape)
     # the residual floor of this tiny grid is ~1e-11 (rounding of x times the
     # vertical couplings); the solution itself is far more accurate
-    x, g = _grads(P, W, tol=5e-11)
+    x, g = _grads(P, W, tol=5e-11, mixed=mixed)
     xd, _ = _dense_solve(P, P["b"])
     lam, _ = _dense_solve(P, W * W * xd)
     assert rel_2(host(x), xd) <= 1e-10

@@ -146,10 +146,12 @@ def test_coefficient_gradient_matches_the_oracle():
         assert rel_inf(host(g), w) <= 1e-15, name
 
 
-def test_differentiable_solve_against_dense_adjoint():
+@pytest.mark.parametrize("mixed", [False, True])
+def test_differentiable_solve_against_dense_adjoint(mixed):
     """ns_solve_fn's gradients (forward solve, adjoint solve on H^T's
-    hierarchy, the seven-array kernel) against the oracle's gradient formula
-    at the dense solutions x = H^{-1} b and lam = H^{-T} g."""
+    hierarchy, the seven-array kernel; FP64 or with FP32 multigrid inside
+    FP64 refinement) against the oracle's gradient formula at the dense
+    solutions x = H^{-1} b and lam = H^{-T} g."""
     from paper_2307_04528_gb300.solver import ns_solve_fn
     P = _ns_problem(16, 8, 4, seed=23)
     L, _, _ = _oracle(P, levels=2)
@@ -166,7 +168,8 @@ def test_differentiable_solve_against_dense_adjoint():
     want = dict(zip(NAMES, N.coeff_grad(L[0], lam, xs)))
     ts = {k: dev(P[k]).requires_grad_(True) for k in NAMES}
     b = dev(P["b"]).requires_grad_(True)
-    x = ns_solve_fn(b, *(ts[k] for k in NAMES), tol=1e-11, floor_accept=1e-9, levels=2)
+    x = ns_solve_fn(b, *(ts[k] for k in NAMES), tol=1e-11, floor_accept=1e-9, mixed=mixed,
+                    levels=2)
     assert rel_2(host(x), xs) <= 1e-9
     (x * dev(g)).sum().backward()
     assert rel_2(host(b.grad), lam) <= 1e-8
