@@ -658,6 +658,10 @@ PROBE_KERNELS = {
     "ns_smooth64": (0, "ns_smooth", 10),
     "ns_smooth64_zero": (0, "ns_smooth0", 5),
     "ns_vcycle64": (0, "ns_vcycle", None),
+    "ns_smooth32": (1, "ns_smooth", 10),
+    "ns_smooth32_zero": (1, "ns_smooth0", 5),
+    "ns_vcycle32": (1, "ns_vcycle", None),
+    "ns_solve_mixed": (1, "ns_solve_mixed", None),
     "ns_solve64": (0, "ns_solve", None),
     "ns_solve64_T": (0, "ns_solve_T", None),
 }
@@ -679,7 +683,7 @@ def run_kernel(args):
     if op.startswith("ns_"):
         from paper_2307_04528_gb300.solver import NSHandle
         P = make_ns_problem(nlon, nlat, nz, args.sigma, 3000)
-        H = NSHandle(*(d(P[k]) for k in ("h", "tx", "ty", "tz", "txr", "tyr", "tzr")))
+        H = NSHandle(*(d(P[k]) for k in ("h", "tx", "ty", "tz", "txr", "tyr", "tzr")), mixed=1)
     else:
         P = make_problem(nlon, nlat, nz, args.sigma, 3000)
         H = MGHandle(d(P["tx"]), d(P["ty"]), d(P["tz"]), d(P["h"]), mixed=1)
@@ -705,14 +709,17 @@ def run_kernel(args):
         if op in ("ns_apply", "ns_apply_T"):
             return H.apply(u, transpose=op.endswith("_T"))
         if op == "ns_smooth":
-            return H.level_smooth(0, b, u)
+            return H.level_smooth(0, b, u, prec=prec)
         if op == "ns_smooth0":
-            return H.level_smooth(0, b, None)
+            return H.level_smooth(0, b, None, prec=prec)
         if op == "ns_vcycle":
-            return H.vcycle(b)
+            return H.vcycle(b, prec=prec)
         if op in ("ns_solve", "ns_solve_T"):
             x64.zero_()
             return H.solve(b64, x64, tol=TOL, transpose=op.endswith("_T"))
+        if op == "ns_solve_mixed":
+            x64.zero_()
+            return H.solve_mixed(b64, x64, tol=TOL)
         if op == "smooth":
             return H.level_smooth(0, b, u, prec=prec)
         if op == "smooth_dot":

@@ -440,12 +440,13 @@ int mg_ns_level_coeffs(mg_ns_handle *h, int level, int transpose, double *h_out,
                        double *ty, double *tz, double *txr, double *tyr, double *tzr,
                        void *stream);
 
-/* One sweep of Eq. (1) on a level of H or H^T:
+/* One sweep of Eq. (1) on a level of H or H^T in FP64 or (prec
+ * MG_PREC_FP32, mixed handles) on the FP32 hierarchy:
  * u_out = (1 - omega) u_in + omega A_z^{-1} (b - dA u_in), u_in NULL = zero
- * guess.  Device FP64 fields of the level's shape; u_out distinct from
- * u_in and b. */
-int mg_ns_level_smooth(mg_ns_handle *h, int level, int transpose, const double *b,
-                       const double *u_in, double *u_out, void *stream);
+ * guess.  Device fields of that precision and the level's shape; u_out
+ * distinct from u_in and b. */
+int mg_ns_level_smooth(mg_ns_handle *h, int level, int transpose, int prec, const void *b,
+                       const void *u_in, void *u_out, void *stream);
 
 int mg_profile_enable(mg_handle *h, int on);
 int mg_profile_read(mg_handle *h, int kind, int level, int prec, int *launches, double *ms);

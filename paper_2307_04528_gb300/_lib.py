@@ -134,7 +134,7 @@ def load() -> ctypes.CDLL:
         "mg_ns_level_shape": (I, [H, I, ctypes.POINTER(I), ctypes.POINTER(I),
                                   ctypes.POINTER(I)]),
         "mg_ns_level_coeffs": (I, [H, I, I, P, P, P, P, P, P, P, P]),
-        "mg_ns_level_smooth": (I, [H, I, I, P, P, P, P]),
+        "mg_ns_level_smooth": (I, [H, I, I, I, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

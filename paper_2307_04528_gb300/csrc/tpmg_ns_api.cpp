@@ -750,13 +750,22 @@ extern "C" int mg_ns_level_coeffs(mg_ns_handle *H, int level, int transpose, dou
     return MG_OK;
 }
 
-extern "C" int mg_ns_level_smooth(mg_ns_handle *H, int level, int transpose, const double *b,
-                                  const double *u_in, double *u_out, void *stream)
+extern "C" int mg_ns_level_smooth(mg_ns_handle *H, int level, int transpose, int prec,
+                                  const void *b, const void *u_in, void *u_out, void *stream)
 {
     CHK(level_ok(H, level));
     if (!b || !u_out || u_out == u_in || u_out == b)
         return fail(MG_ERR_ARG, "null or aliased vectors");
-    NRUN(launch_ns_smooth<double>(view<double>(H->lev[level], transpose != 0), b, u_in, u_out,
-                                  H->p.omega, (cudaStream_t)stream));
+    const cudaStream_t s = (cudaStream_t)stream;
+    NsLevel &v = H->lev[level];
+    if (prec == MG_PREC_FP64) {
+        NRUN(launch_ns_smooth<double>(view<double>(v, transpose != 0), (const double *)b,
+                                      (const double *)u_in, (double *)u_out, H->p.omega, s));
+        return MG_OK;
+    }
+    if (prec != MG_PREC_FP32) return fail(MG_ERR_ARG, "prec %d unknown", prec);
+    if (!H->p.mixed) return fail(MG_ERR_ARG, "handle built without the FP32 hierarchy (mixed=0)");
+    NRUN(launch_ns_smooth<float>(view<float>(v, transpose != 0), (const float *)b,
+                                 (const float *)u_in, (float *)u_out, H->p.omega, s));
     return MG_OK;
 }

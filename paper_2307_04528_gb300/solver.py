@@ -480,10 +480,11 @@ class NSHandle:
                                            _stream()))
         return e
 
-    def level_smooth(self, level, b, u_in=None, transpose=False):
+    def level_smooth(self, level, b, u_in=None, transpose=False, prec=L.MG_PREC_FP64):
+        """One sweep of Eq. (1) on a level of H (or H^T); u_in None: zero guess."""
         out = torch.empty_like(b)
-        L.check(self.lib.mg_ns_level_smooth(self._h, level, int(transpose), _ptr(b), _ptr(u_in),
-                                            _ptr(out), _stream()))
+        L.check(self.lib.mg_ns_level_smooth(self._h, level, int(transpose), prec, _ptr(b),
+                                            _ptr(u_in), _ptr(out), _stream()))
         return out
 
     def _solve(self, fn, b, x, tol, transpose, history_cap, raise_on):

@@ -297,3 +297,23 @@ def test_mixed_operational_size():
         x64, i64 = H.solve(b, tol=1e-10, transpose=tr)
         diff = float(torch.linalg.vector_norm(xm - x64) / torch.linalg.vector_norm(x64))
         assert diff <= 1e-7, (tr, diff)
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+def test_fp32_sweeps_on_every_level(transpose):
+    """Every level's FP32 sweeps (from zero and with a guess) of H and H^T
+    against the oracle's float32 sweeps on the same scaled levels."""
+    from paper_2307_04528_gb300 import _lib as L_
+    P = _ns_problem(96, 46, 12)
+    H = _handle(P, mixed=1)
+    L, T, p = _oracle(P)
+    levs = _ns_float(T if transpose else L, H.fp32_scale)
+    rng = np.random.default_rng(41)
+    for l, lev in enumerate(levs):
+        b = rng.standard_normal(lev.shape).astype(np.float32)
+        u = rng.standard_normal(lev.shape).astype(np.float32)
+        f32 = lambda a: dev(a, torch.float32)
+        z = H.level_smooth(l, f32(b), None, transpose=transpose, prec=L_.MG_PREC_FP32)
+        assert rel_inf(host(z), N.smooth_from_zero(lev, b, p.omega)) <= 2e-5, (l, "zero")
+        s = H.level_smooth(l, f32(b), f32(u), transpose=transpose, prec=L_.MG_PREC_FP32)
+        assert rel_inf(host(s), N.smooth(lev, b, u, p.omega)) <= 2e-5, (l, "guess")
