@@ -317,3 +317,33 @@ def test_fp32_sweeps_on_every_level(transpose):
         assert rel_inf(host(z), N.smooth_from_zero(lev, b, p.omega)) <= 2e-5, (l, "zero")
         s = H.level_smooth(l, f32(b), f32(u), transpose=transpose, prec=L_.MG_PREC_FP32)
         assert rel_inf(host(s), N.smooth(lev, b, u, p.omega)) <= 2e-5, (l, "guess")
+
+
+@pytest.mark.parametrize("shape,params", [((32, 16, 192), {}), ((48, 24, 33), {}),
+                                          ((64, 32, 1), {}), ((16, 8, 5), {"levels": 1}),
+                                          ((4, 2, 3), {})],
+                         ids=["nz192", "nz33", "nz1", "one-level", "nlon4"])
+def test_edge_shapes(shape, params):
+    """The largest column (nz = 192), a layer count that is not a multiple
+    of the warp width, a single layer (no vertical couplings), a single-level
+    hierarchy (the coarse sweeps are the whole cycle) and the smallest grid:
+    both hierarchies, the V-cycles and the BiCGStab solves of H and H^T
+    against the oracle (nz = 192 and the 4 x 2 x 3 grid to 2e-8: their
+    residual floors, the rounding of x times the vertical couplings, are
+    ~6e-9 and ~3e-10)."""
+    P = _ns_problem(*shape, seed=50 + shape[2])
+    H = _handle(P, **params)
+    L, T, p = _oracle(P, **params)
+    assert H.num_levels == len(L)
+    for l in range(len(L)):
+        for tr, lev in ((False, L[l]), (True, T[l])):
+            for name, g, w in zip(NAMES, H.level_coeffs(l, transpose=tr), lev.arrays()):
+                assert rel_inf(host(g), w) <= 1e-15, (l, tr, name)
+    r = np.random.default_rng(51).standard_normal(P["h"].shape)
+    tol = 2e-8 if shape[2] == 192 or shape[0] == 4 else 1e-10
+    for tr, levs in ((False, L), (True, T)):
+        assert rel_inf(host(H.vcycle(dev(r), transpose=tr)), N.vcycle(levs, r, p)) <= 1e-11
+        x, info = H.solve(dev(P["b"]), tol=tol, transpose=tr)
+        xo, _, st = N.solve(levs, P["b"], tol / 10, O.MGParams(method="bicgstab", **params))
+        assert info["status"] == 0 and st in (N.OK, N.NOT_CONVERGED)
+        assert rel_2(host(x), xo) <= 100 * tol
