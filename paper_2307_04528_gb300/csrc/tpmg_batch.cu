@@ -326,6 +326,78 @@ __device__ __forceinline__ double bvec_chunk(T *__restrict__ a, T *__restrict__ 
     return OP == BV_MAXABS ? acc : (double)tacc;
 }
 
+// The FP32 chunk on 16-byte vectors (chunks are multiples of kBlock values;
+// lengths and bases checked by the caller): the same arithmetic per
+// element, four elements per load and store.
+template <int OP>
+__device__ __forceinline__ double bvec_chunk_f4(float *__restrict__ a, float *__restrict__ b,
+                                                const float *__restrict__ c,
+                                                const float *__restrict__ d, size_t c0, size_t c1,
+                                                float alpha, float beta)
+{
+    float4 *a4 = reinterpret_cast<float4 *>(a);
+    float4 *b4 = reinterpret_cast<float4 *>(b);
+    const float4 *c4 = reinterpret_cast<const float4 *>(c);
+    const float4 *d4 = reinterpret_cast<const float4 *>(d);
+    double acc = 0;
+    float tacc = 0;
+#pragma unroll 2
+    for (size_t i = c0 / 4 + threadIdx.x; i < c1 / 4; i += blockDim.x) {
+        if (OP == BV_DOT) {
+            const float4 x = a4[i], y = b4[i];
+            tacc = fmaf(x.x, y.x, tacc);
+            tacc = fmaf(x.y, y.y, tacc);
+            tacc = fmaf(x.z, y.z, tacc);
+            tacc = fmaf(x.w, y.w, tacc);
+        } else if (OP == BV_UPDATE) {
+            float4 x = a4[i], r = b4[i];
+            const float4 dv = c4[i], q = d4[i];
+            x.x = fmaf(alpha, dv.x, x.x);
+            x.y = fmaf(alpha, dv.y, x.y);
+            x.z = fmaf(alpha, dv.z, x.z);
+            x.w = fmaf(alpha, dv.w, x.w);
+            r.x = fmaf(-alpha, q.x, r.x);
+            r.y = fmaf(-alpha, q.y, r.y);
+            r.z = fmaf(-alpha, q.z, r.z);
+            r.w = fmaf(-alpha, q.w, r.w);
+            a4[i] = x;
+            b4[i] = r;
+            tacc = fmaf(r.x, r.x, tacc);
+            tacc = fmaf(r.y, r.y, tacc);
+            tacc = fmaf(r.z, r.z, tacc);
+            tacc = fmaf(r.w, r.w, tacc);
+        } else if (OP == BV_DIR) {
+            const float4 z = b4[i], dv = c4[i];
+            a4[i] = make_float4(fmaf(beta, dv.x, z.x), fmaf(beta, dv.y, z.y),
+                                fmaf(beta, dv.z, z.z), fmaf(beta, dv.w, z.w));
+        } else if (OP == BV_DIR0) {
+            a4[i] = b4[i];
+        } else if (OP == BV_ADD) {
+            float4 x = a4[i];
+            const float4 y = b4[i];
+            x.x += y.x;
+            x.y += y.y;
+            x.z += y.z;
+            x.w += y.w;
+            a4[i] = x;
+        } else {
+            const float4 x = a4[i];
+            acc = max_mag(acc, (double)x.x);  // NaN propagates
+            acc = max_mag(acc, (double)x.y);
+            acc = max_mag(acc, (double)x.z);
+            acc = max_mag(acc, (double)x.w);
+        }
+    }
+    return OP == BV_MAXABS ? acc : (double)tacc;
+}
+
+__device__ __forceinline__ bool f4_chunk(const void *a, const void *b, const void *c,
+                                         const void *d, size_t c0, size_t c1)
+{
+    return ((uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d) % 16 == 0 && c0 % 4 == 0 &&
+           c1 % 4 == 0;
+}
+
 template <typename T, int OP>
 __global__ void __launch_bounds__(kBlock)
 k_bvec(const BVec<T> *__restrict__ vs, const BItem *__restrict__ items, int nitems,
@@ -340,7 +412,14 @@ k_bvec(const BVec<T> *__restrict__ vs, const BItem *__restrict__ items, int nite
         const size_t c1 = c0 + v.chunk < v.n ? c0 + v.chunk : v.n;
         const T alpha = (OP == BV_UPDATE) ? (T)sc[v.sys].alpha : T(0);
         const T beta = (OP == BV_DIR) ? (T)sc[v.sys].beta : T(0);
-        const double acc = bvec_chunk<T, OP>(v.a, v.b, v.c, v.d, c0, c1, alpha, beta);
+        double acc;
+        if constexpr (sizeof(T) == 4) {
+            acc = f4_chunk(v.a, v.b, v.c, v.d, c0, c1)
+                      ? bvec_chunk_f4<OP>(v.a, v.b, v.c, v.d, c0, c1, alpha, beta)
+                      : bvec_chunk<T, OP>(v.a, v.b, v.c, v.d, c0, c1, alpha, beta);
+        } else {
+            acc = bvec_chunk<T, OP>(v.a, v.b, v.c, v.d, c0, c1, alpha, beta);
+        }
         if (OP == BV_DOT || OP == BV_UPDATE) block_store_at<0>(acc, partial, it);
         if (OP == BV_MAXABS) block_store_at<1>(acc, partial, it);
     }
@@ -369,6 +448,29 @@ __device__ __forceinline__ void bmix_chunk(double *__restrict__ x, const double 
                                            float *__restrict__ r32, const float *__restrict__ e32,
                                            size_t c0, size_t c1, double f)
 {
+    if (f4_chunk(x, r, r32, e32, c0, c1)) {  // four values per load and store
+#pragma unroll 2
+        for (size_t i = c0 / 4 + threadIdx.x; i < c1 / 4; i += blockDim.x) {
+            if (MODE == 0) {
+                const double2 a = reinterpret_cast<const double2 *>(r)[2 * i];
+                const double2 b = reinterpret_cast<const double2 *>(r)[2 * i + 1];
+                reinterpret_cast<float4 *>(r32)[i] =
+                    make_float4((float)(a.x * f), (float)(a.y * f), (float)(b.x * f),
+                                (float)(b.y * f));
+            } else {
+                const float4 e = reinterpret_cast<const float4 *>(e32)[i];
+                double2 a = reinterpret_cast<double2 *>(x)[2 * i];
+                double2 b = reinterpret_cast<double2 *>(x)[2 * i + 1];
+                a.x = fma(f, (double)e.x, a.x);
+                a.y = fma(f, (double)e.y, a.y);
+                b.x = fma(f, (double)e.z, b.x);
+                b.y = fma(f, (double)e.w, b.y);
+                reinterpret_cast<double2 *>(x)[2 * i] = a;
+                reinterpret_cast<double2 *>(x)[2 * i + 1] = b;
+            }
+        }
+        return;
+    }
 #pragma unroll 4
     for (size_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
         if (MODE == 0) r32[c] = (float)(r[c] * f);
