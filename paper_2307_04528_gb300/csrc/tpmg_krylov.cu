@@ -15,6 +15,131 @@
 
 namespace tpmg {
 
+// FP32 forms on 16-byte vectors (four elements per load and store, the same
+// arithmetic per element; partial sums grouped by vector) for lengths that
+// are multiples of 4 on 16-byte aligned vectors, as the conjugate-gradient
+// vector kernels.
+namespace {
+
+struct F4 {
+    float v[4];
+};
+
+__device__ __forceinline__ F4 ld4(const float *p, size_t i)
+{
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(p) + i);
+    return {{q.x, q.y, q.z, q.w}};
+}
+
+__device__ __forceinline__ F4 ld4w(const float *p, size_t i)  // a vector this kernel writes
+{
+    const float4 q = reinterpret_cast<const float4 *>(p)[i];
+    return {{q.x, q.y, q.z, q.w}};
+}
+
+__device__ __forceinline__ void st4(float *p, size_t i, const F4 &a)
+{
+    reinterpret_cast<float4 *>(p)[i] = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+}
+
+bool f4_ok(size_t n, const void *a, const void *b, const void *c = nullptr,
+           const void *d = nullptr, const void *e = nullptr, const void *f = nullptr,
+           const void *g = nullptr)
+{
+    return n % 4 == 0 && ((uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d |
+                          (uintptr_t)e | (uintptr_t)f | (uintptr_t)g) % 16 == 0;
+}
+
+#define TPMG_GRID_LOOP4(n4)                                                               \
+    _Pragma("unroll 2") for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;   \
+                             c < (n4); c += (size_t)gridDim.x * blockDim.x)
+
+template <bool FIRST>
+__global__ void __launch_bounds__(kBlock)
+k_bicg_dir_f4(float *__restrict__ p, const float *__restrict__ r, const float *__restrict__ v,
+              size_t n4, const BicgScalars *sc)
+{
+    const float beta = FIRST ? 0.f : (float)sc->beta, omega = FIRST ? 0.f : (float)sc->omega;
+    TPMG_GRID_LOOP4(n4)
+    {
+        const F4 rv = ld4(r, c);
+        if (FIRST) {
+            st4(p, c, rv);
+        } else {
+            const F4 vv = ld4(v, c);
+            F4 pv = ld4w(p, c);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pv.v[q] = fmaf(beta, fmaf(-omega, vv.v[q], pv.v[q]), rv.v[q]);
+            st4(p, c, pv);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_bicg_s_f4(float *__restrict__ sv, const float *__restrict__ r, const float *__restrict__ v,
+            size_t n4, const BicgScalars *sc)
+{
+    const float alpha = (float)sc->alpha;
+    TPMG_GRID_LOOP4(n4)
+    {
+        const F4 rv = ld4(r, c), vv = ld4(v, c);
+        F4 o;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o.v[q] = fmaf(-alpha, vv.v[q], rv.v[q]);
+        st4(sv, c, o);
+    }
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_dot2_f4(const float *__restrict__ t, const float *__restrict__ sv, size_t n4, double *pa,
+          double *pb)
+{
+    float a = 0, b = 0;
+    TPMG_GRID_LOOP4(n4)
+    {
+        const F4 tv = ld4(t, c), s4 = ld4(sv, c);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            a = fmaf(tv.v[q], s4.v[q], a);
+            b = fmaf(tv.v[q], tv.v[q], b);
+        }
+    }
+    block_store<0>((double)a, pa);
+    block_store<0>((double)b, pb);
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_bicg_update_f4(float *__restrict__ x, float *__restrict__ r, const float *__restrict__ ph,
+                 const float *__restrict__ sh, const float *__restrict__ sv,
+                 const float *__restrict__ t, const float *__restrict__ rh, size_t n4,
+                 const BicgScalars *sc, double *pa, double *pb)
+{
+    const float alpha = (float)sc->alpha, omega = (float)sc->omega;
+    float a = 0, b = 0;
+    TPMG_GRID_LOOP4(n4)
+    {
+        F4 xv = ld4w(x, c);
+        const F4 p4 = ld4(ph, c), s4 = ld4(sh, c), v4 = ld4(sv, c), t4 = ld4(t, c),
+                 h4 = ld4(rh, c);
+        F4 rv;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            xv.v[q] = fmaf(omega, s4.v[q], fmaf(alpha, p4.v[q], xv.v[q]));
+            rv.v[q] = fmaf(-omega, t4.v[q], v4.v[q]);
+            a = fmaf(rv.v[q], rv.v[q], a);
+            b = fmaf(h4.v[q], rv.v[q], b);
+        }
+        st4(x, c, xv);
+        st4(r, c, rv);
+    }
+    block_store<0>((double)a, pa);
+    block_store<0>((double)b, pb);
+}
+
+#undef TPMG_GRID_LOOP4
+
+}  // namespace
+
 // p = r (first iteration) or p = r + beta (p - omega v)
 template <typename T, bool FIRST>
 __global__ void __launch_bounds__(kBlock)
@@ -33,6 +158,13 @@ cudaError_t launch_bicg_dir(T *p, const T *r, const T *v, size_t n, const BicgSc
                             bool first, cudaStream_t s)
 {
     const int g = vec_grid(n);
+    if constexpr (sizeof(T) == 4) {
+        if (f4_ok(n, p, r, v)) {
+            if (first) k_bicg_dir_f4<true><<<g, kBlock, 0, s>>>(p, r, v, n / 4, sc);
+            else k_bicg_dir_f4<false><<<g, kBlock, 0, s>>>(p, r, v, n / 4, sc);
+            return cudaGetLastError();
+        }
+    }
     if (first) k_bicg_dir<T, true><<<g, kBlock, 0, s>>>(p, r, v, n, sc);
     else k_bicg_dir<T, false><<<g, kBlock, 0, s>>>(p, r, v, n, sc);
     return cudaGetLastError();
@@ -55,6 +187,12 @@ template <typename T>
 cudaError_t launch_bicg_s(T *sv, const T *r, const T *v, size_t n, const BicgScalars *sc,
                           cudaStream_t s)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (f4_ok(n, sv, r, v)) {
+            k_bicg_s_f4<<<vec_grid(n), kBlock, 0, s>>>(sv, r, v, n / 4, sc);
+            return cudaGetLastError();
+        }
+    }
     k_bicg_s<T><<<vec_grid(n), kBlock, 0, s>>>(sv, r, v, n, sc);
     return cudaGetLastError();
 }
@@ -80,6 +218,12 @@ template <typename T>
 int launch_dot2(const T *t, const T *sv, size_t n, double *pa, double *pb, cudaStream_t s)
 {
     const int g = vec_grid(n);
+    if constexpr (sizeof(T) == 4) {
+        if (f4_ok(n, t, sv)) {
+            k_dot2_f4<<<g, kBlock, 0, s>>>(t, sv, n / 4, pa, pb);
+            return g;
+        }
+    }
     k_dot2<T><<<g, kBlock, 0, s>>>(t, sv, n, pa, pb);
     return g;
 }
@@ -113,6 +257,12 @@ int launch_bicg_update(T *x, T *r, const T *ph, const T *sh, const T *sv, const 
                        cudaStream_t s)
 {
     const int g = vec_grid(n);
+    if constexpr (sizeof(T) == 4) {
+        if (f4_ok(n, x, r, ph, sh, sv, t, rh)) {
+            k_bicg_update_f4<<<g, kBlock, 0, s>>>(x, r, ph, sh, sv, t, rh, n / 4, sc, pa, pb);
+            return g;
+        }
+    }
     k_bicg_update<T><<<g, kBlock, 0, s>>>(x, r, ph, sh, sv, t, rh, n, sc, pa, pb);
     return g;
 }
