@@ -1,4 +1,5 @@
-// Kernels of the nonsymmetric (directed-coupling) operator, FP64.
+// Kernels of the nonsymmetric (directed-coupling) operator: the solve kernels in FP64
+// and FP32, the setup kernels in FP64.
 //
 // Every face carries two couplings, one for each row it enters (the row's
 // own coupling to its east / north / upper neighbour, and the neighbour
