@@ -374,7 +374,9 @@ __device__ __forceinline__ void smooth_load(SmoothLoads<T> &s, const LevelDev<T>
 // 0) loads with the L2 hints and an 8-layer FP32 forward pipeline.  BACK > 0
 // overrides the backward depth (the batched kernels, which hold their
 // work-item descriptors in registers as well).
-template <typename T, bool DOT = false, int BACK = 0>
+// YOUT: the forward values wait in the thread's own output column (read back
+// from L2 and overwritten on the way back) instead of shared memory.
+template <typename T, bool DOT = false, int BACK = 0, bool YOUT = false>
 __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__restrict__ b,
                                               const T *__restrict__ uin, T *__restrict__ uout,
                                               T omega, int col, unsigned char *smraw,
@@ -414,7 +416,10 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
                 v = fma(c.tyn, c.un, v);
                 v = fma(c.tys, c.us, v);
                 const T y = fma(tdn, yprev, v) * c.m;
-                ys[(size_t)k * bd + tid] = y;
+                if (YOUT)
+                    uout[(size_t)k * plane + col] = y;
+                else
+                    ys[(size_t)k * bd + tid] = y;
                 yprev = y;
                 tdn = c.tz;
                 if (k + kDepth < nz)
@@ -445,7 +450,8 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
             const int k = k0 - d;
             if (k >= 0) {
                 const size_t o = (size_t)k * plane + col;
-                if (k < nz - 1) xk = xk + fma(-dqp[d], xk, ys[(size_t)k * bd + tid]);
+                if (k < nz - 1)
+                    xk = xk + fma(-dqp[d], xk, YOUT ? uout[o] : ys[(size_t)k * bd + tid]);
                 const T uo = fma(om1, up[d], omega * xk);
                 uout[o] = uo;
                 if (DOT) *dacc = fma(bp[d], uo, *dacc);

@@ -182,6 +182,13 @@ int launch_stencil(const LevelDev<T> &L, int mode, const T *b, const T *x, T *y,
 // read eleven values per cell, and the register pipeline of smooth_column
 // keeps more of them in flight than a shared-memory ring of the same depth
 // would at its occupancy.
+// FP64 sweeps on a guess keep their forward values in the output column:
+// 90 registers allow 5 blocks per SM, shared memory for nz x 128 doubles
+// only 3.  (FP32 is register-limited at 4 blocks either way, and its
+// forward values are better kept out of DRAM.)
+template <typename T>
+constexpr bool kYOut = sizeof(T) == 8;
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_smooth(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ uin, T *__restrict__ uout,
@@ -189,8 +196,8 @@ k_smooth(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ uin, T *_
 {
     if (flag && !*flag) return;
     extern __shared__ __align__(16) unsigned char smraw[];
-    smooth_column<T>(L, b, uin, uout, omega, blockIdx.x * blockDim.x + threadIdx.x,
-                                  smraw);
+    smooth_column<T, false, 0, kYOut<T>>(L, b, uin, uout, omega,
+                                         blockIdx.x * blockDim.x + threadIdx.x, smraw);
 }
 
 template <typename T>
@@ -215,7 +222,7 @@ k_smooth_dot(LevelDev<T> L, const T *__restrict__ b, const T *__restrict__ uin,
     if (flag && !*flag) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     T acc = 0;
-    smooth_column<T, true>(L, b, uin, uout, omega,
+    smooth_column<T, true, 0, kYOut<T>>(L, b, uin, uout, omega,
                                         blockIdx.x * blockDim.x + threadIdx.x, smraw, &acc);
     block_store<0>((double)acc, partial);
 }
@@ -224,7 +231,7 @@ template <typename T>
 int launch_smooth_dot(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out, double omega,
                       double *partial, cudaStream_t s, const int *flag)
 {
-    const size_t smem = (size_t)L.nz * kBlock * sizeof(T);
+    const size_t smem = kYOut<T> ? 0 : (size_t)L.nz * kBlock * sizeof(T);
     const int ncol = L.nlon * L.nlat;
     const int grid = (ncol + kBlock - 1) / kBlock;
     k_smooth_dot<T><<<grid, kBlock, smem, s>>>(L, b, u_in, u_out, (T)omega, partial, flag);
@@ -339,7 +346,7 @@ cudaError_t launch_smooth(const LevelDev<T> &L, const T *b, const T *u_in, T *u_
         const size_t smem = ring_smem_bytes<T, true>(L.nz, kBlock);
         k_smooth0<T><<<grid, kBlock, smem, s>>>(L, b, u_out, (T)omega, flag);
     } else {
-        const size_t smem = (size_t)L.nz * kBlock * sizeof(T);
+        const size_t smem = kYOut<T> ? 0 : (size_t)L.nz * kBlock * sizeof(T);
         k_smooth<T><<<grid, kBlock, smem, s>>>(L, b, u_in, u_out, (T)omega, flag);
     }
     return cudaGetLastError();
