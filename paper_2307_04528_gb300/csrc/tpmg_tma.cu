@@ -35,7 +35,12 @@
 // backward pass (in shared memory they cap residency; kept in L2 through
 // the output array, the sweep with its fused inner product still ran at
 // 0.96 ms against 0.82 ms at 1536 x 1152 x 70), so the sweeps keep the
-// register pipeline.
+// register pipeline.  Nor did the sweep from a zero guess: its layer of a
+// 32 x 8 tile is only 3 KB (b, t_z, 1/p; 1 KB of q/p on the way back), a
+// ring handoff takes ~3 us under load, and the forward values (70 KB per
+// tile) leave room for two blocks of eight stages per SM, ~50 KB in flight:
+// 1.17 ms against 0.48 ms for the per-thread cp.async ring, which keeps
+// each thread's own copies in flight with no handoff between warps.
 //
 // Waits on the mbarriers are bounded: a thread that gives up records it in
 // a device flag (MG_ERR_TIMEOUT at the end of a solve) and raises an abort
