@@ -285,6 +285,22 @@ int mg_level_prolong_add(mg_handle *h, int level, int prec, const void *ec, void
  * scaled (FP32 level l holds c * coefficients); 0 when not built. */
 double mg_fp32_scale(const mg_handle *h);
 
+/* The precision changes of the mixed-precision refinement (Section 1:
+ * single-precision multigrid; the outer residual and the update in double
+ * precision), on n device values, stream-ordered, no handle needed.
+ * mg_cast_fp32: y[i] = x[i] * scale rounded to the nearest FP32 value, ties
+ *   to even (FP32 subnormals kept, +-0 below half the smallest one, +-inf
+ *   from the overflow threshold; the FP32 right-hand side of an inner solve,
+ *   scale the reciprocal of its power-of-two normalisation).  x and y must
+ *   not overlap.
+ * mg_update_fp64: x[i] += scale * e[i] in FP64 (one rounding: the product
+ *   of a power-of-two scale and an FP32 value is exact).
+ * scale must be finite and non-zero (MG_ERR_ARG); n = 0 is a no-op.  With a
+ * power-of-two scale the conversions run in integer arithmetic, off the FP64
+ * pipe, with the IEEE 754 results. */
+int mg_cast_fp32(const double *x, float *y, double scale, size_t n, void *stream);
+int mg_update_fp64(double *x, const float *e, double scale, size_t n, void *stream);
+
 /* ---- batched ensemble of independent systems.
  * n systems of possibly different shapes share one device workspace and the
  * same parameters; every V-cycle step and fine-level vector operation of all

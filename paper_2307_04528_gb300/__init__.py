@@ -18,7 +18,7 @@ from ._lib import (  # noqa: F401
 
 def __getattr__(name):
     if name in ("MGHandle", "MGBatch", "MGSolveFn", "mg_solve_fn", "NSHandle", "NSSolveFn",
-                "ns_solve_fn"):
+                "ns_solve_fn", "cast_fp32", "update_fp64"):
         from . import solver
         return getattr(solver, name)
     raise AttributeError(name)

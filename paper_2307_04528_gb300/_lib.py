@@ -102,6 +102,8 @@ def load() -> ctypes.CDLL:
         "mg_level_restrict": (I, [H, I, I, P, P, P]),
         "mg_level_prolong_add": (I, [H, I, I, P, P, P]),
         "mg_fp32_scale": (D, [H]),
+        "mg_cast_fp32": (I, [P, P, D, S, P]),
+        "mg_update_fp64": (I, [P, P, D, S, P]),
         "mg_profile_enable": (I, [H, I]),
         "mg_profile_read": (I, [H, I, I, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "mg_launch_count": (ctypes.c_ulonglong, []),

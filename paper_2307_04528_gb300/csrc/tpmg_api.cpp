@@ -1300,6 +1300,38 @@ extern "C" int mg_level_shape(const mg_handle *H, int level, int *nlon, int *nla
 
 extern "C" double mg_fp32_scale(const mg_handle *H) { return H ? H->scale32 : 0.0; }
 
+// ------------------------------------------------------------------ C ABI: precision changes
+static int conv_check(const void *a, const void *b, double scale, size_t n)
+{
+    if (!std::isfinite(scale) || scale == 0.0) return fail(MG_ERR_ARG, "bad scale");
+    if (n > 0 && (!a || !b)) return fail(MG_ERR_ARG, "null argument");
+    return MG_OK;
+}
+
+static int conv_launched(cudaError_t e)
+{
+    if (e != cudaSuccess) return fail(MG_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return MG_OK;
+}
+
+extern "C" int mg_cast_fp32(const double *x, float *y, double scale, size_t n, void *stream)
+{
+    CHK(conv_check(x, y, scale, n));
+    const char *xb = (const char *)x, *yb = (const char *)y;
+    if (n > 0 && xb < yb + n * sizeof(float) && yb < xb + n * sizeof(double))
+        return fail(MG_ERR_ARG, "x and y overlap");
+    if (n == 0) return MG_OK;
+    return conv_launched(launch_cast_scaled(x, y, scale, n, (cudaStream_t)stream));
+}
+
+extern "C" int mg_update_fp64(double *x, const float *e, double scale, size_t n, void *stream)
+{
+    CHK(conv_check(x, e, scale, n));
+    if (n == 0) return MG_OK;
+    return conv_launched(launch_update_mixed(x, e, scale, n, (cudaStream_t)stream));
+}
+
 extern "C" int mg_level_coeffs(mg_handle *H, int level, double *tx, double *ty, double *tz,
                                double *hh, void *stream)
 {

@@ -448,6 +448,7 @@ __device__ __forceinline__ void bmix_chunk(double *__restrict__ x, const double 
                                            float *__restrict__ r32, const float *__restrict__ e32,
                                            size_t c0, size_t c1, double f)
 {
+    const int sx = MODE == 0 ? pow2_exponent(f) : kNotPow2;
     if (f4_chunk(x, r, r32, e32, c0, c1)) {  // four values per load and store
 #pragma unroll 2
         for (size_t i = c0 / 4 + threadIdx.x; i < c1 / 4; i += blockDim.x) {
@@ -455,16 +456,16 @@ __device__ __forceinline__ void bmix_chunk(double *__restrict__ x, const double 
                 const double2 a = reinterpret_cast<const double2 *>(r)[2 * i];
                 const double2 b = reinterpret_cast<const double2 *>(r)[2 * i + 1];
                 reinterpret_cast<float4 *>(r32)[i] =
-                    make_float4((float)(a.x * f), (float)(a.y * f), (float)(b.x * f),
-                                (float)(b.y * f));
+                    make_float4(scaled_to_f32(a.x, f, sx), scaled_to_f32(a.y, f, sx),
+                                scaled_to_f32(b.x, f, sx), scaled_to_f32(b.y, f, sx));
             } else {
                 const float4 e = reinterpret_cast<const float4 *>(e32)[i];
                 double2 a = reinterpret_cast<double2 *>(x)[2 * i];
                 double2 b = reinterpret_cast<double2 *>(x)[2 * i + 1];
-                a.x = fma(f, (double)e.x, a.x);
-                a.y = fma(f, (double)e.y, a.y);
-                b.x = fma(f, (double)e.z, b.x);
-                b.y = fma(f, (double)e.w, b.y);
+                a.x = fma(f, f32_to_f64(e.x), a.x);
+                a.y = fma(f, f32_to_f64(e.y), a.y);
+                b.x = fma(f, f32_to_f64(e.z), b.x);
+                b.y = fma(f, f32_to_f64(e.w), b.y);
                 reinterpret_cast<double2 *>(x)[2 * i] = a;
                 reinterpret_cast<double2 *>(x)[2 * i + 1] = b;
             }
@@ -473,8 +474,8 @@ __device__ __forceinline__ void bmix_chunk(double *__restrict__ x, const double 
     }
 #pragma unroll 4
     for (size_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-        if (MODE == 0) r32[c] = (float)(r[c] * f);
-        else x[c] = fma(f, (double)e32[c], x[c]);
+        if (MODE == 0) r32[c] = scaled_to_f32(r[c], f, sx);
+        else x[c] = fma(f, f32_to_f64(e32[c]), x[c]);
     }
 }
 

@@ -10,6 +10,95 @@
 
 namespace tpmg {
 
+// ------------------------------------------------------------------ conversions
+// FP64 <-> FP32 conversions in integer arithmetic.  A hardware conversion
+// between the two formats issues on the FP64 pipe (ncu counts one FP64-pipe
+// instruction per conversion), which the refinement's residual, cast and
+// update kernels already keep busy; these run on the integer ALU instead and
+// give the results IEEE 754 defines for the conversion.
+
+// x * 2^s rounded to the nearest binary32 value, ties to even: binary32
+// subnormals where the value is below 2^-126, +-0 below half the smallest
+// subnormal, +-infinity from 2^128 (less half an ulp) up; infinities stay
+// infinite and a NaN becomes a quiet NaN of the same sign.  The product is
+// never formed, so no intermediate rounding happens.
+static __device__ __noinline__ float f64_to_f32_rn_rare(unsigned hi, unsigned lo, int s)
+{
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    const unsigned long long frac = ((unsigned long long)(hi & 0xFFFFFu) << 32) | lo;
+    if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (frac ? 0x00400000u : 0u));
+    // |x| = M 2^E with M < 2^53 (no implicit bit for a binary64 subnormal)
+    unsigned long long M = e ? (frac | (1ULL << 52)) : frac;
+    if (M == 0) return __uint_as_float(sign);
+    int E = (e ? e : 1) - 1075 + s;
+    const int lz = __clzll((long long)M) - 11;  // normalise: bit 52 set
+    M <<= lz;
+    E -= lz;
+    const int ef = E + 52 + 127;  // biased binary32 exponent of M 2^E
+    if (ef >= 255) return __uint_as_float(sign | 0x7F800000u);
+    // keep the top 24 bits (normal) or fewer (subnormal result)
+    const int shift = ef >= 1 ? 29 : 30 - ef;
+    if (shift >= 54) return __uint_as_float(sign);  // below half the smallest subnormal
+    const unsigned long long r = M >> shift, rem = M & ((1ULL << shift) - 1),
+                             half = 1ULL << (shift - 1);
+    const unsigned up = (rem > half || (rem == half && (r & 1ULL))) ? 1u : 0u;
+    // normal: (ef - 1) << 23 plus r (implicit bit at 23) carries into the
+    // exponent on rounding up; subnormal: r itself, 2^23 if it rounds up to
+    // the smallest normal
+    const unsigned bits = ef >= 1 ? ((unsigned)(ef - 1) << 23) + (unsigned)r + up
+                                  : (unsigned)r + up;
+    return __uint_as_float(sign | bits);
+}
+
+__device__ __forceinline__ float f64_to_f32_rn(double x, int s = 0)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    const int ef = e - 896 + s;  // 1023 - 127: the binary32 biased exponent
+    if (e == 0 || e == 0x7FF || ef < 1 || ef > 254) return f64_to_f32_rn_rare(hi, lo, s);
+    // normal in, normal out: 23 fraction bits kept, 29 rounded off
+    const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29), rem = lo & 0x1FFFFFFFu;
+    const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) ? 1u : 0u;
+    return __uint_as_float((hi & 0x80000000u) | ((((unsigned)ef << 23) | mant) + up));
+}
+
+// The binary64 value of a binary32 value (exact).
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+    if (e - 1u < 254u)  // normal
+        return __hiloint2double((int)(sign | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
+    if (e == 0xFFu)  // infinity, or a quiet NaN of the same sign
+        return __hiloint2double((int)(sign | 0x7FF00000u | (m ? 0x80000u | (m >> 3) : 0u)),
+                                (int)(m << 29));
+    if (m == 0) return __hiloint2double((int)sign, 0);
+    // subnormal m 2^-149 = 1.f 2^(p - 149), p the position of m's top bit
+    const int p = 31 - __clz((int)m);
+    const unsigned long long f52 = (unsigned long long)(m ^ (1u << p)) << (52 - p);
+    return __hiloint2double((int)(sign | ((unsigned)(p + 874) << 20) | (unsigned)(f52 >> 32)),
+                            (int)(unsigned)f52);
+}
+
+// f = 2^s for a positive normal binary64 power of two f, else kNotPow2.
+constexpr int kNotPow2 = 1 << 30;
+__device__ __forceinline__ int pow2_exponent(double f)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(f);
+    const int e = (int)((u >> 52) & 0x7FFu);
+    return ((u & 0x800FFFFFFFFFFFFFULL) == 0 && e != 0 && e != 0x7FF) ? e - 1023 : kNotPow2;
+}
+
+// The binary32 rounding of x f (s = pow2_exponent(f)): in integer
+// arithmetic when f is a power of two, else by the hardware conversion of
+// the FP64 product.
+__device__ __forceinline__ float scaled_to_f32(double x, double f, int s)
+{
+    return s != kNotPow2 ? f64_to_f32_rn(x, s) : (float)(x * f);
+}
+
 // ------------------------------------------------------------------ reductions
 // Maximum of two magnitudes (values >= 0 or NaN): non-negative doubles order
 // as their bit patterns read as unsigned integers, and a NaN sorts above
@@ -88,10 +177,11 @@ __device__ __forceinline__ void stencil_load(StencilLoads<T> &s, const LevelDev<
     if (MODE) s.b = __ldg(b + o + col);
 }
 
-// TO != T: y receives the rounding of out * yscale (the FP64 residual
-// handed to the FP32 inner solve; yscale a power of two).  NARROW_MUL: the
-// product is formed in TO after the rounding, exact for a yscale that is a
-// normal TO value (one FP64 operation fewer per cell).  The reduction uses out.
+// TO != T (T double, TO float): y receives the rounding of out * yscale (the
+// FP64 residual handed to the FP32 inner solve; yscale a power of two),
+// rounded in integer arithmetic (f64_to_f32_rn).  NARROW_MUL: the product is
+// formed in TO after the rounding, exact for a yscale that is a normal TO
+// value (one FP64 operation fewer per cell).  The reduction uses out.
 // HSUM: L.h holds the horizontal diagonal h + the four horizontal couplings,
 // and the horizontal terms are taken in sum form, dh x_c - sum T x_nb (four
 // FMAs instead of four subtractions and four FMAs); the vertical couplings,
@@ -146,8 +236,9 @@ __device__ __forceinline__ T stencil_column(const LevelDev<T> &L, const T *__res
                     if constexpr (sizeof(TO) == sizeof(T))
                         y[(size_t)k * plane + col] = out;
                     else
-                        y[(size_t)k * plane + col] =
-                            NARROW_MUL ? (TO)out * (TO)yscale : (TO)(out * yscale);
+                        y[(size_t)k * plane + col] = NARROW_MUL
+                                                         ? f64_to_f32_rn(out) * (TO)yscale
+                                                         : f64_to_f32_rn(out * yscale);
                     if (RED) acc = fma(out, MODE ? out : xc, acc);
                     xdn = xc;
                     tdn = c.tz;

@@ -745,21 +745,23 @@ cudaError_t launch_add(T *x, const T *e, size_t n, cudaStream_t s)
 __global__ void __launch_bounds__(kBlock)
 k_cast_scaled(const double *__restrict__ r, float *__restrict__ r32, double inv, size_t n)
 {
+    const int sx = pow2_exponent(inv);
 #pragma unroll 4
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
          c += (size_t)gridDim.x * blockDim.x)
-        r32[c] = (float)(r[c] * inv);
+        r32[c] = scaled_to_f32(r[c], inv, sx);
 }
 
 __global__ void __launch_bounds__(kBlock)
 k_cast_scaled_v4(const double2 *__restrict__ r, float4 *__restrict__ r32, double inv, size_t n4)
 {
+    const int sx = pow2_exponent(inv);
 #pragma unroll 2
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n4;
          c += (size_t)gridDim.x * blockDim.x) {
         const double2 a = __ldg(r + 2 * c), b = __ldg(r + 2 * c + 1);
-        r32[c] = make_float4((float)(a.x * inv), (float)(a.y * inv), (float)(b.x * inv),
-                             (float)(b.y * inv));
+        r32[c] = make_float4(scaled_to_f32(a.x, inv, sx), scaled_to_f32(a.y, inv, sx),
+                             scaled_to_f32(b.x, inv, sx), scaled_to_f32(b.y, inv, sx));
     }
 }
 
@@ -781,7 +783,7 @@ k_update_mixed(double *__restrict__ x, const float *__restrict__ e, double scale
 #pragma unroll 4
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
          c += (size_t)gridDim.x * blockDim.x)
-        x[c] = fma(scale, (double)e[c], x[c]);
+        x[c] = fma(scale, f32_to_f64(e[c]), x[c]);
 }
 
 __global__ void __launch_bounds__(kBlock)
@@ -792,10 +794,10 @@ k_update_mixed_v4(double2 *__restrict__ x, const float4 *__restrict__ e, double 
          c += (size_t)gridDim.x * blockDim.x) {
         const float4 ev = __ldg(e + c);
         double2 a = x[2 * c], b = x[2 * c + 1];
-        a.x = fma(scale, (double)ev.x, a.x);
-        a.y = fma(scale, (double)ev.y, a.y);
-        b.x = fma(scale, (double)ev.z, b.x);
-        b.y = fma(scale, (double)ev.w, b.y);
+        a.x = fma(scale, f32_to_f64(ev.x), a.x);
+        a.y = fma(scale, f32_to_f64(ev.y), a.y);
+        b.x = fma(scale, f32_to_f64(ev.z), b.x);
+        b.y = fma(scale, f32_to_f64(ev.w), b.y);
         x[2 * c] = a;
         x[2 * c + 1] = b;
     }
@@ -964,9 +966,10 @@ cudaError_t launch_column_lu(const LevelDev<double> &L, double *m, double *dq, c
 __global__ void __launch_bounds__(kBlock)
 k_to_float(const double *__restrict__ in, float *__restrict__ out, double scale, size_t n)
 {
+    const int sx = pow2_exponent(scale);
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n;
          c += (size_t)gridDim.x * blockDim.x)
-        out[c] = (float)(in[c] * scale);
+        out[c] = scaled_to_f32(in[c], scale, sx);
 }
 
 cudaError_t launch_to_float(const double *in, float *out, double scale, size_t n, cudaStream_t s)

@@ -257,6 +257,29 @@ class MGHandle:
         return u
 
 
+def cast_fp32(x, scale):
+    """The FP32 rounding of x * scale (mg_cast_fp32; x a CUDA float64
+    tensor): the right-hand side handed to an FP32 inner solve."""
+    if x.dtype != torch.float64 or not x.is_cuda:
+        raise TypeError("x must be a CUDA float64 tensor")
+    x = x.contiguous()
+    y = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    L.check(L.load().mg_cast_fp32(_ptr(x), _ptr(y), float(scale), x.numel(), _stream()))
+    return y
+
+
+def update_fp64(x, e, scale):
+    """x += scale * e in FP64 in place (mg_update_fp64; x CUDA float64, e
+    CUDA float32 of the same size): the refinement's update."""
+    if x.dtype != torch.float64 or e.dtype != torch.float32 or not (x.is_cuda and e.is_cuda):
+        raise TypeError("x must be CUDA float64 and e CUDA float32")
+    if x.numel() != e.numel() or not x.is_contiguous():
+        raise ValueError("x must be contiguous and e of the same size")
+    e = e.contiguous()
+    L.check(L.load().mg_update_fp64(_ptr(x), _ptr(e), float(scale), x.numel(), _stream()))
+    return x
+
+
 class MGFloorWarning(RuntimeWarning):
     """A differentiable solve stopped on maxit above its tolerance but below the
     caller's floor_accept, and its solution was used."""
