@@ -574,20 +574,22 @@ __device__ __forceinline__ void smooth_column(const LevelDev<T> &L, const T *__r
 // wrote after a block barrier.  All 32 lanes must call it with the same
 // col < ncol.
 constexpr int kWarpLayers = (kMaxLayers + 31) / 32;  // layers per lane at most
+// CM: the layers per lane the code is unrolled for (ceil(nz / 32) <= CM <=
+// kWarpLayers; the launchers take the smallest of 2, 3, kWarpLayers that
+// holds the level, so no predicated-off layer slots are issued).
 
 // The two scans of the warp sweep over one lane's layers k0 .. k0 + C - 1:
 // v holds the right-hand sides v_k on entry and the column solution x_k of
 // H_z x = v on return; tprev = t_{k0-1} (0 for the first lane).
-template <typename T>
-__device__ __forceinline__ void warp_column_scan(T (&v)[kWarpLayers], const T (&tz)[kWarpLayers],
-                                                 const T (&m)[kWarpLayers],
-                                                 const T (&dq)[kWarpLayers], T tprev, int C,
-                                                 int k0, int nz, int lane)
+template <typename T, int CM>
+__device__ __forceinline__ void warp_column_scan(T (&v)[CM], const T (&tz)[CM], const T (&m)[CM],
+                                                 const T (&dq)[CM], T tprev, int C, int k0,
+                                                 int nz, int lane)
 {
     // forward: this lane's map y_out = A y_in + Cy, then an inclusive scan
     T A = 1, Cy = 0, tp = tprev;
 #pragma unroll
-    for (int c = 0; c < kWarpLayers; ++c) {
+    for (int c = 0; c < CM; ++c) {
         if (c < C && k0 + c < nz) {
             const T a = tp * m[c];
             Cy = fma(a, Cy, v[c] * m[c]);
@@ -608,7 +610,7 @@ __device__ __forceinline__ void warp_column_scan(T (&v)[kWarpLayers], const T (&
     if (lane == 0) y = T(0);
     tp = tprev;
 #pragma unroll
-    for (int c = 0; c < kWarpLayers; ++c) {
+    for (int c = 0; c < CM; ++c) {
         if (c < C && k0 + c < nz) {
             y = fma(tp, y, v[c]) * m[c];
             v[c] = y;  // v now holds y
@@ -619,7 +621,7 @@ __device__ __forceinline__ void warp_column_scan(T (&v)[kWarpLayers], const T (&
     // backward: x_bottom = E x_above + F over this lane's layers, suffix scan
     T E = 1, F = 0;
 #pragma unroll
-    for (int c = kWarpLayers - 1; c >= 0; --c) {
+    for (int c = CM - 1; c >= 0; --c) {
         if (c < C && k0 + c < nz) {
             const T e = T(1) - dq[c];
             F = fma(e, F, v[c]);
@@ -638,7 +640,7 @@ __device__ __forceinline__ void warp_column_scan(T (&v)[kWarpLayers], const T (&
     T x = __shfl_down_sync(0xffffffffu, F, 1);
     if (lane == 31) x = T(0);
 #pragma unroll
-    for (int c = kWarpLayers - 1; c >= 0; --c) {
+    for (int c = CM - 1; c >= 0; --c) {
         if (c < C && k0 + c < nz) {
             x = x + fma(-dq[c], x, v[c]);
             v[c] = x;  // v now holds x
@@ -646,7 +648,7 @@ __device__ __forceinline__ void warp_column_scan(T (&v)[kWarpLayers], const T (&
     }
 }
 
-template <typename T, bool ZERO>
+template <typename T, bool ZERO, int CM = kWarpLayers>
 __device__ __forceinline__ void smooth_warp_column(const LevelDev<T> &L, const T *__restrict__ b,
                                                    const T *uin, T *uout, T omega, int col,
                                                    int lane)
@@ -659,9 +661,9 @@ __device__ __forceinline__ void smooth_warp_column(const LevelDev<T> &L, const T
     const size_t plane = (size_t)nlon * nlat;
     const int C = (nz + 31) / 32;
     const int k0 = lane * C;
-    T v[kWarpLayers], tz[kWarpLayers], m[kWarpLayers], dq[kWarpLayers], u0[kWarpLayers];
+    T v[CM], tz[CM], m[CM], dq[CM], u0[CM];
 #pragma unroll
-    for (int c = 0; c < kWarpLayers; ++c) {
+    for (int c = 0; c < CM; ++c) {
         const int k = k0 + c;
         v[c] = tz[c] = m[c] = dq[c] = u0[c] = T(0);
         if (c < C && k < nz) {
@@ -681,10 +683,10 @@ __device__ __forceinline__ void smooth_warp_column(const LevelDev<T> &L, const T
         }
     }
     const T tprev = (k0 >= 1 && k0 - 1 < nz) ? __ldg(L.tz + (size_t)(k0 - 1) * plane + col) : T(0);
-    warp_column_scan<T>(v, tz, m, dq, tprev, C, k0, nz, lane);
+    warp_column_scan<T, CM>(v, tz, m, dq, tprev, C, k0, nz, lane);
     const T om1 = T(1) - omega;
 #pragma unroll
-    for (int c = 0; c < kWarpLayers; ++c) {
+    for (int c = 0; c < CM; ++c) {
         const int k = k0 + c;
         if (c < C && k < nz)
             uout[(size_t)k * plane + col] = ZERO ? omega * v[c] : fma(om1, u0[c], omega * v[c]);
@@ -702,7 +704,7 @@ __device__ __forceinline__ void smooth_warp_column(const LevelDev<T> &L, const T
 // kCoarseShArrays * ncol * nz values of dynamic shared memory.
 constexpr int kCoarseShArrays = 8;
 
-template <typename T>
+template <typename T, int CM = kWarpLayers>
 __device__ __forceinline__ void coarse_solve_sh(const LevelDev<T> &L, const T *__restrict__ b,
                                                 T *__restrict__ out, T omega, int sweeps, T *sh)
 {
@@ -732,9 +734,9 @@ __device__ __forceinline__ void coarse_solve_sh(const LevelDev<T> &L, const T *_
             const bool hasN = j + 1 < nlat, hasS = j > 0;
             const int oc = col * nz, oe = ie * nz, ow = iw * nz;
             const int on = (col + nlon) * nz, os = (col - nlon) * nz;
-            T v[kWarpLayers], tz[kWarpLayers], m[kWarpLayers], dq[kWarpLayers], u0[kWarpLayers];
+            T v[CM], tz[CM], m[CM], dq[CM], u0[CM];
 #pragma unroll
-            for (int c = 0; c < kWarpLayers; ++c) {
+            for (int c = 0; c < CM; ++c) {
                 const int k = k0 + c;
                 v[c] = tz[c] = m[c] = dq[c] = u0[c] = T(0);
                 if (c < C && k < nz) {
@@ -753,9 +755,9 @@ __device__ __forceinline__ void coarse_solve_sh(const LevelDev<T> &L, const T *_
                 }
             }
             const T tprev = (k0 >= 1 && k0 - 1 < nz) ? stz[oc + k0 - 1] : T(0);
-            warp_column_scan<T>(v, tz, m, dq, tprev, C, k0, nz, lane);
+            warp_column_scan<T, CM>(v, tz, m, dq, tprev, C, k0, nz, lane);
 #pragma unroll
-            for (int c = 0; c < kWarpLayers; ++c) {
+            for (int c = 0; c < CM; ++c) {
                 const int k = k0 + c;
                 if (c < C && k < nz)
                     oth[oc + k] = it == 0 ? omega * v[c] : fma(om1, u0[c], omega * v[c]);
@@ -1100,7 +1102,7 @@ __device__ __forceinline__ void resid_restrict_band(const LevelDev<T> &F, const 
                                                     const T *__restrict__ b,
                                                     const T *__restrict__ u, T *__restrict__ bc,
                                                     int warp, int lane, int Jb, int k,
-                                                    T om1 = T(0))
+                                                    T om1 = T(0), int band = kRRBand)
 {
     using P2 = typename Pair<T>::type;
     constexpr unsigned kAll = 0xffffffffu;
@@ -1109,7 +1111,7 @@ __device__ __forceinline__ void resid_restrict_band(const LevelDev<T> &F, const 
     const bool owned = lane >= 1 && lane <= kRROwned && Iown < nc;
     int I = Iown < 0 ? Iown + nc : (Iown >= nc ? Iown - nc : Iown);
     if (I >= nc) I = nc - 1;  // past the east neighbour of the last column: unused
-    const int Je = min(ncJ, Jb + kRRBand);
+    const int Je = min(ncJ, Jb + band);
     const size_t plane = (size_t)nf * nlat, plane_c = (size_t)nc * ncJ;
     const size_t o = (size_t)k * plane + 2 * I;
     const bool up = k + 1 < nz, dn = k > 0;

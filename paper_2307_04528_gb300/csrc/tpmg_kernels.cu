@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "tpmg_device.cuh"
 #include "tpmg_internal.h"
@@ -240,7 +241,7 @@ int launch_smooth_dot(const LevelDev<T> &L, const T *b, const T *u_in, T *u_out,
 
 // One warp per column (smooth_warp_column), for levels small enough that
 // the serial column recurrences would dominate.
-template <typename T, bool ZERO>
+template <typename T, bool ZERO, int CM>
 __global__ void __launch_bounds__(kBlock)
 k_smooth_warp(LevelDev<T> L, const T *__restrict__ b, const T *uin, T *uout, T omega,
               const int *__restrict__ flag)
@@ -248,7 +249,22 @@ k_smooth_warp(LevelDev<T> L, const T *__restrict__ b, const T *uin, T *uout, T o
     if (flag && !*flag) return;
     const int col = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     if (col >= L.nlon * L.nlat) return;  // whole warps
-    smooth_warp_column<T, ZERO>(L, b, uin, uout, omega, col, threadIdx.x & 31);
+    smooth_warp_column<T, ZERO, CM>(L, b, uin, uout, omega, col, threadIdx.x & 31);
+}
+
+// Layers per lane the warp sweeps are unrolled for (smooth_warp_column):
+// the smallest of 2, 3 and kWarpLayers that holds nz layers in 32 lanes.
+static inline int warp_layers_for(int nz) { return nz <= 64 ? 2 : nz <= 96 ? 3 : kWarpLayers; }
+
+// f.template operator()<CM>() for the CM of nz.
+template <typename F>
+static inline auto with_warp_layers(int nz, F &&f)
+{
+    switch (warp_layers_for(nz)) {
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 3: return f(std::integral_constant<int, 3>{});
+    default: return f(std::integral_constant<int, kWarpLayers>{});
+    }
 }
 
 // The coarsest-level solve (Section 2.3's simple iteration: `sweeps`
@@ -256,7 +272,7 @@ k_smooth_warp(LevelDev<T> L, const T *__restrict__ b, const T *uin, T *uout, T o
 // columns, a block barrier separates the sweeps, and the sweeps alternate
 // between out and scratch so that the last one lands in out.
 
-template <typename T>
+template <typename T, int CM>
 __global__ void __launch_bounds__(kCoarseSolveThreads)
 k_coarse_solve(LevelDev<T> L, const T *__restrict__ b, T *out, T *scratch, T omega, int sweeps,
                const int *__restrict__ flag)
@@ -266,11 +282,12 @@ k_coarse_solve(LevelDev<T> L, const T *__restrict__ b, T *out, T *scratch, T ome
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     T *cur = (sweeps % 2 == 1) ? out : scratch;
     T *oth = (cur == out) ? scratch : out;
-    for (int c = warp; c < ncol; c += nw) smooth_warp_column<T, true>(L, b, nullptr, cur, omega, c, lane);
+    for (int c = warp; c < ncol; c += nw)
+        smooth_warp_column<T, true, CM>(L, b, nullptr, cur, omega, c, lane);
     for (int it = 1; it < sweeps; ++it) {
         __syncthreads();  // the previous sweep is visible to the whole block
         for (int c = warp; c < ncol; c += nw)
-            smooth_warp_column<T, false>(L, b, cur, oth, omega, c, lane);
+            smooth_warp_column<T, false, CM>(L, b, cur, oth, omega, c, lane);
         T *t = cur;
         cur = oth;
         oth = t;
@@ -278,14 +295,14 @@ k_coarse_solve(LevelDev<T> L, const T *__restrict__ b, T *out, T *scratch, T ome
 }
 
 // The same solve with the whole level in shared memory (coarse_solve_sh).
-template <typename T>
+template <typename T, int CM>
 __global__ void __launch_bounds__(kCoarseSolveThreads)
 k_coarse_solve_sh(LevelDev<T> L, const T *__restrict__ b, T *__restrict__ out, T omega, int sweeps,
                   const int *__restrict__ flag)
 {
     if (flag && !*flag) return;
     extern __shared__ __align__(16) unsigned char sh_raw[];
-    coarse_solve_sh<T>(L, b, out, omega, sweeps, reinterpret_cast<T *>(sh_raw));
+    coarse_solve_sh<T, CM>(L, b, out, omega, sweeps, reinterpret_cast<T *>(sh_raw));
 }
 
 // Opt-in shared memory per block (set by smooth_prepare).
@@ -319,12 +336,17 @@ cudaError_t launch_coarse_solve(const LevelDev<T> &L, const T *b, T *out, T *scr
                                 int sweeps, cudaStream_t s)
 {
     const size_t sh = coarse_sh_bytes(L.nlon * L.nlat, L.nz, sizeof(T));
-    if (sweeps >= 1 && coarse_sh_fits(L.nlon * L.nlat, L.nz, sizeof(T)))
-        k_coarse_solve_sh<T><<<1, kCoarseSolveThreads, sh, s>>>(L, b, out, (T)omega, sweeps,
-                                                                nullptr);
-    else
-        k_coarse_solve<T><<<1, kCoarseSolveThreads, 0, s>>>(L, b, out, scratch, (T)omega, sweeps,
-                                                             nullptr);
+    const bool in_sh = sweeps >= 1 && coarse_sh_fits(L.nlon * L.nlat, L.nz, sizeof(T));
+    with_warp_layers(L.nz, [&](auto cm) {
+        constexpr int CM = decltype(cm)::value;
+        if (in_sh)
+            k_coarse_solve_sh<T, CM><<<1, kCoarseSolveThreads, sh, s>>>(L, b, out, (T)omega,
+                                                                        sweeps, nullptr);
+        else
+            k_coarse_solve<T, CM><<<1, kCoarseSolveThreads, 0, s>>>(L, b, out, scratch,
+                                                                    (T)omega, sweeps, nullptr);
+        return 0;
+    });
     return cudaGetLastError();
 }
 
@@ -334,13 +356,21 @@ cudaError_t launch_smooth(const LevelDev<T> &L, const T *b, const T *u_in, T *u_
 {
     const int ncol = L.nlon * L.nlat;
     const int grid = (ncol + kBlock - 1) / kBlock;
-    if (sizeof(T) == 4 && (size_t)ncol * L.nz <= kWarpSweepCells) {
-        const int wgrid = (int)(((size_t)ncol * 32 + kBlock - 1) / kBlock);
-        if (u_in == nullptr)
-            k_smooth_warp<T, true><<<wgrid, kBlock, 0, s>>>(L, b, nullptr, u_out, (T)omega, flag);
-        else
-            k_smooth_warp<T, false><<<wgrid, kBlock, 0, s>>>(L, b, u_in, u_out, (T)omega, flag);
-        return cudaGetLastError();
+    if constexpr (sizeof(T) == 4) {
+        if ((size_t)ncol * L.nz <= kWarpSweepCells) {
+            const int wgrid = (int)(((size_t)ncol * 32 + kBlock - 1) / kBlock);
+            with_warp_layers(L.nz, [&](auto cm) {
+                constexpr int CM = decltype(cm)::value;
+                if (u_in == nullptr)
+                    k_smooth_warp<T, true, CM><<<wgrid, kBlock, 0, s>>>(L, b, nullptr, u_out,
+                                                                        (T)omega, flag);
+                else
+                    k_smooth_warp<T, false, CM><<<wgrid, kBlock, 0, s>>>(L, b, u_in, u_out,
+                                                                         (T)omega, flag);
+                return 0;
+            });
+            return cudaGetLastError();
+        }
     }
     if (u_in == nullptr) {
         const size_t smem = ring_smem_bytes<T, true>(L.nz, kBlock);
@@ -380,8 +410,12 @@ cudaError_t smooth_prepare()
     const void *kernels[] = {(const void *)k_smooth<double>,     (const void *)k_smooth<float>,
                              (const void *)k_smooth0<double>,    (const void *)k_smooth0<float>,
                              (const void *)k_smooth_dot<double>, (const void *)k_smooth_dot<float>,
-                             (const void *)k_coarse_solve_sh<double>,
-                             (const void *)k_coarse_solve_sh<float>};
+                             (const void *)k_coarse_solve_sh<double, 2>,
+                             (const void *)k_coarse_solve_sh<double, 3>,
+                             (const void *)k_coarse_solve_sh<double, kWarpLayers>,
+                             (const void *)k_coarse_solve_sh<float, 2>,
+                             (const void *)k_coarse_solve_sh<float, 3>,
+                             (const void *)k_coarse_solve_sh<float, kWarpLayers>};
     for (const void *k : kernels)
         if ((e = set_dynamic_smem_limit(k, lim)) != cudaSuccess) return e;
     return cudaSuccess;
@@ -414,7 +448,9 @@ k_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ r, T *__restrict__ bc
 }
 
 // Residual and restriction fused (resid_restrict_band): grid x = warps of
-// kRROwned coarse columns, y = layers, z = bands of kRRBand coarse rows.  With
+// kRROwned coarse columns, y = layers, z = bands of `band` coarse rows
+// (kRRBand; fewer on levels too small to fill the GPU, shortening the serial
+// row walk of each warp at the cost of forming band-edge rows twice).  With
 // the layers before the bands in launch order, the blocks of one band at
 // neighbouring layers run together and share the planes above and below in
 // L2 (bands before layers: 0.662 instead of 0.614 ms at 1536 x 1152 x 70).
@@ -425,13 +461,13 @@ k_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ r, T *__restrict__ bc
 template <typename T, bool PRE>
 __global__ void __launch_bounds__(kBlock, (PRE && sizeof(T) == 4) ? 12 : 0)
 k_resid_restrict(LevelDev<T> F, LinkDev K, const T *__restrict__ b, const T *__restrict__ u,
-                 T *__restrict__ bc, T om1, int band0, const int *__restrict__ flag)
+                 T *__restrict__ bc, T om1, int band0, int band, const int *__restrict__ flag)
 {
     if (flag && !*flag) return;
     const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     if (warp * kRROwned >= F.nlon / 2) return;  // whole warps
     resid_restrict_band<T, PRE>(F, K, b, u, bc, warp, threadIdx.x & 31,
-                                (band0 + (int)blockIdx.z) * kRRBand, blockIdx.y, om1);
+                                (band0 + (int)blockIdx.z) * band, blockIdx.y, om1, band);
 }
 
 bool resid_restrict_fits(const void *b, const void *u, size_t value_bytes)
@@ -446,14 +482,21 @@ cudaError_t launch_resid_restrict(const LevelDev<T> &F, const LinkDev &K, const 
 {
     const int nc = F.nlon / 2;
     const int warps = (nc + kRROwned - 1) / kRROwned;
-    const int bands = (K.nlat_c + kRRBand - 1) / kRRBand;
+    // the widest band whose warps still make two waves of 48 per SM
+    int band = kRRBand;
+    while (band > 1 && (long long)warps * F.nz * ((K.nlat_c + band - 1) / band) <
+                           2LL * 48 * g_sms)
+        band /= 2;
+    const int bands = (K.nlat_c + band - 1) / band;
     const T om1 = T(1) - (T)omega;
     for (int band0 = 0; band0 < bands; band0 += 65535) {  // grid z limit
         const dim3 grid((warps * 32 + kBlock - 1) / kBlock, F.nz, std::min(65535, bands - band0));
         if (presmooth)
-            k_resid_restrict<T, true><<<grid, kBlock, 0, s>>>(F, K, b, u, bc, om1, band0, flag);
+            k_resid_restrict<T, true><<<grid, kBlock, 0, s>>>(F, K, b, u, bc, om1, band0, band,
+                                                              flag);
         else
-            k_resid_restrict<T, false><<<grid, kBlock, 0, s>>>(F, K, b, u, bc, om1, band0, flag);
+            k_resid_restrict<T, false><<<grid, kBlock, 0, s>>>(F, K, b, u, bc, om1, band0, band,
+                                                               flag);
     }
     return cudaGetLastError();
 }
