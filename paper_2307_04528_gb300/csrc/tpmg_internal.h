@@ -111,6 +111,10 @@ template <typename T>
 cudaError_t launch_resid_restrict(const LevelDev<T> &F, const LinkDev &K, const T *b, const T *u,
                                   T *bc, cudaStream_t s, const int *flag = nullptr,
                                   bool presmooth = false, double omega = 0.0);
+// Coarse rows per band of its row walk: kRRBand, fewer on levels too small
+// to fill the GPU (the same sums in the same order whatever the band).
+template <typename T>
+int rr_band(const LevelDev<T> &F, const LinkDev &K);
 template <typename T>
 cudaError_t launch_restrict(const LevelDev<T> &F, const LinkDev &K, const T *r, T *bc,
                             cudaStream_t s, const int *flag = nullptr);

@@ -475,6 +475,18 @@ bool resid_restrict_fits(const void *b, const void *u, size_t value_bytes)
     return (uintptr_t)b % (2 * value_bytes) == 0 && (uintptr_t)u % (2 * value_bytes) == 0;
 }
 
+// Coarse rows per band of the fused residual + restriction: the widest
+// band (of kRRBand, 4, 2, 1) whose warps still make two waves of 48 per SM.
+template <typename T>
+int rr_band(const LevelDev<T> &F, const LinkDev &K)
+{
+    const long long warps = (F.nlon / 2 + kRROwned - 1) / kRROwned;
+    int band = kRRBand;
+    while (band > 1 && warps * F.nz * ((K.nlat_c + band - 1) / band) < 2LL * 48 * g_sms)
+        band /= 2;
+    return band;
+}
+
 template <typename T>
 cudaError_t launch_resid_restrict(const LevelDev<T> &F, const LinkDev &K, const T *b, const T *u,
                                   T *bc, cudaStream_t s, const int *flag, bool presmooth,
@@ -482,11 +494,7 @@ cudaError_t launch_resid_restrict(const LevelDev<T> &F, const LinkDev &K, const 
 {
     const int nc = F.nlon / 2;
     const int warps = (nc + kRROwned - 1) / kRROwned;
-    // the widest band whose warps still make two waves of 48 per SM
-    int band = kRRBand;
-    while (band > 1 && (long long)warps * F.nz * ((K.nlat_c + band - 1) / band) <
-                           2LL * 48 * g_sms)
-        band /= 2;
+    const int band = rr_band(F, K);
     const int bands = (K.nlat_c + band - 1) / band;
     const T om1 = T(1) - (T)omega;
     for (int band0 = 0; band0 < bands; band0 += 65535) {  // grid z limit
@@ -1065,6 +1073,7 @@ cudaError_t launch_coeff_grad(int nlon, int nlat, int nz, const double *lam, con
     template cudaError_t launch_resid_restrict<T>(const LevelDev<T> &, const LinkDev &, const T *, \
                                                   const T *, T *, cudaStream_t, const int *, bool, \
                                                   double);                                        \
+    template int rr_band<T>(const LevelDev<T> &, const LinkDev &);                                 \
     template cudaError_t launch_restrict<T>(const LevelDev<T> &, const LinkDev &, const T *, T *,  \
                                             cudaStream_t, const int *);                           \
     template cudaError_t launch_prolong_add<T>(const LevelDev<T> &, const LinkDev &, const T *,    \
